@@ -1,0 +1,245 @@
+"""FP64 CPU oracle of the 2DGS rasterizer hot path (test infrastructure).
+
+This package is the plain, slow, double-precision definition that the CUDA
+library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import it; the product path never
+does.  It shares no code with the CUDA library.  The C source
+``gs2d_oracle.c`` holds the arithmetic; this module only compiles it (gcc,
+OpenMP) and marshals numpy arrays through ctypes.
+
+Passages followed: Eq. 1 (Sec. 3.1, alpha compositing), Sec. 3.1 (2D
+Gaussian surfels, L1 + D-SSIM), Sec. 3.2 (depth loss on inverse depth,
+elongation rate eta, Eq. 2 decomposed-gradient densification, antialiasing
+low-pass filter), Sec. 4.1 (median depth), of CityGaussianV2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs2d_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libgs2d_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# plane order of a render and of an adjoint set
+PLANES = ["r", "g", "b", "alpha", "depth", "invdepth", "median", "nx", "ny", "nz",
+          "distortion", "T_final"]
+OUT_PLANES = 12
+ADJ_PLANES = 11
+FLAG_ALPHA, FLAG_RHO, FLAG_TSTOP, FLAG_MEDIAN, FLAG_BRANCH = 1, 2, 4, 8, 16
+
+DEFAULT_SETTINGS = dict(near=0.2, alpha_min=1.0 / 255.0, T_min=1e-4, alpha_max=0.99,
+                        rho_max=9.0, screen_inv_sigma2=2.0, bg=(0.0, 0.0, 0.0), tile=16)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (-O2, OpenMP)."""
+    with _lock:
+        os.makedirs(_BUILD, exist_ok=True)
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = build()
+        lib = ctypes.CDLL(path)
+        lib.oracle_ssim_sum.restype = ctypes.c_double
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def cam_array(cam: dict) -> np.ndarray:
+    c = np.zeros(18, np.float64)
+    c[0:9] = np.asarray(cam["R"], np.float64).reshape(9)
+    c[9:12] = np.asarray(cam["t"], np.float64).reshape(3)
+    c[12], c[13], c[14], c[15] = cam["fx"], cam["fy"], cam["cx"], cam["cy"]
+    c[16], c[17] = cam["width"], cam["height"]
+    return c
+
+
+def settings_array(settings: dict | None = None) -> np.ndarray:
+    s = dict(DEFAULT_SETTINGS)
+    if settings:
+        s.update(settings)
+    a = np.zeros(10, np.float64)
+    a[0], a[1], a[2], a[3] = s["near"], s["alpha_min"], s["T_min"], s["alpha_max"]
+    a[4], a[5] = s["rho_max"], s["screen_inv_sigma2"]
+    a[6:9] = s["bg"]
+    a[9] = s["tile"]
+    return a
+
+
+def _scene_args(scene):
+    # FP32 inputs widen exactly; float64 inputs (finite differences) pass as is
+    mu = np.ascontiguousarray(scene["mu"], np.float64)
+    quat = np.ascontiguousarray(scene["quat"], np.float64)
+    scale = np.ascontiguousarray(scene["scale"], np.float64)
+    opac = np.ascontiguousarray(scene["opacity"], np.float64)
+    sh = np.ascontiguousarray(scene["sh"], np.float64)
+    n = mu.shape[0]
+    deg = int(scene["sh_degree"])
+    assert sh.size == n * (deg + 1) ** 2 * 3
+    return n, deg, (mu, quat, scale, opac, sh)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def sh_basis(dirs: np.ndarray) -> np.ndarray:
+    d = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
+    Y = np.zeros((d.shape[0], 16), np.float64)
+    _load().oracle_sh_basis(ctypes.c_int(d.shape[0]), _p(d), _p(Y))
+    return Y
+
+
+def preprocess(scene, cam, settings=None):
+    lib = _load()
+    n, deg, arrs = _scene_args(scene)
+    c, s = cam_array(cam), settings_array(settings)
+    out = dict(M=np.zeros((n, 9)), rgb=np.zeros((n, 3)), normal=np.zeros((n, 3)),
+               zkey=np.zeros(n), bbox=np.zeros((n, 4)), rect=np.zeros((n, 4), np.int32),
+               live=np.zeros(n, np.int32), cond=np.zeros(n))
+    lib.oracle_preprocess(ctypes.c_int64(n), ctypes.c_int(deg), *[_p(a) for a in arrs], _p(c), _p(s),
+                          _p(out["M"]), _p(out["rgb"]), _p(out["normal"]), _p(out["zkey"]),
+                          _p(out["bbox"]), _p(out["rect"]), _p(out["live"]), _p(out["cond"]))
+    r = out["rect"]
+    out["tiles"] = np.where(out["live"] > 0, (r[:, 2] - r[:, 0]) * (r[:, 3] - r[:, 1]), 0)
+    return out
+
+
+def render(scene, cam, settings=None, mode: str = "binned", pixels=None, shift=None):
+    """Render every pixel (or the flat pixel indices in ``pixels``).
+
+    Returns dict(out=[12, H, W] or [12, P], count, flags, dexact, ncand)."""
+    lib = _load()
+    n, deg, arrs = _scene_args(scene)
+    c, s = cam_array(cam), settings_array(settings)
+    W, H = int(cam["width"]), int(cam["height"])
+    if pixels is None:
+        P, pix, shape = W * H, None, (H, W)
+    else:
+        pix = np.ascontiguousarray(pixels, np.int64)
+        P, shape = pix.size, (pix.size,)
+    out = np.zeros((OUT_PLANES, P))
+    count = np.zeros(P, np.int32)
+    flags = np.zeros(P, np.int32)
+    dexact = np.zeros(P)
+    ncand = np.zeros(P, np.int32)
+    sh = None if shift is None else np.ascontiguousarray(shift, np.float64).reshape(n, 2)
+    lib.oracle_render(ctypes.c_int64(n), ctypes.c_int(deg), *[_p(a) for a in arrs], _p(c), _p(s),
+                      ctypes.c_int(0 if mode == "brute" else 1), ctypes.c_int64(P), _p(pix),
+                      _p(sh), _p(out), _p(count), _p(flags), _p(dexact), _p(ncand))
+    return dict(out=out.reshape((OUT_PLANES,) + shape), count=count.reshape(shape),
+                flags=flags.reshape(shape), dexact=dexact.reshape(shape),
+                ncand=ncand.reshape(shape))
+
+
+def pixel_cond(scene, cam, settings=None):
+    """Largest centred-Jacobian condition number of an object-branch pair
+    blended at each pixel (0 if none)."""
+    lib = _load()
+    n, deg, arrs = _scene_args(scene)
+    c, s = cam_array(cam), settings_array(settings)
+    W, H = int(cam["width"]), int(cam["height"])
+    mc = np.zeros(W * H)
+    lib.oracle_pixel_cond(ctypes.c_int64(n), ctypes.c_int(deg), *[_p(a) for a in arrs], _p(c),
+                          _p(s), _p(mc))
+    return mc.reshape(H, W)
+
+
+def backward(scene, cam, adj_sets, settings=None):
+    """Gradients of set 0's loss w.r.t. (mu, quat, scale, opacity, sh) and the
+    screen-translation gradients of every set.  adj_sets: [S, 11, H, W]."""
+    lib = _load()
+    n, deg, arrs = _scene_args(scene)
+    c, s = cam_array(cam), settings_array(settings)
+    adj = np.ascontiguousarray(adj_sets, np.float64)
+    S = adj.shape[0]
+    K = (deg + 1) ** 2
+    g = dict(mu=np.zeros((n, 3)), quat=np.zeros((n, 4)), scale=np.zeros((n, 2)),
+             opacity=np.zeros(n), sh=np.zeros((n, K, 3)), screen=np.zeros((S, n, 2)),
+             inter=np.zeros((n, 16)))
+    lib.oracle_backward(ctypes.c_int64(n), ctypes.c_int(deg), *[_p(a) for a in arrs], _p(c),
+                        _p(s), ctypes.c_int(S), _p(adj), _p(g["mu"]), _p(g["quat"]),
+                        _p(g["scale"]), _p(g["opacity"]), _p(g["sh"]), _p(g["screen"]),
+                        _p(g["inter"]))
+    return g
+
+
+def loss(out, target_rgb, target_invdepth=None, weights=(0.8, 0.2, 0.0)):
+    """L1, SSIM, depth loss, total; adjoint sets (total, SSIM term, L1 term),
+    each [11, H, W]."""
+    lib = _load()
+    out = np.ascontiguousarray(out, np.float64)
+    H, W = out.shape[-2:]
+    tgt = np.ascontiguousarray(target_rgb, np.float64)
+    tinv = None if target_invdepth is None else np.ascontiguousarray(target_invdepth, np.float64)
+    w = np.asarray(weights, np.float64)
+    losses = np.zeros(4)
+    adj = np.zeros((3, ADJ_PLANES, H, W))
+    lib.oracle_loss(ctypes.c_int(W), ctypes.c_int(H), _p(out), _p(tgt), _p(tinv), _p(w),
+                    _p(losses), _p(adj[0]), _p(adj[1]), _p(adj[2]))
+    return dict(l1=losses[0], ssim=losses[1], depth=losses[2], total=losses[3], adj=adj)
+
+
+def ssim_sum(x, y, want_grad=True):
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    H, W = x.shape
+    g = np.zeros_like(x) if want_grad else None
+    v = lib.oracle_ssim_sum(ctypes.c_int(W), ctypes.c_int(H), _p(x), _p(y), _p(g))
+    return v, g
+
+
+def densify_accumulate(screen, visible, stats=None):
+    lib = _load()
+    scr = np.ascontiguousarray(screen, np.float64)
+    n = scr.shape[1]
+    vis = np.ascontiguousarray(visible, np.int32)
+    st = np.zeros((n, 4)) if stats is None else np.ascontiguousarray(stats, np.float64).copy()
+    lib.oracle_densify_accumulate(ctypes.c_int64(n), _p(scr), _p(vis), _p(st))
+    return st
+
+
+def densify_select(stats, scale, omega=0.9, grad_thr=0.0002, eta_thr=0.1):
+    lib = _load()
+    st = np.ascontiguousarray(stats, np.float64)
+    n = st.shape[0]
+    sc = np.ascontiguousarray(scale, np.float64)
+    mask = np.zeros(n, np.uint8)
+    g = np.zeros(n)
+    k = np.zeros(1)
+    lib.oracle_densify_select(ctypes.c_int64(n), _p(st), _p(sc), ctypes.c_double(omega),
+                              ctypes.c_double(grad_thr), ctypes.c_double(eta_thr), _p(mask), _p(g),
+                              _p(k))
+    return mask, g, float(k[0])
+
+
+def elongation(scale, eta_thr=0.1):
+    lib = _load()
+    sc = np.ascontiguousarray(scale, np.float64)
+    keep = np.zeros(sc.shape[0], np.uint8)
+    lib.oracle_elongation(ctypes.c_int64(sc.shape[0]), _p(sc), ctypes.c_double(eta_thr), _p(keep))
+    return keep

@@ -1,0 +1,463 @@
+"""Pins of the FP64 oracle to things other than itself: closed forms,
+library routines, brute force and invariants (CPU only).
+
+Each test names the passage of CityGaussianV2 (arXiv 2411.00771) or of the
+definition it checks, and is built so that a plausible slip in the oracle (a
+dropped term, a wrong sign or index, a transposed operand) fails one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.ndimage import correlate
+from scipy.spatial.transform import Rotation
+from scipy.special import sph_harm_y
+
+import oracle
+from paper_2411_00771_gb300 import synthetic as syn
+from tests.scenes import camera, make_scene, pixel_grid
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+ALPHA_MIN = 1.0 / 255.0
+
+
+def _render(scene, cam, **kw):
+    return oracle.render(scene, cam, **kw)
+
+
+# --------------------------------------------------------------------------
+# Geometry: ray-splat intersection and the low-pass max (Sec. 3.1 surfel
+# model; Sec. 3.2 antialiasing filter)
+
+def test_fronto_parallel_single_splat_closed_form():
+    """A disk facing the camera on the optical axis: rho_obj = |d|^2 z0^2 /
+    (f^2 s^2) per axis, rho_scr = 2 |d|^2, alpha = o exp(-min/2)."""
+    cam = camera(64, 64, 64.0)
+    z0, su, sv, o = 3.0, 0.21, 0.13, 0.8
+    sc = make_scene([dict(mu=(0, 0, z0), scale=(su, sv), opacity=o, rgb=(0.9, 0.4, 0.1))])
+    r = _render(sc, cam)
+    x, y = pixel_grid(cam)
+    dx, dy = x - 32.0, y - 32.0
+    rho_obj = (dx * z0 / (64.0 * su)) ** 2 + (dy * z0 / (64.0 * sv)) ** 2
+    rho_scr = 2.0 * (dx * dx + dy * dy)
+    rho = np.minimum(rho_obj, rho_scr)
+    alpha = np.minimum(0.99, o * np.exp(-0.5 * rho))
+    blended = (rho <= 9.0) & (alpha >= ALPHA_MIN)
+    exp_alpha = np.where(blended, alpha, 0.0)
+    assert np.abs(r["out"][3] - exp_alpha).max() < 1e-12
+    assert np.array_equal(r["count"], blended.astype(np.int32))
+    # colour = alpha * rgb, depth = alpha * z0, normal faces the camera
+    assert np.abs(r["out"][0] - 0.9 * exp_alpha).max() < 1e-12
+    assert np.abs(r["out"][2] - 0.1 * exp_alpha).max() < 1e-12
+    assert np.abs(r["out"][4] - z0 * exp_alpha).max() < 1e-12
+    assert np.abs(r["out"][5] - exp_alpha / z0).max() < 1e-12
+    assert np.abs(r["out"][9] + exp_alpha).max() < 1e-12
+    assert np.abs(r["out"][11] - (1 - exp_alpha)).max() < 1e-12
+    assert np.abs(r["out"][6] - np.where(blended, z0, 0.0)).max() < 1e-12
+
+
+def _independent_rho(mu, quat_wxyz, scale, cam, x, y):
+    """Ray-plane intersection written independently: t = (n.mu)/(n.r)."""
+    R = Rotation.from_quat([quat_wxyz[1], quat_wxyz[2], quat_wxyz[3], quat_wxyz[0]]).as_matrix()
+    tu, tv, n = R[:, 0], R[:, 1], R[:, 2]
+    r = np.stack([(x - cam["cx"]) / cam["fx"], (y - cam["cy"]) / cam["fy"], np.ones_like(x)], -1)
+    t = (n @ mu) / (r @ n)
+    P = t[..., None] * r
+    u = ((P - mu) @ tu) / scale[0]
+    v = ((P - mu) @ tv) / scale[1]
+    return u * u + v * v, t
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tilted_splat_matches_ray_plane_intersection(seed):
+    rng = np.random.default_rng(100 + seed)
+    cam = camera(48, 40, 50.0, cx=23.3, cy=19.1)
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    mu = np.array([rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2), rng.uniform(2.5, 3.5)])
+    scale = np.array([rng.uniform(0.1, 0.3), rng.uniform(0.1, 0.3)])
+    o = 0.7
+    sc = make_scene([dict(mu=mu, quat=q, scale=scale, opacity=o)])
+    r = _render(sc, cam)
+    x, y = pixel_grid(cam)
+    rho_obj, zobj = _independent_rho(mu, q, scale, cam, x, y)
+    c = np.array([cam["fx"] * mu[0] / mu[2] + cam["cx"], cam["fy"] * mu[1] / mu[2] + cam["cy"]])
+    rho_scr = 2 * ((x - c[0]) ** 2 + (y - c[1]) ** 2)
+    rho = np.minimum(rho_obj, rho_scr)
+    z = np.where(rho_obj <= rho_scr, zobj, mu[2])
+    alpha = o * np.exp(-0.5 * rho)
+    blended = (rho <= 9) & (alpha >= ALPHA_MIN)
+    assert blended.sum() > 20
+    assert np.abs(r["out"][3] - np.where(blended, alpha, 0)).max() < 1e-10
+    assert np.abs(r["out"][4] - np.where(blended, alpha * z, 0)).max() < 1e-9
+
+
+def test_subpixel_splat_is_screen_filter():
+    """s -> 0: only the screen-space filter remains, G = exp(-|x - c|^2)."""
+    cam = camera(32, 32, 40.0)
+    mu = np.array([0.013, -0.021, 3.0])
+    sc = make_scene([dict(mu=mu, scale=(1e-6, 1e-6), opacity=0.9,
+                          quat=(0.9, 0.3, -0.2, 0.1))])
+    r = _render(sc, cam)
+    x, y = pixel_grid(cam)
+    c = (40 * mu[0] / mu[2] + 16, 40 * mu[1] / mu[2] + 16)
+    d2 = (x - c[0]) ** 2 + (y - c[1]) ** 2
+    alpha = 0.9 * np.exp(-d2)
+    blended = (2 * d2 <= 9) & (alpha >= ALPHA_MIN)
+    assert np.abs(r["out"][3] - np.where(blended, alpha, 0)).max() < 1e-12
+    # depth is the centre depth when the screen filter wins
+    assert np.abs(r["out"][4] - np.where(blended, alpha * 3.0, 0)).max() < 1e-12
+
+
+def test_near_plane_cull():
+    """A disk whose 3-sigma extent reaches the near plane (0.2) is culled."""
+    cam = camera(32, 32, 32.0)
+    q = Rotation.from_euler("x", 60, degrees=True).as_quat()  # x y z w
+    quat = (q[3], q[0], q[1], q[2])
+    ok = make_scene([dict(mu=(0, 0, 1.0), quat=quat, scale=(0.1, 0.2), opacity=0.9)])
+    bad = make_scene([dict(mu=(0, 0, 1.0), quat=quat, scale=(0.1, 0.4), opacity=0.9)])
+    # min depth of the 3-sigma disk = z - 3 * |(s_u t_u.z, s_v t_v.z)|
+    tvz = Rotation.from_quat(q).as_matrix()[2, 1]
+    assert 1.0 - 3 * abs(0.2 * tvz) > 0.2 and 1.0 - 3 * abs(0.4 * tvz) < 0.2
+    assert oracle.preprocess(ok, cam)["live"][0] == 1
+    assert oracle.preprocess(bad, cam)["live"][0] == 0
+    assert _render(bad, cam)["count"].sum() == 0
+
+
+# --------------------------------------------------------------------------
+# Compositing (Eq. 1) and the rendered auxiliaries
+
+def _two_splats(z1, z2, o1, o2):
+    big = (5.0, 5.0)
+    return make_scene([dict(mu=(0, 0, z1), scale=big, opacity=o1, rgb=(1, 0, 0)),
+                       dict(mu=(0, 0, z2), scale=big, opacity=o2, rgb=(0, 0, 1))])
+
+
+def test_two_splats_closed_form_and_order():
+    cam = camera(16, 16, 16.0)
+    z1, z2, o1, o2 = 2.0, 3.0, 0.3, 0.6
+    r = _render(_two_splats(z1, z2, o1, o2), cam)
+    # centre pixel: rho is tiny but not zero; read the exact alphas back
+    x, y = 8.5, 8.5
+    d2 = (x - 8) ** 2 + (y - 8) ** 2
+    a1 = o1 * math.exp(-0.5 * d2 * (z1 / (16 * 5.0)) ** 2)
+    a2 = o2 * math.exp(-0.5 * d2 * (z2 / (16 * 5.0)) ** 2)
+    w1, w2 = a1, a2 * (1 - a1)
+    p = (8, 8)
+    out = r["out"][:, p[0], p[1]]
+    assert abs(out[0] - w1) < 1e-14 and abs(out[2] - w2) < 1e-14
+    assert abs(out[11] - (1 - a1) * (1 - a2)) < 1e-14
+    assert abs(out[4] - (w1 * z1 + w2 * z2)) < 1e-13
+    assert abs(out[10] - 2 * w1 * w2 * abs(z1 - z2)) < 1e-13
+    assert abs(r["dexact"][p] - 2 * w1 * w2 * abs(z1 - z2)) < 1e-13
+    # both entered with T > 0.5 (1 and 1 - a1 = 0.7): median is the second
+    assert out[6] == z2
+    # swapping the depths swaps the order
+    r2 = _render(_two_splats(z2, z1, o1, o2), cam)
+    o2_ = r2["out"][:, p[0], p[1]]
+    b2 = o2 * math.exp(-0.5 * d2 * (z1 / 80.0) ** 2)
+    b1 = o1 * math.exp(-0.5 * d2 * (z2 / 80.0) ** 2)
+    assert abs(o2_[2] - b2) < 1e-14 and abs(o2_[0] - b1 * (1 - b2)) < 1e-14
+
+
+def test_median_pivot():
+    cam = camera(16, 16, 16.0)
+    r = _render(_two_splats(2.0, 3.0, 0.6, 0.6), cam)
+    assert r["out"][6, 8, 8] == 2.0  # second pair entered with T = 0.4 < 0.5
+
+
+def test_transmittance_stop_and_alpha_clamp():
+    cam = camera(16, 16, 16.0)
+    big = (50.0, 50.0)
+    sc = make_scene([dict(mu=(0, 0, 2.0 + 0.1 * k), scale=big, opacity=0.8) for k in range(10)])
+    r = _render(sc, cam)
+    # alpha ~ 0.8 everywhere: T = 0.2^k, stop before T(1-a) < 1e-4 -> 5 pairs
+    assert np.all(r["count"] == 5)
+    assert np.all(r["out"][11] >= 1e-4)
+    sc1 = make_scene([dict(mu=(0, 0, 2.0), scale=big, opacity=1.0)])
+    r1 = _render(sc1, cam)
+    assert np.all(np.abs(r1["out"][3] - 0.99) < 1e-12)
+
+
+def test_alpha_cutoff():
+    cam = camera(16, 16, 16.0)
+    sc = make_scene([dict(mu=(0, 0, 2.0), scale=(50.0, 50.0), opacity=0.999 * ALPHA_MIN)])
+    r = _render(sc, cam)
+    assert r["count"].sum() == 0
+    assert r["out"][11].min() == 1.0 and np.abs(r["out"][:11]).max() == 0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_brute_force_equals_binned(seed):
+    """Binning by the 3-sigma cover loses no pair: every pixel equals the
+    brute-force loop over all surfels, bit for bit."""
+    scene, cam, _, _ = syn.tiny_scene(seed=seed, n=200, width=32, height=32, fx=32.0,
+                                      log_scale_range=(-4.0, -1.0), sh_degree=1,
+                                      z_range=(0.5, 4.0))
+    rb = _render(scene, cam, mode="brute")
+    rt = _render(scene, cam, mode="binned")
+    assert np.array_equal(rb["out"], rt["out"])
+    assert np.array_equal(rb["count"], rt["count"])
+
+
+def test_invariants_on_random_scene():
+    scene, cam, _, _ = syn.tiny_scene()
+    r = _render(scene, cam)
+    out = r["out"]
+    assert np.all(out[11] >= 1e-4) and np.all(out[11] <= 1.0)
+    assert np.abs(out[3] + out[11] - 1.0).max() < 1e-12
+    assert np.all(r["count"] <= r["ncand"]) and np.all(r["count"] >= 0)
+    assert np.all(out[3] <= 1.0 + 1e-12)
+
+
+def test_transparent_scene_gives_background():
+    scene, cam, _, _ = syn.tiny_scene(n=300)
+    scene = dict(scene)
+    scene["opacity"] = np.zeros_like(scene["opacity"])
+    r = oracle.render(scene, cam, settings=dict(bg=(0.25, 0.5, 0.75)))
+    assert r["count"].sum() == 0
+    for c, v in enumerate((0.25, 0.5, 0.75)):
+        assert np.all(r["out"][c] == v)
+
+
+def test_permutation_invariance_of_disjoint_splats():
+    """Surfels whose footprints do not overlap: any index order renders the
+    same image bit for bit."""
+    cam = camera(64, 64, 64.0)
+    rng = np.random.default_rng(3)
+    surf = []
+    for gx in range(4):
+        for gy in range(4):
+            surf.append(dict(mu=((gx - 1.5) * 0.8, (gy - 1.5) * 0.8, 3.0 + rng.uniform(0, 0.5)),
+                             scale=(0.05, 0.07), opacity=rng.uniform(0.3, 0.9),
+                             rgb=rng.uniform(0, 1, 3)))
+    a = _render(make_scene(surf), cam)
+    perm = rng.permutation(len(surf))
+    b = _render(make_scene([surf[i] for i in perm]), cam)
+    assert np.array_equal(a["out"], b["out"])
+
+
+def test_distortion_one_pass_equals_pairwise_sum_when_depths_ordered():
+    cam = camera(32, 32, 32.0)
+    rng = np.random.default_rng(9)
+    surf = [dict(mu=(rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3), 2 + 0.2 * k),
+                 scale=(0.3, 0.3), opacity=0.5) for k in range(8)]
+    r = _render(make_scene(surf), cam)
+    assert np.abs(r["out"][10] - r["dexact"]).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Spherical harmonics (colour, Sec. 3.1)
+
+def test_sh_orthonormal_by_quadrature():
+    xg, wg = np.polynomial.legendre.leggauss(24)  # cos(theta)
+    nphi = 48
+    phi = (np.arange(nphi) + 0.5) * 2 * np.pi / nphi
+    ct, ph = np.meshgrid(xg, phi, indexing="ij")
+    st = np.sqrt(1 - ct ** 2)
+    dirs = np.stack([st * np.cos(ph), st * np.sin(ph), ct], -1).reshape(-1, 3)
+    w = (wg[:, None] * np.full(nphi, 2 * np.pi / nphi)[None, :]).reshape(-1)
+    Y = oracle.sh_basis(dirs)
+    G = (Y * w[:, None]).T @ Y
+    assert np.abs(G - np.eye(16)).max() < 1e-12
+
+
+def test_sh_matches_complex_basis_with_condon_shortley_phase():
+    rng = np.random.default_rng(0)
+    d = rng.normal(size=(50, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    theta = np.arccos(d[:, 2])
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    Y = oracle.sh_basis(d)
+    for l in range(4):
+        for m in range(-l, l + 1):
+            c = sph_harm_y(l, abs(m), theta, phi)
+            if m > 0:
+                ref = math.sqrt(2) * c.real
+            elif m < 0:
+                ref = math.sqrt(2) * c.imag
+            else:
+                ref = c.real
+            assert np.abs(Y[:, l * l + l + m] - ref).max() < 1e-12, (l, m)
+
+
+def test_view_dependent_colour_of_degree_one_splat():
+    cam = camera(32, 32, 32.0)
+    cam["t"] = np.array([0.1, -0.2, 0.3])  # camera centre = -t
+    sh = np.zeros((4, 3))
+    sh[0] = [0.3, -0.2, 0.1]
+    sh[1:] = [[0.2, 0.1, -0.3], [0.05, 0.4, 0.2], [-0.25, 0.3, 0.15]]
+    mu = np.array([0.05, 0.02, 3.0])
+    sc = make_scene([dict(mu=mu, scale=(5.0, 5.0), opacity=0.5, sh=sh)], sh_degree=1)
+    pre = oracle.preprocess(sc, cam)
+    d = mu - (-cam["t"])
+    d /= np.linalg.norm(d)
+    theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+    Y = [sph_harm_y(0, 0, theta, phi).real,
+         math.sqrt(2) * sph_harm_y(1, 1, theta, phi).imag,
+         sph_harm_y(1, 0, theta, phi).real,
+         math.sqrt(2) * sph_harm_y(1, 1, theta, phi).real]
+    rgb = np.maximum(0, np.array(Y) @ sh + 0.5)
+    assert np.abs(pre["rgb"][0] - rgb).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Losses (Sec. 3.1 L1 + D-SSIM; Sec. 3.2 depth loss on inverse depth)
+
+def _ssim_scipy(x, y):
+    g = np.exp(-((np.arange(11) - 5) ** 2) / (2 * 1.5 ** 2))
+    g /= g.sum()
+    k = np.outer(g, g)
+    f = lambda a: correlate(a, k, mode="constant", cval=0.0)
+    mx, my = f(x), f(y)
+    vx, vy, cxy = f(x * x) - mx * mx, f(y * y) - my * my, f(x * y) - mx * my
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    return (((2 * mx * my + C1) * (2 * cxy + C2)) / ((mx ** 2 + my ** 2 + C1) * (vx + vy + C2))).sum()
+
+
+def test_ssim_matches_scipy_and_identity():
+    rng = np.random.default_rng(0)
+    x = rng.uniform(0, 1, (23, 31)); y = rng.uniform(0, 1, (23, 31))
+    v, g = oracle.ssim_sum(x, y)
+    assert abs(v - _ssim_scipy(x, y)) < 1e-10
+    v1, g1 = oracle.ssim_sum(x, x)
+    assert abs(v1 - x.size) < 1e-9 and np.abs(g1).max() < 1e-9
+
+
+def test_ssim_gradient_finite_difference():
+    rng = np.random.default_rng(1)
+    x = rng.uniform(0, 1, (17, 19)); y = rng.uniform(0, 1, (17, 19))
+    _, g = oracle.ssim_sum(x, y)
+    for (i, j) in [(0, 0), (3, 4), (8, 9), (16, 18), (10, 0)]:
+        h = 1e-6
+        xp = x.copy(); xp[i, j] += h
+        xm = x.copy(); xm[i, j] -= h
+        fd = (oracle.ssim_sum(xp, y, False)[0] - oracle.ssim_sum(xm, y, False)[0]) / (2 * h)
+        assert abs(fd - g[i, j]) < 1e-7
+
+
+def test_loss_closed_forms_and_decomposition():
+    H, W = 12, 14
+    out = np.zeros((12, H, W))
+    out[0:3] = 0.6
+    out[5] = 0.3
+    tgt = np.full((3, H, W), 0.5)
+    tinv = np.full((H, W), 0.2)
+    L = oracle.loss(out, tgt, tinv, (0.8, 0.2, 0.5))
+    assert abs(L["l1"] - 0.1) < 1e-15 and abs(L["depth"] - 0.1) < 1e-15
+    assert abs(L["total"] - (0.8 * 0.1 + 0.2 * (1 - L["ssim"]) + 0.5 * 0.1)) < 1e-15
+    adj = L["adj"]
+    assert np.allclose(adj[2][0:3], 0.8 / (3 * H * W))
+    assert np.allclose(adj[0][0:3], adj[1][0:3] + adj[2][0:3], rtol=0, atol=1e-18)
+    assert np.allclose(adj[0][5], 0.5 / (H * W)) and np.all(adj[1][5] == 0)
+
+
+# --------------------------------------------------------------------------
+# Gradients: central finite differences in FP64
+
+def _fd_scene(seed, deg):
+    scene, cam, tgt, tinv = syn.tiny_scene(seed=seed, n=60, width=32, height=32, fx=32.0,
+                                           sh_degree=deg, xy_range=0.8,
+                                           log_scale_range=(-2.5, -1.5))
+    for k in ("mu", "quat", "scale", "opacity", "sh"):
+        scene[k] = scene[k].astype(np.float64)
+    return scene, cam, tgt, tinv
+
+
+def _fd_check(scene, f, grads, rng, n_per=10, tol=1e-6):
+    for key in ("mu", "quat", "scale", "opacity", "sh"):
+        flat = scene[key].reshape(-1)
+        for i in rng.choice(flat.size, n_per, replace=False):
+            h = 1e-6 * max(1.0, abs(flat[i]))
+            sp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in scene.items()}
+            sp[key].reshape(-1)[i] += h
+            lp = f(sp)
+            sp[key].reshape(-1)[i] -= 2 * h
+            lm = f(sp)
+            fd = (lp - lm) / (2 * h)
+            an = grads[key].reshape(-1)[i]
+            assert abs(fd - an) <= tol * max(1.0, abs(fd)), (key, i, fd, an)
+
+
+def test_gradients_of_training_loss_by_finite_differences():
+    scene, cam, tgt, tinv = _fd_scene(5, 3)
+    w = (0.8, 0.2, 0.5)
+    L = oracle.loss(_render(scene, cam)["out"], tgt, tinv, w)
+    g = oracle.backward(scene, cam, L["adj"][:1])
+    f = lambda sc: oracle.loss(_render(sc, cam)["out"], tgt, tinv, w)["total"]
+    _fd_check(scene, f, g, np.random.default_rng(0))
+
+
+def test_gradients_of_every_output_plane_by_finite_differences():
+    """A random linear functional of all 11 differentiable planes (colour,
+    alpha, depth, inverse depth, median, normal, distortion)."""
+    scene, cam, _, _ = _fd_scene(7, 2)
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(1, 11, 32, 32))
+    g = oracle.backward(scene, cam, A)
+    f = lambda sc, shift=None: float((A[0] * oracle.render(sc, cam, shift=shift)["out"][:11]).sum())
+    _fd_check(scene, f, g, rng, tol=1e-6)
+    # screen-space translation gradient (densification statistic)
+    n = scene["mu"].shape[0]
+    for i in rng.choice(n, 15, replace=False):
+        for ax in range(2):
+            h = 1e-6
+            s = np.zeros((n, 2)); s[i, ax] = h
+            lp = f(scene, s)
+            s[i, ax] = -h
+            lm = f(scene, s)
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g["screen"][0, i, ax]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_screen_gradient_sets_follow_their_adjoints():
+    """Set k's screen gradient is linear in set k's adjoint: the SSIM-term and
+    L1-term sets add up to the colour part of the total set."""
+    scene, cam, tgt, tinv = _fd_scene(11, 0)
+    L = oracle.loss(_render(scene, cam)["out"], tgt, None, (0.8, 0.2, 0.0))
+    g = oracle.backward(scene, cam, L["adj"])
+    s = g["screen"]
+    assert np.abs(s[0] - (s[1] + s[2])).max() < 1e-14
+    assert np.abs(s[0]).max() > 0
+
+
+# --------------------------------------------------------------------------
+# Densification (Sec. 3.2 Eq. 2) and the elongation filter (Sec. 3.2)
+
+def test_dgd_scaling_closed_forms():
+    paper = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
+    omega = paper["omega"]["value"]
+    # S_tot, S_ssim, S_l1, cnt
+    st = np.array([[4.0, 1.0, 3.0, 2.0], [2.0, 1.0, 1.0, 1.0], [9.0, 9.0, 0.0, 0.0]])
+    sc = np.ones((3, 2))
+    mask, g, k = oracle.densify_select(st, sc, omega=omega, grad_thr=0.0, eta_thr=0.0)
+    avg_tot = (2.0 + 2.0) / 2
+    avg_ssim = (0.5 + 1.0) / 2
+    assert abs(k - max(omega * avg_tot / avg_ssim, 1.0)) < 1e-15
+    assert abs(g[0] - k * 0.5) < 1e-15 and abs(g[1] - k * 1.0) < 1e-15 and g[2] == 0
+    assert list(mask) == [1, 1, 0]
+    # omega * ratio < 1: the SSIM gradient is used unscaled
+    st2 = np.array([[1.0, 2.0, 0.0, 1.0]])
+    _, g2, k2 = oracle.densify_select(st2, np.ones((1, 2)), omega=omega)
+    assert k2 == 1.0 and g2[0] == 2.0
+
+
+def test_elongation_rate_threshold():
+    eps = 1e-6
+    sc = np.array([[1.0, 1.0], [0.1 + eps, 1.0], [1.0, 0.1 - eps], [2.0, 0.5]])
+    keep = oracle.elongation(sc, eta_thr=0.1)
+    assert list(keep) == [1, 1, 0, 1]
+    st = np.tile([1.0, 1.0, 1.0, 1.0], (4, 1))
+    mask, _, _ = oracle.densify_select(st, sc, grad_thr=0.5, eta_thr=0.1)
+    assert list(mask) == [1, 1, 0, 1]
+
+
+def test_densify_accumulate_counts_visible_views():
+    scr = np.zeros((3, 3, 2))
+    scr[0, 0] = (3, 4); scr[1, 0] = (0, 1); scr[2, 0] = (6, 8)
+    st = oracle.densify_accumulate(scr, np.array([1, 0, 1]))
+    st = oracle.densify_accumulate(scr, np.array([1, 0, 1]), st)
+    assert np.allclose(st[0], [10.0, 2.0, 20.0, 2.0]) and np.all(st[1] == 0)
+    assert np.allclose(st[2], [0, 0, 0, 2.0])
