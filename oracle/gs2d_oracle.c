@@ -49,7 +49,10 @@ enum { O_R = 0, O_G = 1, O_B = 2, O_ALPHA = 3, O_DEPTH = 4, O_INVDEPTH = 5,
        O_MEDIAN = 6, O_NX = 7, O_NY = 8, O_NZ = 9, O_DIST = 10, O_TFINAL = 11,
        OUT_PLANES = 12, ADJ_PLANES = 11 };
 
-/* per-pixel flags: a decision taken within a hair of a threshold */
+/* per-pixel flags: a decision taken within a hair of a threshold.  The
+ * margins (relative 1e-5 for alpha, the transmittance stop and the median
+ * pivot; 1e-4 absolute on rho) exceed the FP32 error of those quantities
+ * after tens of compositing steps (a few 1e-7 relative). */
 enum { F_ALPHA = 1, F_RHO = 2, F_TSTOP = 4, F_MEDIAN = 8, F_BRANCH = 16 };
 
 typedef struct {
@@ -358,7 +361,7 @@ static int composite_pixel(const pre_t* pre, const int* cand, int ncand, double 
       continue;
     }
     if (fabs(pr.rho - set[SET_RHO_MAX]) < 1e-4) px->flags |= F_RHO;
-    if (fabs(pr.alpha / set[SET_ALPHA_MIN] - 1.0) < 1e-4) px->flags |= F_ALPHA;
+    if (fabs(pr.alpha / set[SET_ALPHA_MIN] - 1.0) < 1e-5) px->flags |= F_ALPHA;
     if (!(pr.alpha >= set[SET_ALPHA_MIN])) continue;
     tmp[m] = pr;
     keys[m].z = pre[n].zkey; keys[m].n = n; keys[m].slot = m;
@@ -371,7 +374,7 @@ static int composite_pixel(const pre_t* pre, const int* cand, int ncand, double 
   for (int k = 0; k < m; ++k) {
     pair_t pr = tmp[keys[k].slot];
     const double Tn = T * (1.0 - pr.alpha);
-    if (fabs(Tn / set[SET_T_MIN] - 1.0) < 1e-3) px->flags |= F_TSTOP;
+    if (fabs(Tn / set[SET_T_MIN] - 1.0) < 1e-5) px->flags |= F_TSTOP;
     if (Tn < set[SET_T_MIN]) break;
     const double w = pr.alpha * T;
     pr.T = T; pr.w = w;
@@ -382,7 +385,7 @@ static int composite_pixel(const pre_t* pre, const int* cand, int ncand, double 
     Z += w * pr.z;
     px->out[O_INVDEPTH] += w / pr.z;
     for (int c = 0; c < 3; ++c) px->out[O_NX + c] += w * P->nrm[c];
-    if (fabs(T / 0.5 - 1.0) < 1e-3) px->flags |= F_MEDIAN;
+    if (fabs(T / 0.5 - 1.0) < 1e-5) px->flags |= F_MEDIAN;
     if (T > 0.5) px->out[O_MEDIAN] = pr.z;
     if (pr.obj && fabs(pr.rho_obj - pr.rho_scr) < 1e-5 * (1 + pr.rho_scr)) px->flags |= F_BRANCH;
     blended[nb++] = pr;
@@ -919,7 +922,7 @@ int oracle_loss(int W, int H, const double* out, const double* tgt, const double
   free(ds);
   l1 /= 3.0 * n;
   ss /= 3.0 * n;
-  if (tinv && w[2] != 0) {
+  if (tinv) {
     for (int64_t k = 0; k < n; ++k) {
       const double d = out[O_INVDEPTH * n + k] - tinv[k];
       ld += fabs(d);
