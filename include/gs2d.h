@@ -1,0 +1,264 @@
+/*
+ * gs2d.h -- C ABI of the GB300 (sm_103a) 2D Gaussian (surfel) splatting
+ * rasterizer: the hot path of CityGaussianV2 (arXiv 2411.00771).
+ *
+ * The library renders a surfel scene from a pinhole camera (per-surfel
+ * preprocess, (tile, depth) sort, front-to-back compositing), differentiates
+ * the render by a hand-written adjoint, evaluates the L1 + D-SSIM + depth
+ * losses, and computes the decomposed-gradient densification statistics
+ * (Eq. 2) and the elongation filter.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns gs_status: GS_OK (0) or a negative error code.  No
+ *    call aborts the process.  gs_last_error() returns a thread-local text
+ *    of the last failure.
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device; "host" pointers are CPU memory.  Unless stated, buffers are
+ *    owned by the caller and must stay valid until the work queued on
+ *    `stream` has completed.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is queued asynchronously on it.  gs_render reads one
+ *    4-byte count back to the host and therefore synchronises the stream
+ *    once per call.
+ *  - Arrays are FP32, C order.  Surfel parameters are structure-of-arrays:
+ *    mu [N][3], quat [N][4] as (w, x, y, z) (normalised inside), scale [N][2]
+ *    (activated, > 0), opacity [N] (activated, in [0, 1]), sh [N][K][3] with
+ *    K = (sh_degree + 1)^2 real spherical-harmonic coefficients per channel
+ *    (index l*l + l + m, Condon-Shortley phase).
+ *  - Images are planar: plane p of an H x W image is at offset p*H*W.
+ *  - Errors detected on the device (instance-count capacity) are reported
+ *    by the call that launched the work after its one synchronisation.
+ */
+#ifndef GS2D_H
+#define GS2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gs_status;
+enum {
+  GS_OK = 0,
+  GS_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, ...)   */
+  GS_ERR_OOM = -2,      /* an allocation through the allocator failed         */
+  GS_ERR_CAPACITY = -3, /* a size limit of the library was exceeded           */
+  GS_ERR_CUDA = -4,     /* a CUDA runtime call or kernel launch failed        */
+  GS_ERR_TIMEOUT = -5,  /* a bounded wait ran out                             */
+  GS_ERR_STATE = -6     /* call made on an object in the wrong state          */
+};
+
+/* Planes of a render, [GS_OUT_PLANES][H][W] FP32 (Eq. 1 of Sec. 3.1 for the
+ * colour; Sec. 3.1 "2D Gaussian Splatting" for distortion and normal;
+ * Sec. 3.2 for inverse depth; Sec. 4.1 for median depth):
+ *   R, G, B       sum_i w_i c_i + T_final * bg, w_i = alpha_i prod_{j<i}(1 - alpha_j)
+ *   ALPHA         sum_i w_i
+ *   DEPTH         sum_i w_i z_i   (expected depth times alpha; divide by ALPHA)
+ *   INVDEPTH      sum_i w_i / z_i (inverse depth for the depth loss)
+ *   MEDIAN        z of the last blended pair entered with transmittance > 0.5
+ *   NX, NY, NZ    sum_i w_i n_i (view-space normals facing the camera)
+ *   DISTORTION    sum_i 2 w_i (z_i A_{i-1} - Z_{i-1}) (depth distortion)
+ *   T_FINAL       transmittance after the last blended pair
+ * The first GS_ADJ_PLANES planes are differentiable; an adjoint set has the
+ * same layout without T_FINAL. */
+enum {
+  GS_PLANE_R = 0, GS_PLANE_G = 1, GS_PLANE_B = 2, GS_PLANE_ALPHA = 3,
+  GS_PLANE_DEPTH = 4, GS_PLANE_INVDEPTH = 5, GS_PLANE_MEDIAN = 6,
+  GS_PLANE_NX = 7, GS_PLANE_NY = 8, GS_PLANE_NZ = 9, GS_PLANE_DISTORTION = 10,
+  GS_PLANE_T_FINAL = 11, GS_OUT_PLANES = 12, GS_ADJ_PLANES = 11
+};
+/* bit masks of adjoint planes */
+#define GS_MASK_RGB 0x7u
+#define GS_MASK_ALL 0x7FFu
+
+/* Pinhole camera: world-to-camera rotation R (row-major) and translation t,
+ * x_cam = R x_world + t; the camera looks down +z, x right, y down.  Pixel
+ * (i, j) samples the point (i + 0.5, j + 0.5).  Host struct, read during the
+ * call. */
+typedef struct {
+  double R[9];
+  double t[3];
+  double fx, fy, cx, cy;
+  int32_t width, height;
+} gs_camera;
+
+/* Rasterizer constants.  gs_default_settings() fills the values used
+ * throughout: near 0.2, alpha_min 1/255, T_min 1e-4, alpha_max 0.99,
+ * rho_max 9 (3-sigma support), screen_inv_sigma2 2 (antialiasing filter of
+ * variance 1/2 pixel^2), black background. */
+typedef struct {
+  float near_plane;
+  float alpha_min;
+  float T_min;
+  float alpha_max;
+  float rho_max;
+  float screen_inv_sigma2;
+  float bg[3];
+} gs_settings;
+
+/* Device-memory allocator used for every buffer the library allocates.
+ * alloc returns a device pointer (NULL on failure) usable on `stream`;
+ * free releases it in stream order.  A zeroed struct selects
+ * cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* ctx, void* stream);
+  void (*free)(void* ptr, size_t bytes, void* ctx, void* stream);
+  void* ctx;
+} gs_allocator;
+
+typedef struct {
+  int64_t n;                 /* number of surfels, >= 0, < 2^31             */
+  int32_t sh_degree;         /* 0..3                                         */
+  const float* mu;           /* device [n][3]                                */
+  const float* quat;         /* device [n][4]                                */
+  const float* scale;        /* device [n][2]                                */
+  const float* opacity;      /* device [n]                                   */
+  const float* sh;           /* device [n][(d+1)^2][3]                       */
+  gs_settings settings;
+  gs_allocator allocator;
+} gs_scene_desc;
+
+typedef struct gs_scene gs_scene;
+typedef struct gs_frame gs_frame;
+
+/* Sec. 3.1: the surfel scene (mu, rotation, (s_u, s_v), opacity, SH).  The
+ * parameter arrays are borrowed, not copied: they must stay valid and hold
+ * the current values whenever work of this scene runs.  Returns GS_ERR_ARG
+ * for bad sizes or null arrays (arrays may be null when n == 0). */
+gs_status gs_default_settings(gs_settings* out);
+gs_status gs_create_scene(gs_scene** out, const gs_scene_desc* desc);
+/* Re-point the borrowed parameter arrays (after densification changes n). */
+gs_status gs_set_params(gs_scene* scene, int64_t n, const float* mu, const float* quat,
+                        const float* scale, const float* opacity, const float* sh);
+gs_status gs_destroy_scene(gs_scene* scene);
+
+/* Render one view (Eq. 1 with the 2DGS surfel model, Sec. 3.1-3.2).
+ *  out:       device [GS_OUT_PLANES][H][W] FP32, written entirely.
+ *  n_contrib: device [H][W] int32 number of blended pairs, or NULL.
+ *  saved:     if non-NULL, receives a frame holding what gs_backward and
+ *             gs_densify_accumulate need; the frame keeps a pointer to `out`
+ *             (its ALPHA and DEPTH planes are read by the backward), so `out`
+ *             must stay unchanged until the frame is released.
+ * Synchronises `stream` once (to size the tile lists). */
+gs_status gs_render(gs_scene* scene, const gs_camera* cam, float* out, int32_t* n_contrib,
+                    gs_frame** saved, void* stream);
+gs_status gs_frame_release(gs_frame* frame, void* stream);
+
+typedef struct {
+  int64_t n_instances;      /* (surfel, tile) pairs in the tile lists        */
+  int64_t n_visible;        /* surfels with a non-empty tile rectangle       */
+  int64_t pairs_evaluated;  /* list entries the forward blend evaluated      */
+  int64_t pairs_blended;    /* pairs that entered the composite              */
+  int64_t bwd_pairs_evaluated; /* list entries the last backward replayed    */
+  int32_t tiles_x, tiles_y;
+} gs_frame_info;
+/* Counters of a frame (synchronises `stream`). */
+gs_status gs_frame_get_info(gs_frame* frame, gs_frame_info* info, void* stream);
+
+/* Debug / parity access to the frame's tile lists: copies (device to
+ * device) up to `cap` sorted surfel indices into `values` (device int32)
+ * and [tiles_x*tiles_y][2] int32 ranges into `ranges` (device), and the
+ * per-surfel tile rectangles [n][4] (tx0, ty0, tx1, ty1) into `rects`
+ * (device int32, may be NULL). */
+gs_status gs_frame_copy_lists(gs_frame* frame, int32_t* values, int64_t cap, int32_t* ranges,
+                              int32_t* rects, void* stream);
+
+/* Sec. 3.1 and 3.2 losses: L1 = mean |C - C*|, SSIM with an 11x11 Gaussian
+ * window (sigma 1.5, zero padded, C1 = 0.01^2, C2 = 0.03^2) averaged over
+ * pixels and channels, L_depth = mean |I - I*| on inverse depth;
+ * total = w_l1 L1 + w_ssim (1 - SSIM) + w_depth L_depth.
+ *  out:            device [GS_OUT_PLANES][H][W] (a render).
+ *  target_rgb:     device [3][H][W].  target_invdepth: device [H][W] or NULL.
+ *  adj_total:      device [GS_ADJ_PLANES][H][W]; planes R, G, B and (when
+ *                  target_invdepth is given) INVDEPTH are written with
+ *                  d total / d plane; other planes are not touched.
+ *  adj_ssim, adj_l1: device [GS_ADJ_PLANES][H][W] or NULL; planes R, G, B
+ *                  receive the adjoint of the weighted SSIM term and of the
+ *                  weighted L1 term (their sum is adj_total's colour).
+ *  losses:         device float[4] = L1, SSIM, L_depth, total. */
+typedef struct {
+  float w_l1, w_ssim, w_depth;
+} gs_loss_weights;
+gs_status gs_loss(int32_t width, int32_t height, const float* out, const float* target_rgb,
+                  const float* target_invdepth, const gs_loss_weights* w, float* adj_total,
+                  float* adj_ssim, float* adj_l1, float* losses, void* stream);
+
+/* Parameter gradients, device, same shapes as the parameters.  gs_backward
+ * ADDS into them (like accumulating .grad); a null pointer skips that
+ * parameter. */
+typedef struct {
+  float* mu;
+  float* quat;
+  float* scale;
+  float* opacity;
+  float* sh;
+} gs_param_grads;
+
+/* Hand-written adjoint of gs_render (reverse replay per pixel from the
+ * saved final transmittance).
+ *  adj_sets:    host array of n_sets (1..3) device pointers, each
+ *               [GS_ADJ_PLANES][H][W]; set 0 drives the parameter gradients.
+ *  plane_masks: host array of n_sets bit masks of the planes that are
+ *               non-zero in each set (bit p = plane p); sets after the first
+ *               may use only the colour planes (mask within GS_MASK_RGB).
+ *  grads:       parameter gradients to accumulate into (set 0).
+ *  screen_grads: device [n_sets][N][2] or NULL: ADDS, per set, the gradient
+ *               of that set's loss with respect to a screen-space translation
+ *               of each surfel's opacity footprint (pixels), the view-space
+ *               position gradient used by densification (Sec. 3.1, Eq. 2). */
+gs_status gs_backward(gs_scene* scene, gs_frame* frame, const float* const* adj_sets,
+                      const uint32_t* plane_masks, int32_t n_sets, const gs_param_grads* grads,
+                      float* screen_grads, void* stream);
+
+/* Decomposed densification statistics (Sec. 3.2, Eq. 2).  For every surfel
+ * visible in the frame (non-empty tile rectangle):
+ *   stats[n][s] += || screen_grads[s][n] ||_2 for s < min(n_sets, 3),
+ *   stats[n][3] += 1.
+ * Set order: 0 total loss, 1 SSIM term, 2 L1 term.  stats: device [N][4]. */
+gs_status gs_densify_accumulate(gs_scene* scene, gs_frame* frame, const float* screen_grads,
+                                int32_t n_sets, float* stats, void* stream);
+
+/* DGD selection (Sec. 3.2, Eq. 2) with the elongation filter (Sec. 3.2):
+ *   k   = max(omega * avg_n(S_tot/cnt) / avg_n(S_ssim/cnt), 1) over cnt > 0
+ *         (k = 1 if the SSIM average is 0),
+ *   g_n = k * S_ssim/cnt (0 when cnt = 0),
+ *   eta_n = min(s_u, s_v) / max(s_u, s_v),
+ *   mask_n = (cnt > 0) and (g_n >= grad_thr) and (eta_n >= eta_thr).
+ *  stats: device [n][4]; scale: device [n][2]; mask: device uint8 [n];
+ *  g_out: device float [n] or NULL; k_out: device float[1] or NULL. */
+gs_status gs_densify_select(int64_t n, const float* stats, const float* scale, float omega,
+                            float grad_thr, float eta_thr, uint8_t* mask, float* g_out,
+                            float* k_out, void* stream);
+
+/* Elongation filter alone (Sec. 3.2): keep[n] = eta_n >= eta_thr. */
+gs_status gs_elongation_filter(int64_t n, const float* scale, float eta_thr, uint8_t* keep,
+                               void* stream);
+
+/* Diagnostics.
+ * gs_kernel_launches: number of CUDA kernels this library has launched in
+ *   this process (all entry points, all devices).
+ * gs_profile_enable: when on, every launch of the kernel groups below is
+ *   bracketed by CUDA events recorded on its own stream.
+ * gs_profile_read: synchronises the recorded events of one group, returns
+ *   their summed duration (ms) and count, and forgets them.  Groups:
+ *   0 preprocess, 1 scan/sort/emit/ranges, 2 forward blend, 3 loss,
+ *   4 backward blend, 5 preprocess backward, 6 densify/filter. */
+enum {
+  GS_PROF_PREPROCESS = 0, GS_PROF_SORT = 1, GS_PROF_BLEND_FWD = 2, GS_PROF_LOSS = 3,
+  GS_PROF_BLEND_BWD = 4, GS_PROF_PREPROCESS_BWD = 5, GS_PROF_DENSIFY = 6, GS_PROF_GROUPS = 7
+};
+uint64_t gs_kernel_launches(void);
+gs_status gs_profile_enable(int32_t on);
+gs_status gs_profile_read(int32_t group, double* total_ms, int64_t* launches);
+
+/* Wait for `stream` with a bound: GS_ERR_TIMEOUT after timeout_ms. */
+gs_status gs_sync(void* stream, int32_t timeout_ms);
+const char* gs_last_error(void);
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS2D_H */

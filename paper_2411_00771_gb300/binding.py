@@ -1,0 +1,342 @@
+"""Thin ctypes binding of ``libgs2d.so`` (the C ABI in ``include/gs2d.h``).
+
+Argument marshalling only: every step of the rasterizer runs in the CUDA
+library.  Tensors are PyTorch CUDA tensors (PyTorch owns device memory and
+streams); their device pointers are passed through.  If the compiled
+library is missing this module raises at import: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgs2d.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2411_00771_gb300/build.py "
+                      "(or __graft_entry__.build()); there is no fallback path")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OUT_PLANES = 12
+ADJ_PLANES = 11
+MASK_RGB = 0x7
+MASK_ALL = 0x7FF
+PLANE = dict(r=0, g=1, b=2, alpha=3, depth=4, invdepth=5, median=6, nx=7, ny=8, nz=9,
+             distortion=10, T_final=11)
+ERRORS = {-1: "GS_ERR_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_CAPACITY", -4: "GS_ERR_CUDA",
+          -5: "GS_ERR_TIMEOUT", -6: "GS_ERR_STATE"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3), ("fx", ctypes.c_double),
+                ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class gs_settings(ctypes.Structure):
+    _fields_ = [("near_plane", ctypes.c_float), ("alpha_min", ctypes.c_float),
+                ("T_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
+                ("rho_max", ctypes.c_float), ("screen_inv_sigma2", ctypes.c_float),
+                ("bg", ctypes.c_float * 3)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class gs_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class gs_scene_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32),
+                ("mu", ctypes.c_void_p), ("quat", ctypes.c_void_p), ("scale", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p),
+                ("settings", gs_settings), ("allocator", gs_allocator)]
+
+
+class gs_frame_info(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int64), ("n_visible", ctypes.c_int64),
+                ("pairs_evaluated", ctypes.c_int64), ("pairs_blended", ctypes.c_int64),
+                ("bwd_pairs_evaluated", ctypes.c_int64), ("tiles_x", ctypes.c_int32),
+                ("tiles_y", ctypes.c_int32)]
+
+
+class gs_loss_weights(ctypes.Structure):
+    _fields_ = [("w_l1", ctypes.c_float), ("w_ssim", ctypes.c_float), ("w_depth", ctypes.c_float)]
+
+
+class gs_param_grads(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_void_p), ("quat", ctypes.c_void_p), ("scale", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+_V = ctypes.c_void_p
+_SIGS = {
+    "gs_default_settings": [ctypes.POINTER(gs_settings)],
+    "gs_create_scene": [ctypes.POINTER(_V), ctypes.POINTER(gs_scene_desc)],
+    "gs_set_params": [_V, ctypes.c_int64, _V, _V, _V, _V, _V],
+    "gs_destroy_scene": [_V],
+    "gs_render": [_V, ctypes.POINTER(gs_camera), _V, _V, ctypes.POINTER(_V), _V],
+    "gs_frame_release": [_V, _V],
+    "gs_frame_get_info": [_V, ctypes.POINTER(gs_frame_info), _V],
+    "gs_frame_copy_lists": [_V, _V, ctypes.c_int64, _V, _V, _V],
+    "gs_loss": [ctypes.c_int32, ctypes.c_int32, _V, _V, _V, ctypes.POINTER(gs_loss_weights), _V, _V,
+                _V, _V, _V],
+    "gs_backward": [_V, _V, ctypes.POINTER(_V), ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32,
+                    ctypes.POINTER(gs_param_grads), _V, _V],
+    "gs_densify_accumulate": [_V, _V, _V, ctypes.c_int32, _V, _V],
+    "gs_densify_select": [ctypes.c_int64, _V, _V, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                          _V, _V, _V, _V],
+    "gs_elongation_filter": [ctypes.c_int64, _V, ctypes.c_float, _V, _V],
+    "gs_sync": [_V, ctypes.c_int32],
+    "gs_profile_enable": [ctypes.c_int32],
+    "gs_profile_read": [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.gs_last_error.restype = ctypes.c_char_p
+_lib.gs_last_error.argtypes = []
+_lib.gs_version.restype = ctypes.c_char_p
+_lib.gs_version.argtypes = []
+_lib.gs_kernel_launches.restype = ctypes.c_uint64
+_lib.gs_kernel_launches.argtypes = []
+
+EXPORTED = list(_SIGS) + ["gs_last_error", "gs_version", "gs_kernel_launches"]
+PROF_GROUPS = ["preprocess", "sort", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "densify"]
+
+
+def lib():
+    return _lib
+
+
+def _check(code):
+    if code != 0:
+        raise GsError(code, _lib.gs_last_error().decode())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t, dtype=torch.float32, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_settings(**kw) -> gs_settings:
+    s = gs_settings()
+    _check(_lib.gs_default_settings(ctypes.byref(s)))
+    for k, v in kw.items():
+        if k == "bg":
+            for i in range(3):
+                s.bg[i] = float(v[i])
+        else:
+            setattr(s, k, float(v))
+    return s
+
+
+def make_camera(cam: dict) -> gs_camera:
+    c = gs_camera()
+    R = [float(x) for x in torch.as_tensor(cam["R"], dtype=torch.float64).reshape(9).tolist()]
+    t = [float(x) for x in torch.as_tensor(cam["t"], dtype=torch.float64).reshape(3).tolist()]
+    for i in range(9):
+        c.R[i] = R[i]
+    for i in range(3):
+        c.t[i] = t[i]
+    c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+class Frame:
+    """Saved state of one render, needed by backward and densify stats."""
+
+    def __init__(self, handle, scene, cam, out):
+        self.handle = ctypes.c_void_p(handle)
+        self.scene = scene
+        self.cam = cam
+        self.out = out  # keeps the output planes alive (read by the backward)
+
+    def info(self, stream=None) -> dict:
+        i = gs_frame_info()
+        _check(_lib.gs_frame_get_info(self.handle, ctypes.byref(i), _stream(stream)))
+        return {k: getattr(i, k) for k, _ in gs_frame_info._fields_}
+
+    def lists(self, stream=None):
+        info = self.info(stream)
+        K = info["n_instances"]
+        ntiles = info["tiles_x"] * info["tiles_y"]
+        dev = self.out.device
+        vals = torch.empty(max(K, 1), dtype=torch.int32, device=dev)
+        ranges = torch.empty((ntiles, 2), dtype=torch.int32, device=dev)
+        rects = torch.empty((max(self.scene.n, 1), 4), dtype=torch.int32, device=dev)
+        _check(_lib.gs_frame_copy_lists(self.handle, _ptr(vals, torch.int32), K, _ptr(ranges, torch.int32),
+                                        _ptr(rects, torch.int32) if self.scene.n > 0 else None,
+                                        _stream(stream)))
+        return vals[:K], ranges, rects[:self.scene.n]
+
+    def release(self, stream=None):
+        if self.handle:
+            _check(_lib.gs_frame_release(self.handle, _stream(stream)))
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            if self.handle and self.handle.value:
+                _lib.gs_frame_release(self.handle, None)
+        except Exception:
+            pass
+
+
+class Scene:
+    """A borrowed view of surfel parameter tensors (see gs_create_scene)."""
+
+    def __init__(self, mu, quat, scale, opacity, sh, sh_degree: int, settings: gs_settings = None):
+        self.settings = settings if settings is not None else default_settings()
+        self.sh_degree = int(sh_degree)
+        self._handle = ctypes.c_void_p()
+        desc = gs_scene_desc()
+        desc.settings = self.settings
+        desc.sh_degree = self.sh_degree
+        self._fill(desc, mu, quat, scale, opacity, sh)
+        _check(_lib.gs_create_scene(ctypes.byref(self._handle), ctypes.byref(desc)))
+
+    def _fill(self, desc, mu, quat, scale, opacity, sh):
+        n = mu.shape[0]
+        K = (self.sh_degree + 1) ** 2
+        desc.n = n
+        desc.mu = _ptr(mu, shape=(n, 3), name="mu")
+        desc.quat = _ptr(quat, shape=(n, 4), name="quat")
+        desc.scale = _ptr(scale, shape=(n, 2), name="scale")
+        desc.opacity = _ptr(opacity, shape=(n,), name="opacity")
+        desc.sh = _ptr(sh, shape=(n, K, 3), name="sh")
+        self.n = n
+        self.params = (mu, quat, scale, opacity, sh)
+
+    def set_params(self, mu, quat, scale, opacity, sh):
+        d = gs_scene_desc()
+        d.sh_degree = self.sh_degree
+        self._fill(d, mu, quat, scale, opacity, sh)
+        _check(_lib.gs_set_params(self._handle, d.n, d.mu, d.quat, d.scale, d.opacity, d.sh))
+
+    def render(self, cam: dict, out=None, n_contrib=None, save: bool = True, stream=None):
+        W, H = int(cam["width"]), int(cam["height"])
+        dev = self.params[0].device
+        if out is None:
+            out = torch.empty((OUT_PLANES, H, W), dtype=torch.float32, device=dev)
+        c = make_camera(cam)
+        fh = ctypes.c_void_p()
+        _check(_lib.gs_render(self._handle, ctypes.byref(c), _ptr(out, shape=(OUT_PLANES, H, W), name="out"),
+                              _ptr(n_contrib, torch.int32, (H, W), "n_contrib"),
+                              ctypes.byref(fh) if save else None, _stream(stream)))
+        frame = Frame(fh.value, self, cam, out) if save else None
+        return out, frame
+
+    def backward(self, frame: Frame, adj_sets, masks, grads: dict, screen=None, stream=None):
+        n_sets = len(adj_sets)
+        arr = (ctypes.c_void_p * n_sets)(*[_ptr(a, name="adjoint").value for a in adj_sets])
+        m = (ctypes.c_uint32 * n_sets)(*[int(x) for x in masks])
+        g = gs_param_grads()
+        for k in ("mu", "quat", "scale", "opacity", "sh"):
+            t = grads.get(k)
+            setattr(g, k, None if t is None else _ptr(t, name=f"grad {k}").value)
+        _check(_lib.gs_backward(self._handle, frame.handle, arr, m, n_sets, ctypes.byref(g),
+                                _ptr(screen, shape=(n_sets, self.n, 2), name="screen"), _stream(stream)))
+
+    def densify_accumulate(self, frame: Frame, screen, stats, stream=None):
+        n_sets = screen.shape[0]
+        _check(_lib.gs_densify_accumulate(self._handle, frame.handle, _ptr(screen, name="screen"), n_sets,
+                                          _ptr(stats, shape=(self.n, 4), name="stats"), _stream(stream)))
+
+    def close(self):
+        if self._handle:
+            _lib.gs_destroy_scene(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def loss(out, target, tinv=None, weights=(0.8, 0.2, 0.0), adj_total=None, adj_ssim=None,
+         adj_l1=None, losses=None, stream=None):
+    H, W = out.shape[-2:]
+    dev = out.device
+    if adj_total is None:
+        adj_total = torch.zeros((ADJ_PLANES, H, W), dtype=torch.float32, device=dev)
+    if losses is None:
+        losses = torch.empty(4, dtype=torch.float32, device=dev)
+    w = gs_loss_weights(*[float(x) for x in weights])
+    _check(_lib.gs_loss(W, H, _ptr(out, shape=(OUT_PLANES, H, W), name="out"),
+                        _ptr(target, shape=(3, H, W), name="target"),
+                        _ptr(tinv, shape=(H, W), name="target_invdepth"), ctypes.byref(w),
+                        _ptr(adj_total, shape=(ADJ_PLANES, H, W), name="adj_total"),
+                        _ptr(adj_ssim, shape=(ADJ_PLANES, H, W), name="adj_ssim"),
+                        _ptr(adj_l1, shape=(ADJ_PLANES, H, W), name="adj_l1"),
+                        _ptr(losses, shape=(4,), name="losses"), _stream(stream)))
+    return losses, adj_total, adj_ssim, adj_l1
+
+
+def densify_select(stats, scale, omega=0.9, grad_thr=0.0002, eta_thr=0.1, stream=None):
+    n = stats.shape[0]
+    dev = stats.device
+    mask = torch.empty(n, dtype=torch.uint8, device=dev)
+    g = torch.empty(n, dtype=torch.float32, device=dev)
+    k = torch.empty(1, dtype=torch.float32, device=dev)
+    _check(_lib.gs_densify_select(n, _ptr(stats, shape=(n, 4), name="stats"),
+                                  _ptr(scale, shape=(n, 2), name="scale"), float(omega), float(grad_thr),
+                                  float(eta_thr), _ptr(mask, torch.uint8), _ptr(g), _ptr(k),
+                                  _stream(stream)))
+    return mask, g, k
+
+
+def elongation_filter(scale, eta_thr=0.1, stream=None):
+    n = scale.shape[0]
+    keep = torch.empty(n, dtype=torch.uint8, device=scale.device)
+    _check(_lib.gs_elongation_filter(n, _ptr(scale, shape=(n, 2), name="scale"), float(eta_thr),
+                                     _ptr(keep, torch.uint8), _stream(stream)))
+    return keep
+
+
+def kernel_launches() -> int:
+    return int(_lib.gs_kernel_launches())
+
+
+def profile_enable(on: bool = True):
+    _check(_lib.gs_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """{group: (total_ms, launches)} for the recorded launches; clears them."""
+    res = {}
+    for i, name in enumerate(PROF_GROUPS):
+        t = ctypes.c_double()
+        k = ctypes.c_int64()
+        _check(_lib.gs_profile_read(i, ctypes.byref(t), ctypes.byref(k)))
+        res[name] = (t.value, k.value)
+    return res
+
+
+def sync(timeout_ms=10000, stream=None):
+    _check(_lib.gs_sync(_stream(stream), int(timeout_ms)))

@@ -1,0 +1,530 @@
+// C ABI of the library: scene and frame objects, buffer management and the
+// order of kernel launches for render, loss, backward and densification.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gs2d_internal.cuh"
+
+using namespace gs2d;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gs_status fail(gs_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+gs_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(GS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GS_CK(expr)                                   \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr); \
+  } while (0)
+
+// Allocations through the caller's allocator (or the stream-ordered pool).
+struct Alloc {
+  gs_allocator a{};
+  void* get(size_t bytes, cudaStream_t st) const {
+    if (bytes == 0) bytes = 16;
+    if (a.alloc) return a.alloc(bytes, a.ctx, st);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p, size_t bytes, cudaStream_t st) const {
+    if (!p) return;
+    if (a.free) a.free(p, bytes, a.ctx, st);
+    else cudaFreeAsync(p, st);
+  }
+};
+
+// A list of buffers freed together.
+struct Buffers {
+  struct B {
+    void* p;
+    size_t bytes;
+  };
+  std::vector<B> list;
+  const Alloc* al = nullptr;
+  template <typename T>
+  T* get(size_t count, cudaStream_t st) {
+    void* p = al->get(count * sizeof(T), st);
+    if (p) list.push_back({p, count * sizeof(T)});
+    return static_cast<T*>(p);
+  }
+  void release(void* p, cudaStream_t st) {
+    for (size_t i = 0; i < list.size(); ++i)
+      if (list[i].p == p) {
+        al->put(p, list[i].bytes, st);
+        list.erase(list.begin() + (long)i);
+        return;
+      }
+  }
+  void release_all(cudaStream_t st) {
+    for (auto& b : list) al->put(b.p, b.bytes, st);
+    list.clear();
+  }
+};
+
+void set_pool_threshold() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done = true;
+}
+
+SetDev to_dev(const gs_settings& s) {
+  SetDev d;
+  d.near_plane = s.near_plane;
+  d.alpha_min = s.alpha_min;
+  d.T_min = s.T_min;
+  d.alpha_max = s.alpha_max;
+  d.rho_max = s.rho_max;
+  d.sinv = s.screen_inv_sigma2;
+  d.bg[0] = s.bg[0];
+  d.bg[1] = s.bg[1];
+  d.bg[2] = s.bg[2];
+  return d;
+}
+
+int bits_for(int64_t v) {
+  int b = 0;
+  while ((int64_t(1) << b) < v) ++b;
+  return b;
+}
+
+}  // namespace
+
+// ---- launch accounting and optional per-kernel event timing ---------------
+namespace gs2d {
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+std::atomic<int> g_prof_on{0};
+std::mutex g_prof_mu;
+struct EvPair {
+  cudaEvent_t a, b;
+};
+std::vector<EvPair> g_prof_pending[kProfCount];
+std::vector<cudaEvent_t> g_prof_free;
+thread_local cudaEvent_t g_prof_open[kProfCount] = {};
+cudaEvent_t prof_event() {
+  if (!g_prof_free.empty()) {
+    cudaEvent_t e = g_prof_free.back();
+    g_prof_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+__global__ void api_unpack_rect_kernel(const uint2* __restrict__ rect, const uint32_t* __restrict__ tcount,
+                                   int n, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint2 r = rect[i];
+  const bool v = tcount[i] > 0;
+  out[4 * i] = v ? (int)(r.x & 0xFFFF) : 0;
+  out[4 * i + 1] = v ? (int)(r.x >> 16) : 0;
+  out[4 * i + 2] = v ? (int)(r.y & 0xFFFF) : 0;
+  out[4 * i + 3] = v ? (int)(r.y >> 16) : 0;
+}
+
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+void prof_begin(int id, cudaStream_t st) {
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEvent_t e = prof_event();
+  if (e && cudaEventRecord(e, st) == cudaSuccess) g_prof_open[id] = e;
+  else g_prof_open[id] = nullptr;
+}
+
+void prof_end(int id, cudaStream_t st) {
+  if (!g_prof_on.load(std::memory_order_relaxed) || !g_prof_open[id]) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEvent_t e = prof_event();
+  if (e && cudaEventRecord(e, st) == cudaSuccess) g_prof_pending[id].push_back({g_prof_open[id], e});
+  g_prof_open[id] = nullptr;
+}
+}  // namespace gs2d
+
+struct gs_scene {
+  ParamsDev P;
+  gs_settings settings;
+  Alloc al;
+};
+
+struct gs_frame {
+  gs_scene* scene = nullptr;
+  CamDev cam{};
+  int n = 0;
+  int sh_degree = 0;
+  int64_t K = 0;
+  int64_t n_visible = 0;
+  Buffers buf;
+  float4* rec = nullptr;
+  uint2* rect = nullptr;
+  uint32_t* tcount = nullptr;
+  uint32_t* vals = nullptr;
+  int2* ranges = nullptr;
+  int32_t* last = nullptr;
+  int32_t* med = nullptr;
+  unsigned long long* counters = nullptr;  // evaluated, blended, bwd replayed, visible
+  const float* out = nullptr;
+};
+
+extern "C" {
+
+uint64_t gs_kernel_launches(void) { return gs2d::g_launches.load(); }
+
+gs_status gs_profile_enable(int32_t on) {
+  gs2d::g_prof_on.store(on ? 1 : 0);
+  return GS_OK;
+}
+
+gs_status gs_profile_read(int32_t kernel, double* total_ms, int64_t* launches) {
+  if (kernel < 0 || kernel >= kProfCount || !total_ms || !launches)
+    return fail(GS_ERR_ARG, "gs_profile_read: bad argument");
+  std::lock_guard<std::mutex> lk(gs2d::g_prof_mu);
+  double t = 0.0;
+  int64_t k = 0;
+  for (auto& pr : gs2d::g_prof_pending[kernel]) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(pr.b) == cudaSuccess && cudaEventElapsedTime(&ms, pr.a, pr.b) == cudaSuccess) {
+      t += ms;
+      ++k;
+    }
+    cudaGetLastError();
+    gs2d::g_prof_free.push_back(pr.a);
+    gs2d::g_prof_free.push_back(pr.b);
+  }
+  gs2d::g_prof_pending[kernel].clear();
+  *total_ms = t;
+  *launches = k;
+  return GS_OK;
+}
+
+const char* gs_version(void) { return "gs2d-gb300 0.1 (sm_103a)"; }
+
+const char* gs_last_error(void) { return g_last_error.c_str(); }
+
+gs_status gs_default_settings(gs_settings* s) {
+  if (!s) return fail(GS_ERR_ARG, "gs_default_settings: null");
+  s->near_plane = 0.2f;
+  s->alpha_min = 1.0f / 255.0f;
+  s->T_min = 1e-4f;
+  s->alpha_max = 0.99f;
+  s->rho_max = 9.0f;
+  s->screen_inv_sigma2 = 2.0f;
+  s->bg[0] = s->bg[1] = s->bg[2] = 0.0f;
+  return GS_OK;
+}
+
+gs_status gs_set_params(gs_scene* sc, int64_t n, const float* mu, const float* quat,
+                        const float* scale, const float* opacity, const float* sh) {
+  if (!sc) return fail(GS_ERR_ARG, "gs_set_params: null scene");
+  if (n < 0 || n >= (int64_t(1) << 31)) return fail(GS_ERR_ARG, "gs_set_params: n out of range");
+  if (n > 0 && (!mu || !quat || !scale || !opacity || !sh))
+    return fail(GS_ERR_ARG, "gs_set_params: null parameter array");
+  sc->P.n = (int)n;
+  sc->P.mu = mu;
+  sc->P.quat = quat;
+  sc->P.scale = scale;
+  sc->P.opacity = opacity;
+  sc->P.sh = sh;
+  return GS_OK;
+}
+
+gs_status gs_create_scene(gs_scene** out, const gs_scene_desc* d) {
+  if (!out || !d) return fail(GS_ERR_ARG, "gs_create_scene: null argument");
+  *out = nullptr;
+  if (d->sh_degree < 0 || d->sh_degree > 3) return fail(GS_ERR_ARG, "gs_create_scene: sh_degree must be 0..3");
+  const gs_settings& s = d->settings;
+  if (!(s.rho_max > 0.f) || !(s.screen_inv_sigma2 > 0.f) || !(s.alpha_max > 0.f) ||
+      !(s.alpha_max < 1.f) || !(s.T_min > 0.f) || !(s.near_plane > 0.f))
+    return fail(GS_ERR_ARG, "gs_create_scene: invalid settings");
+  gs_scene* sc = new (std::nothrow) gs_scene();
+  if (!sc) return fail(GS_ERR_OOM, "gs_create_scene: host allocation");
+  sc->settings = s;
+  sc->al.a = d->allocator;
+  sc->P.sh_degree = d->sh_degree;
+  gs_status st = gs_set_params(sc, d->n, d->mu, d->quat, d->scale, d->opacity, d->sh);
+  if (st != GS_OK) {
+    delete sc;
+    return st;
+  }
+  set_pool_threshold();
+  *out = sc;
+  return GS_OK;
+}
+
+gs_status gs_destroy_scene(gs_scene* sc) {
+  delete sc;
+  return GS_OK;
+}
+
+gs_status gs_frame_release(gs_frame* f, void* stream) {
+  if (!f) return GS_OK;
+  f->buf.release_all((cudaStream_t)stream);
+  delete f;
+  return GS_OK;
+}
+
+gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_contrib,
+                    gs_frame** saved, void* stream) {
+  if (saved) *saved = nullptr;
+  if (!sc || !c || !out) return fail(GS_ERR_ARG, "gs_render: null argument");
+  if (c->width <= 0 || c->height <= 0 || c->width > 16 * 65535 || c->height > 16 * 65535)
+    return fail(GS_ERR_ARG, "gs_render: bad image size");
+  if (!(c->fx > 0) || !(c->fy > 0)) return fail(GS_ERR_ARG, "gs_render: focal lengths must be > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  gs_frame* f = new (std::nothrow) gs_frame();
+  if (!f) return fail(GS_ERR_OOM, "gs_render: host allocation");
+  f->scene = sc;
+  f->n = sc->P.n;
+  f->sh_degree = sc->P.sh_degree;
+  f->out = out;
+  f->buf.al = &sc->al;
+  CamDev& cam = f->cam;
+  for (int i = 0; i < 9; ++i) cam.R[i] = c->R[i];
+  for (int i = 0; i < 3; ++i) cam.t[i] = c->t[i];
+  cam.fx = c->fx; cam.fy = c->fy; cam.cx = c->cx; cam.cy = c->cy;
+  for (int i = 0; i < 3; ++i)
+    cam.campos[i] = -(c->R[i] * c->t[0] + c->R[3 + i] * c->t[1] + c->R[6 + i] * c->t[2]);
+  cam.W = c->width; cam.H = c->height;
+  cam.tiles_x = (cam.W + kTile - 1) / kTile;
+  cam.tiles_y = (cam.H + kTile - 1) / kTile;
+  const int ntiles = cam.tiles_x * cam.tiles_y;
+  const int64_t n = f->n;
+  const SetDev set = to_dev(sc->settings);
+  Buffers tmp;
+  tmp.al = &sc->al;
+  auto cleanup = [&](gs_status s) {
+    tmp.release_all(st);
+    gs_frame_release(f, stream);
+    return s;
+  };
+  // per-surfel buffers
+  f->rec = f->buf.get<float4>((size_t)(n > 0 ? n : 1) * kRecF4, st);
+  f->rect = f->buf.get<uint2>(n > 0 ? n : 1, st);
+  f->tcount = f->buf.get<uint32_t>(n > 0 ? n : 1, st);
+  f->ranges = f->buf.get<int2>(ntiles, st);
+  f->last = f->buf.get<int32_t>((size_t)cam.W * cam.H, st);
+  f->med = f->buf.get<int32_t>((size_t)cam.W * cam.H, st);
+  f->counters = f->buf.get<unsigned long long>(8, st);
+  uint32_t* dkey = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* idx = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* dkey2 = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* idx2 = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* cnts = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* offs = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* rtmp = tmp.get<uint32_t>(radix_tmp_words(n) + scan_tmp_words(n) + 4, st);
+  if (!f->rec || !f->rect || !f->tcount || !f->ranges || !f->last || !f->med || !f->counters || !dkey ||
+      !idx || !dkey2 || !idx2 || !cnts || !offs || !rtmp)
+    return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed"));
+  uint32_t* total = rtmp + radix_tmp_words(n) + scan_tmp_words(n);
+  cudaError_t e;
+#define GS_CKC(expr)                                          \
+  do {                                                        \
+    e = (expr);                                               \
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, #expr)); \
+  } while (0)
+  GS_CKC(cudaMemsetAsync(f->counters, 0, 8 * sizeof(unsigned long long), st));
+  GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, st));
+  uint32_t *skey = dkey, *sidx = idx;
+  GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st));
+  GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st));
+  GS_CKC(launch_scan(cnts, offs, n, total, rtmp + radix_tmp_words(n), st));
+  uint32_t Kh = 0;
+  GS_CKC(cudaMemcpyAsync(&Kh, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  GS_CKC(cudaStreamSynchronize(st));
+  const int64_t K = Kh;
+  if (K >= (int64_t(1) << 31)) return cleanup(fail(GS_ERR_CAPACITY, "gs_render: more than 2^31 tile instances"));
+  f->K = K;
+  uint32_t* keys = tmp.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* vals = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* keys2 = tmp.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* vals2 = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* ktmp = tmp.get<uint32_t>(radix_tmp_words(K), st);
+  if (!keys || !vals || !keys2 || !vals2 || !ktmp)
+    return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed (tile lists)"));
+  GS_CKC(launch_emit(sidx, offs, f->rect, n, cam.tiles_x, keys, vals, st));
+  uint32_t *tk = keys, *tv = vals;
+  GS_CKC(radix_sort_pairs(keys, vals, keys2, vals2, K, bits_for(ntiles), ktmp, &tk, &tv, st));
+  f->vals = tv;
+  f->buf.release(tv == vals ? vals2 : vals, st);
+  GS_CKC(launch_ranges(tk, K, f->ranges, ntiles, st));
+  GS_CKC(launch_blend_fwd(cam, set, f->rec, f->vals, f->ranges, out, n_contrib, f->last, f->med,
+                          f->counters, st));
+#undef GS_CKC
+  tmp.release_all(st);
+  if (saved) {
+    *saved = f;
+  } else {
+    gs_frame_release(f, stream);
+  }
+  return GS_OK;
+}
+
+gs_status gs_frame_get_info(gs_frame* f, gs_frame_info* info, void* stream) {
+  if (!f || !info) return fail(GS_ERR_ARG, "gs_frame_get_info: null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long h[8];
+  GS_CK(cudaMemcpyAsync(h, f->counters, sizeof h, cudaMemcpyDeviceToHost, st));
+  GS_CK(cudaStreamSynchronize(st));
+  info->n_instances = f->K;
+  info->pairs_evaluated = (int64_t)h[0];
+  info->pairs_blended = (int64_t)h[1];
+  info->bwd_pairs_evaluated = (int64_t)h[2];
+  info->tiles_x = f->cam.tiles_x;
+  info->tiles_y = f->cam.tiles_y;
+  // visible surfels: count non-zero tile counts on the host (debug path)
+  std::vector<uint32_t> tc((size_t)f->n);
+  if (f->n > 0) {
+    GS_CK(cudaMemcpyAsync(tc.data(), f->tcount, sizeof(uint32_t) * (size_t)f->n,
+                          cudaMemcpyDeviceToHost, st));
+    GS_CK(cudaStreamSynchronize(st));
+  }
+  int64_t v = 0;
+  for (uint32_t x : tc) v += x > 0;
+  info->n_visible = v;
+  return GS_OK;
+}
+
+gs_status gs_frame_copy_lists(gs_frame* f, int32_t* values, int64_t cap, int32_t* ranges,
+                              int32_t* rects, void* stream) {
+  if (!f) return fail(GS_ERR_ARG, "gs_frame_copy_lists: null frame");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t k = f->K < cap ? f->K : cap;
+  if (values && k > 0)
+    GS_CK(cudaMemcpyAsync(values, f->vals, sizeof(uint32_t) * (size_t)k, cudaMemcpyDeviceToDevice, st));
+  if (ranges)
+    GS_CK(cudaMemcpyAsync(ranges, f->ranges, sizeof(int2) * (size_t)f->cam.tiles_x * f->cam.tiles_y,
+                          cudaMemcpyDeviceToDevice, st));
+  if (rects && f->n > 0) {
+    api_unpack_rect_kernel<<<div_up(f->n, 256), 256, 0, st>>>(f->rect, f->tcount, f->n, rects);
+    count_launch();
+    GS_CK(cudaGetLastError());
+  }
+  return GS_OK;
+}
+
+gs_status gs_loss(int32_t W, int32_t H, const float* out, const float* tgt, const float* tinv,
+                  const gs_loss_weights* w, float* adj_total, float* adj_ssim, float* adj_l1,
+                  float* losses, void* stream) {
+  if (W <= 0 || H <= 0 || !out || !tgt || !w || !adj_total || !losses)
+    return fail(GS_ERR_ARG, "gs_loss: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  float* tmp = static_cast<float*>(al.get(loss_tmp_floats(W, H) * sizeof(float), st));
+  if (!tmp) return fail(GS_ERR_OOM, "gs_loss: scratch allocation failed");
+  cudaError_t e = launch_loss(W, H, out, tgt, tinv, *w, adj_total, adj_ssim, adj_l1, losses, tmp, st);
+  al.put(tmp, 0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_loss");
+  return GS_OK;
+}
+
+gs_status gs_backward(gs_scene* sc, gs_frame* f, const float* const* adj_sets,
+                      const uint32_t* plane_masks, int32_t n_sets, const gs_param_grads* grads,
+                      float* screen_grads, void* stream) {
+  if (!sc || !f || !adj_sets || !plane_masks || !grads) return fail(GS_ERR_ARG, "gs_backward: null argument");
+  if (f->scene != sc) return fail(GS_ERR_STATE, "gs_backward: frame belongs to another scene");
+  if (sc->P.n != f->n) return fail(GS_ERR_STATE, "gs_backward: surfel count changed since the render");
+  if (n_sets < 1 || n_sets > 3) return fail(GS_ERR_ARG, "gs_backward: n_sets must be 1..3");
+  AdjDev adj{};
+  adj.n_sets = n_sets;
+  for (int s = 0; s < n_sets; ++s) {
+    if (!adj_sets[s]) return fail(GS_ERR_ARG, "gs_backward: null adjoint set");
+    if (s > 0 && (plane_masks[s] & ~GS_MASK_RGB)) return fail(GS_ERR_ARG, "gs_backward: sets after the first may use only colour planes");
+    adj.set[s] = adj_sets[s];
+    adj.mask[s] = plane_masks[s] & GS_MASK_ALL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = f->n;
+  float* grec = static_cast<float*>(sc->al.get(sizeof(float) * kGradRec * (size_t)(n > 0 ? n : 1), st));
+  if (!grec) return fail(GS_ERR_OOM, "gs_backward: scratch allocation failed");
+  cudaError_t e = cudaMemsetAsync(grec, 0, sizeof(float) * kGradRec * (size_t)n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->counters + 2, 0, sizeof(unsigned long long), st);
+  const SetDev set = to_dev(sc->settings);
+  if (e == cudaSuccess)
+    e = launch_blend_bwd(f->cam, set, f->rec, f->vals, f->ranges, f->out, f->last, f->med, adj, grec,
+                         screen_grads, n, f->counters, st);
+  if (e == cudaSuccess) e = launch_preprocess_bwd(sc->P, f->cam, f->tcount, grec, *grads, st);
+  sc->al.put(grec, sizeof(float) * kGradRec * (size_t)(n > 0 ? n : 1), st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_backward");
+  return GS_OK;
+}
+
+gs_status gs_densify_accumulate(gs_scene* sc, gs_frame* f, const float* screen, int32_t n_sets,
+                                float* stats, void* stream) {
+  if (!sc || !f || !screen || !stats) return fail(GS_ERR_ARG, "gs_densify_accumulate: null argument");
+  if (f->n != sc->P.n) return fail(GS_ERR_STATE, "gs_densify_accumulate: surfel count changed");
+  if (n_sets < 1) return fail(GS_ERR_ARG, "gs_densify_accumulate: n_sets must be >= 1");
+  cudaError_t e = launch_densify_accumulate(f->tcount, screen, f->n, n_sets, stats, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_densify_accumulate");
+  return GS_OK;
+}
+
+gs_status gs_densify_select(int64_t n, const float* stats, const float* scale, float omega,
+                            float grad_thr, float eta_thr, uint8_t* mask, float* g_out, float* k_out,
+                            void* stream) {
+  if (n < 0 || (n > 0 && (!stats || !scale || !mask))) return fail(GS_ERR_ARG, "gs_densify_select: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  double* tmp = static_cast<double*>(al.get(densify_tmp_doubles(n) * sizeof(double), st));
+  if (!tmp) return fail(GS_ERR_OOM, "gs_densify_select: scratch allocation failed");
+  cudaError_t e = launch_densify_select(n, stats, scale, omega, grad_thr, eta_thr, mask, g_out, k_out, tmp, st);
+  al.put(tmp, 0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_densify_select");
+  return GS_OK;
+}
+
+gs_status gs_elongation_filter(int64_t n, const float* scale, float eta_thr, uint8_t* keep, void* stream) {
+  if (n < 0 || (n > 0 && (!scale || !keep))) return fail(GS_ERR_ARG, "gs_elongation_filter: bad argument");
+  cudaError_t e = launch_elongation(n, scale, eta_thr, keep, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_elongation_filter");
+  return GS_OK;
+}
+
+gs_status gs_sync(void* stream, int32_t timeout_ms) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery((cudaStream_t)stream);
+    if (e == cudaSuccess) return GS_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "gs_sync");
+    const auto dt = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+    if (dt.count() >= timeout_ms) return fail(GS_ERR_TIMEOUT, "gs_sync: stream still busy");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,250 @@
+// Photometric and depth losses with their adjoints (Sec. 3.1: L1 + D-SSIM;
+// Sec. 3.2: L1 on inverse depth).
+//
+// Kernel 1, per 16 x 16 tile and colour channel: loads a 26 x 26 halo of the
+// render and the target, forms the five windowed moments (mu_x, mu_y,
+// E[x^2], E[y^2], E[xy]) with the separable 11-tap Gaussian (zero padded),
+// the SSIM map and its partials with respect to mu_x, E[x^2] and E[xy];
+// the partials go to scratch, the map and |x - y| to per-block sums.
+// Kernel 2 blurs the three partial maps again (the window is symmetric, so
+// the adjoint of the windowed sum is the same windowed sum) and writes the
+// adjoint planes of the weighted SSIM term, the weighted L1 term and their
+// sum, plus the inverse-depth adjoint.  A last one-block kernel reduces the
+// per-block sums in double.
+#include <math.h>
+
+#include "gs2d_internal.cuh"
+
+namespace gs2d {
+namespace {
+
+constexpr int kT = 16;
+constexpr int kR = 5;
+constexpr int kHalo = kT + 2 * kR;  // 26
+
+struct Gauss {
+  float w[2 * kR + 1];
+};
+
+__global__ void __launch_bounds__(kT* kT) ssim_fwd_kernel(int W, int H, const float* __restrict__ out,
+                                                          const float* __restrict__ tgt, Gauss g,
+                                                          float* __restrict__ part,
+                                                          float* __restrict__ bsum) {
+  __shared__ float sx[kHalo][kHalo], sy[kHalo][kHalo];
+  __shared__ float hm[5][kHalo][kT];
+  const int c = blockIdx.z;
+  const size_t HW = (size_t)W * H;
+  const float* X = out + c * HW;
+  const float* Y = tgt + c * HW;
+  const int ox = blockIdx.x * kT - kR, oy = blockIdx.y * kT - kR;
+  const int t = threadIdx.y * kT + threadIdx.x;
+  for (int i = t; i < kHalo * kHalo; i += kT * kT) {
+    const int hy = i / kHalo, hx = i % kHalo;
+    const int gx = ox + hx, gy = oy + hy;
+    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+    sx[hy][hx] = in ? X[(size_t)gy * W + gx] : 0.f;
+    sy[hy][hx] = in ? Y[(size_t)gy * W + gx] : 0.f;
+  }
+  __syncthreads();
+  // horizontal pass over all halo rows
+  for (int i = t; i < kHalo * kT; i += kT * kT) {
+    const int hy = i / kT, cx = i % kT;
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * kR + 1; ++k) {
+      const float a = sx[hy][cx + k], b = sy[hy][cx + k], wk = g.w[k];
+      m0 = fmaf(wk, a, m0);
+      m1 = fmaf(wk, b, m1);
+      m2 = fmaf(wk, a * a, m2);
+      m3 = fmaf(wk, b * b, m3);
+      m4 = fmaf(wk, a * b, m4);
+    }
+    hm[0][hy][cx] = m0; hm[1][hy][cx] = m1; hm[2][hy][cx] = m2; hm[3][hy][cx] = m3; hm[4][hy][cx] = m4;
+  }
+  __syncthreads();
+  const int px = blockIdx.x * kT + threadIdx.x, py = blockIdx.y * kT + threadIdx.y;
+  float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < 2 * kR + 1; ++k) {
+    const float wk = g.w[k];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) m[q] = fmaf(wk, hm[q][threadIdx.y + k][threadIdx.x], m[q]);
+  }
+  float ssim = 0.f, l1 = 0.f;
+  if (px < W && py < H) {
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    const float ux = m[0], uy = m[1];
+    const float vx = m[2] - ux * ux, vy = m[3] - uy * uy, cxy = m[4] - ux * uy;
+    const float A1 = 2.f * ux * uy + C1, A2 = 2.f * cxy + C2;
+    const float B1 = ux * ux + uy * uy + C1, B2 = vx + vy + C2;
+    const float iB = 1.f / (B1 * B2);
+    const float s = A1 * A2 * iB;
+    const float dux = 2.f * uy * A2 * iB - s * 2.f * ux / B1;
+    const float dvx = -s / B2;
+    const float dcxy = 2.f * A1 * iB;
+    const size_t pix = (size_t)py * W + px;
+    part[(0 * 3 + c) * HW + pix] = dux - 2.f * ux * dvx - uy * dcxy;
+    part[(1 * 3 + c) * HW + pix] = dvx;
+    part[(2 * 3 + c) * HW + pix] = dcxy;
+    ssim = s;
+    l1 = fabsf(sx[threadIdx.y + kR][threadIdx.x + kR] - sy[threadIdx.y + kR][threadIdx.x + kR]);
+  }
+  // block sums
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ssim += __shfl_xor_sync(0xffffffffu, ssim, o);
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+  }
+  __shared__ float ws[2][8];
+  if ((t & 31) == 0) { ws[0][t >> 5] = l1; ws[1][t >> 5] = ssim; }
+  __syncthreads();
+  if (t == 0) {
+    float a = 0.f, b = 0.f;
+    for (int i = 0; i < 8; ++i) { a += ws[0][i]; b += ws[1][i]; }
+    const size_t bi = ((size_t)c * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    bsum[2 * bi] = a;
+    bsum[2 * bi + 1] = b;
+  }
+}
+
+__global__ void __launch_bounds__(kT* kT) ssim_bwd_kernel(
+    int W, int H, const float* __restrict__ out, const float* __restrict__ tgt,
+    const float* __restrict__ tinv, Gauss g, gs_loss_weights wt, const float* __restrict__ part,
+    float* __restrict__ adj_total, float* __restrict__ adj_ssim, float* __restrict__ adj_l1,
+    float* __restrict__ dsum) {
+  __shared__ float sp[3][kHalo][kHalo];
+  __shared__ float hm[3][kHalo][kT];
+  const int c = blockIdx.z;
+  const size_t HW = (size_t)W * H;
+  const int ox = blockIdx.x * kT - kR, oy = blockIdx.y * kT - kR;
+  const int t = threadIdx.y * kT + threadIdx.x;
+  for (int i = t; i < kHalo * kHalo; i += kT * kT) {
+    const int hy = i / kHalo, hx = i % kHalo;
+    const int gx = ox + hx, gy = oy + hy;
+    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+    const size_t pix = (size_t)gy * W + gx;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sp[q][hy][hx] = in ? part[(q * 3 + c) * HW + pix] : 0.f;
+  }
+  __syncthreads();
+  for (int i = t; i < kHalo * kT; i += kT * kT) {
+    const int hy = i / kT, cx = i % kT;
+    float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * kR + 1; ++k) {
+      const float wk = g.w[k];
+      m0 = fmaf(wk, sp[0][hy][cx + k], m0);
+      m1 = fmaf(wk, sp[1][hy][cx + k], m1);
+      m2 = fmaf(wk, sp[2][hy][cx + k], m2);
+    }
+    hm[0][hy][cx] = m0; hm[1][hy][cx] = m1; hm[2][hy][cx] = m2;
+  }
+  __syncthreads();
+  const int px = blockIdx.x * kT + threadIdx.x, py = blockIdx.y * kT + threadIdx.y;
+  float dl = 0.f;
+  if (px < W && py < H) {
+    float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2 * kR + 1; ++k) {
+      const float wk = g.w[k];
+      b0 = fmaf(wk, hm[0][threadIdx.y + k][threadIdx.x], b0);
+      b1 = fmaf(wk, hm[1][threadIdx.y + k][threadIdx.x], b1);
+      b2 = fmaf(wk, hm[2][threadIdx.y + k][threadIdx.x], b2);
+    }
+    const size_t pix = (size_t)py * W + px;
+    const float x = out[c * HW + pix], y = tgt[c * HW + pix];
+    const float dssim = b0 + 2.f * x * b1 + y * b2;
+    const float inv = 1.f / (3.f * (float)HW);
+    const float as = -wt.w_ssim * dssim * inv;
+    const float d = x - y;
+    const float al = wt.w_l1 * (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * inv;
+    adj_total[c * HW + pix] = as + al;
+    if (adj_ssim) adj_ssim[c * HW + pix] = as;
+    if (adj_l1) adj_l1[c * HW + pix] = al;
+    if (c == 0 && tinv) {
+      const float e = out[5 * HW + pix] - tinv[pix];
+      dl = fabsf(e);
+      adj_total[5 * HW + pix] = wt.w_depth * (e > 0.f ? 1.f : (e < 0.f ? -1.f : 0.f)) / (float)HW;
+    }
+  }
+  if (c == 0 && dsum) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
+    __shared__ float ws[8];
+    if ((t & 31) == 0) ws[t >> 5] = dl;
+    __syncthreads();
+    if (t == 0) {
+      float a = 0.f;
+      for (int i = 0; i < 8; ++i) a += ws[i];
+      dsum[blockIdx.y * gridDim.x + blockIdx.x] = a;
+    }
+  }
+}
+
+__global__ void loss_reduce_kernel(const float* __restrict__ bsum, int nb, const float* __restrict__ dsum,
+                                   int nd, int W, int H, gs_loss_weights wt, int has_depth,
+                                   float* __restrict__ losses) {
+  __shared__ double red[3][256];
+  double a = 0.0, b = 0.0, d = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    a += bsum[2 * i];
+    b += bsum[2 * i + 1];
+  }
+  if (has_depth)
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) d += dsum[i];
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  red[2][threadIdx.x] = d;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+      red[2][threadIdx.x] += red[2][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double n3 = 3.0 * (double)W * (double)H;
+    const double l1 = red[0][0] / n3, ss = red[1][0] / n3;
+    const double ld = has_depth ? red[2][0] / ((double)W * H) : 0.0;
+    losses[0] = (float)l1;
+    losses[1] = (float)ss;
+    losses[2] = (float)ld;
+    losses[3] = (float)(wt.w_l1 * l1 + wt.w_ssim * (1.0 - ss) + wt.w_depth * ld);
+  }
+}
+
+}  // namespace
+
+size_t loss_tmp_floats(int W, int H) {
+  const size_t gx = div_up(W, kT), gy = div_up(H, kT);
+  return 9 * (size_t)W * H + 2 * 3 * gx * gy + gx * gy + 64;
+}
+
+cudaError_t launch_loss(int W, int H, const float* out, const float* tgt, const float* tinv,
+                        const gs_loss_weights& w, float* adj_total, float* adj_ssim,
+                        float* adj_l1, float* losses, float* tmp, cudaStream_t st) {
+  Gauss g;
+  double s = 0.0, e[2 * kR + 1];
+  for (int i = 0; i < 2 * kR + 1; ++i) {
+    e[i] = exp(-((i - kR) * (i - kR)) / (2.0 * 1.5 * 1.5));
+    s += e[i];
+  }
+  for (int i = 0; i < 2 * kR + 1; ++i) g.w[i] = (float)(e[i] / s);
+  const unsigned gx = div_up(W, kT), gy = div_up(H, kT);
+  float* part = tmp;
+  float* bsum = tmp + 9 * (size_t)W * H;
+  float* dsum = bsum + 2 * 3 * (size_t)gx * gy;
+  const dim3 grid(gx, gy, 3), blk(kT, kT);
+  ProfScope ps(kProfLoss, st);
+  count_launch(3);
+  ssim_fwd_kernel<<<grid, blk, 0, st>>>(W, H, out, tgt, g, part, bsum);
+  ssim_bwd_kernel<<<grid, blk, 0, st>>>(W, H, out, tgt, tinv, g, w, part, adj_total, adj_ssim,
+                                        adj_l1, dsum);
+  loss_reduce_kernel<<<1, 256, 0, st>>>(bsum, 3 * gx * gy, dsum, gx * gy, W, H, w, tinv != nullptr,
+                                        losses);
+  return cudaGetLastError();
+}
+
+}  // namespace gs2d

@@ -1,0 +1,354 @@
+// Per-surfel preprocess (forward) and its adjoint (backward).
+//
+// Forward (Sec. 3.1 surfel model; Sec. 3.2 antialiasing filter): for each
+// surfel compute the view-space frame, cull disks whose 3-sigma extent
+// reaches the near plane, the projected centre c, the centred homography
+// of the tangent plane in inverse form (Ji, e), the conservative screen
+// bounding box of {rho <= rho_max} (ellipse of the disk union the screen
+// filter disk) and its tile rectangle, SH colour and the camera-facing
+// normal.  The geometry runs in FP64 so that pixel offsets from c and the
+// inverse Jacobian of nearly edge-on disks are accurate to FP32 rounding;
+// the record the blends read is FP32 with c split into two floats.
+//
+// Backward: chains the per-surfel gradient record of the blend backward
+// (d Ji, d e, d c, d p_z, d opacity, d rgb, d normal) to the parameters,
+// in FP32, recomputing the forward intermediates.
+#include <math.h>
+
+#include "gs2d_internal.cuh"
+
+namespace gs2d {
+namespace {
+
+// Real SH basis (degree <= 3, Condon-Shortley phase), as Cartesian
+// polynomials of the unit direction (x, y, z).  Constants:
+// 1/(2 sqrt(pi)), sqrt(3/(4 pi)), sqrt(15/pi)/2, sqrt(5/pi)/4,
+// sqrt(15/pi)/4, sqrt(35/(2 pi))/4, sqrt(105/pi)/2, sqrt(21/(2 pi))/4,
+// sqrt(7/pi)/4, sqrt(105/pi)/4.
+constexpr float kY0 = 0.28209479177387814f;
+constexpr float kY1 = 0.48860251190291992f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.54627421529603959f;
+constexpr float kY3a = 0.59004358992664352f;
+constexpr float kY3b = 2.8906114426405538f;
+constexpr float kY3c = 0.45704579946446572f;
+constexpr float kY3d = 0.37317633259011546f;
+constexpr float kY3e = 1.4453057213202769f;
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, int deg, float* Y) {
+  Y[0] = kY0;
+  if (deg < 1) return;
+  Y[1] = -kY1 * y;
+  Y[2] = kY1 * z;
+  Y[3] = -kY1 * x;
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kY2a * x * y;
+  Y[5] = -kY2a * y * z;
+  Y[6] = kY2b * (2.f * zz - xx - yy);
+  Y[7] = -kY2a * x * z;
+  Y[8] = kY2c * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = -kY3a * y * (3.f * xx - yy);
+  Y[10] = kY3b * x * y * z;
+  Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+  Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+  Y[14] = kY3e * z * (xx - yy);
+  Y[15] = -kY3a * x * (xx - 3.f * yy);
+}
+
+// gradient of the polynomial basis, dY[k] = (dY/dx, dY/dy, dY/dz)
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int deg, float3* dY) {
+  dY[0] = make_float3(0.f, 0.f, 0.f);
+  if (deg < 1) return;
+  dY[1] = make_float3(0.f, -kY1, 0.f);
+  dY[2] = make_float3(0.f, 0.f, kY1);
+  dY[3] = make_float3(-kY1, 0.f, 0.f);
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  dY[4] = make_float3(kY2a * y, kY2a * x, 0.f);
+  dY[5] = make_float3(0.f, -kY2a * z, -kY2a * y);
+  dY[6] = make_float3(-2.f * kY2b * x, -2.f * kY2b * y, 4.f * kY2b * z);
+  dY[7] = make_float3(-kY2a * z, 0.f, -kY2a * x);
+  dY[8] = make_float3(2.f * kY2c * x, -2.f * kY2c * y, 0.f);
+  if (deg < 3) return;
+  dY[9] = make_float3(-kY3a * 6.f * x * y, -kY3a * (3.f * xx - 3.f * yy), 0.f);
+  dY[10] = make_float3(kY3b * y * z, kY3b * x * z, kY3b * x * y);
+  dY[11] = make_float3(kY3c * 2.f * x * y, -kY3c * (4.f * zz - xx - 3.f * yy), -kY3c * 8.f * y * z);
+  dY[12] = make_float3(-kY3d * 6.f * x * z, -kY3d * 6.f * y * z, kY3d * (6.f * zz - 3.f * xx - 3.f * yy));
+  dY[13] = make_float3(-kY3c * (4.f * zz - 3.f * xx - yy), kY3c * 2.f * x * y, -kY3c * 8.f * x * z);
+  dY[14] = make_float3(kY3e * 2.f * x * z, -kY3e * 2.f * y * z, kY3e * (xx - yy));
+  dY[15] = make_float3(-kY3a * (3.f * xx - 3.f * yy), kY3a * 6.f * x * y, 0.f);
+}
+
+template <typename T>
+struct V3 {
+  T x, y, z;
+};
+
+// Columns of the rotation of the unit quaternion (w, x, y, z).
+template <typename T>
+__device__ __forceinline__ void quat_cols(T w, T x, T y, T z, V3<T>& r1, V3<T>& r2, V3<T>& r3) {
+  r1 = {T(1) - T(2) * (y * y + z * z), T(2) * (x * y + w * z), T(2) * (x * z - w * y)};
+  r2 = {T(2) * (x * y - w * z), T(1) - T(2) * (x * x + z * z), T(2) * (y * z + w * x)};
+  r3 = {T(2) * (x * z + w * y), T(2) * (y * z - w * x), T(1) - T(2) * (x * x + y * y)};
+}
+
+template <typename T>
+__device__ __forceinline__ V3<T> rot(const double* R, V3<T> v) {
+  return {T(R[0]) * v.x + T(R[1]) * v.y + T(R[2]) * v.z,
+          T(R[3]) * v.x + T(R[4]) * v.y + T(R[5]) * v.z,
+          T(R[6]) * v.x + T(R[7]) * v.y + T(R[8]) * v.z};
+}
+template <typename T>
+__device__ __forceinline__ V3<T> rotT(const double* R, V3<T> v) {
+  return {T(R[0]) * v.x + T(R[3]) * v.y + T(R[6]) * v.z,
+          T(R[1]) * v.x + T(R[4]) * v.y + T(R[7]) * v.z,
+          T(R[2]) * v.x + T(R[5]) * v.y + T(R[8]) * v.z};
+}
+
+__global__ void __launch_bounds__(256) preprocess_kernel(ParamsDev P, CamDev cam, SetDev set,
+                                                         float4* __restrict__ rec,
+                                                         uint2* __restrict__ rect,
+                                                         uint32_t* __restrict__ tcount,
+                                                         uint32_t* __restrict__ dkey,
+                                                         uint32_t* __restrict__ idx) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= P.n) return;
+  idx[n] = (uint32_t)n;
+  uint32_t cnt = 0, key = 0xFFFFFFFFu;
+  uint2 rc = make_uint2(0u, 0u);
+  const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
+  const double qn2 = (double)qw * qw + (double)qx * qx + (double)qy * qy + (double)qz * qz;
+  if (qn2 > 0.0) {
+    const double iq = 1.0 / sqrt(qn2);
+    V3<double> r1, r2, r3;
+    quat_cols<double>(qw * iq, qx * iq, qy * iq, qz * iq, r1, r2, r3);
+    const V3<double> mu = {(double)P.mu[3 * n], (double)P.mu[3 * n + 1], (double)P.mu[3 * n + 2]};
+    V3<double> p = rot<double>(cam.R, mu);
+    p.x += cam.t[0]; p.y += cam.t[1]; p.z += cam.t[2];
+    const V3<double> tu = rot<double>(cam.R, r1), tv = rot<double>(cam.R, r2), nv = rot<double>(cam.R, r3);
+    const double su = P.scale[2 * n], sv = P.scale[2 * n + 1];
+    const V3<double> a = {su * tu.x, su * tu.y, su * tu.z}, b = {sv * tv.x, sv * tv.y, sv * tv.z};
+    const double zmin = p.z - sqrt((double)set.rho_max) * sqrt(a.z * a.z + b.z * b.z);
+    if (zmin > (double)set.near_plane) {
+      const double iz = 1.0 / p.z;
+      const double xi = p.x * iz, yi = p.y * iz;
+      const double cx = cam.fx * xi + cam.cx, cy = cam.fy * yi + cam.cy;
+      const double J11 = cam.fx * (a.x - a.z * xi) * iz, J12 = cam.fx * (b.x - b.z * xi) * iz;
+      const double J21 = cam.fy * (a.y - a.z * yi) * iz, J22 = cam.fy * (b.y - b.z * yi) * iz;
+      const double w1 = a.z * iz, w2 = b.z * iz;
+      const double det = J11 * J22 - J12 * J21;
+      float4 r1f;
+      float2 ef;
+      if (det != 0.0) {
+        const double id = 1.0 / det;
+        const double i11 = J22 * id, i12 = -J12 * id, i21 = -J21 * id, i22 = J11 * id;
+        r1f = make_float4((float)i11, (float)i12, (float)i21, (float)i22);
+        ef = make_float2((float)(-(i11 * w1 + i21 * w2)), (float)(-(i12 * w1 + i22 * w2)));
+      } else {
+        // edge-on disk: no object-space footprint (rho_obj is NaN, the
+        // screen filter decides)
+        const float qnan = __int_as_float(0x7fffffff);
+        r1f = make_float4(qnan, qnan, qnan, qnan);
+        ef = make_float2(0.f, 0.f);
+      }
+      // bounding box of {rho_obj <= rho_max} in offsets from c: dual conic
+      // of the centred homography H = [[J, 0], [w^T, 1]]
+      const double rm = set.rho_max;
+      const double C11 = rm * (J11 * J11 + J12 * J12), C22 = rm * (J21 * J21 + J22 * J22);
+      const double C13 = rm * (J11 * w1 + J12 * w2), C23 = rm * (J21 * w1 + J22 * w2);
+      const double C33 = rm * (w1 * w1 + w2 * w2) - 1.0;
+      const double ex = sqrt(fmax(C13 * C13 - C11 * C33, 0.0));
+      const double ey = sqrt(fmax(C23 * C23 - C22 * C33, 0.0));
+      const double rf = sqrt((double)set.rho_max / (double)set.sinv);
+      const double x0 = (C13 - ex) / C33, x1 = (C13 + ex) / C33;
+      const double y0 = (C23 - ey) / C33, y1 = (C23 + ey) / C33;
+      const double xmin = cx + fmin(fmin(x0, x1), -rf), xmax = cx + fmax(fmax(x0, x1), rf);
+      const double ymin = cy + fmin(fmin(y0, y1), -rf), ymax = cy + fmax(fmax(y0, y1), rf);
+      double ilo = ceil(xmin - 0.5), ihi = floor(xmax - 0.5);
+      double jlo = ceil(ymin - 0.5), jhi = floor(ymax - 0.5);
+      ilo = fmax(ilo, 0.0); jlo = fmax(jlo, 0.0);
+      ihi = fmin(ihi, (double)(cam.W - 1)); jhi = fmin(jhi, (double)(cam.H - 1));
+      if (ilo <= ihi && jlo <= jhi) {
+        const int tx0 = (int)ilo / kTile, tx1 = (int)ihi / kTile + 1;
+        const int ty0 = (int)jlo / kTile, ty1 = (int)jhi / kTile + 1;
+        rc = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+        cnt = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
+        const float pz = (float)p.z;
+        key = __float_as_uint(pz);
+        // colour: SH at the world direction from the camera centre
+        double dx = mu.x - cam.campos[0], dy = mu.y - cam.campos[1], dz = mu.z - cam.campos[2];
+        const double il = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+        float Y[16];
+        sh_basis((float)(dx * il), (float)(dy * il), (float)(dz * il), P.sh_degree, Y);
+        const int K = (P.sh_degree + 1) * (P.sh_degree + 1);
+        const float* f = P.sh + (size_t)n * K * 3;
+        float col[3];
+        for (int c = 0; c < 3; ++c) {
+          float acc = 0.f;
+          for (int k = 0; k < K; ++k) acc = fmaf(f[k * 3 + c], Y[k], acc);
+          col[c] = fmaxf(acc + 0.5f, 0.f);
+        }
+        const double s = (nv.x * p.x + nv.y * p.y + nv.z * p.z) > 0.0 ? -1.0 : 1.0;
+        const float chx = (float)cx, chy = (float)cy;
+        float4* R = rec + (size_t)n * kRecF4;
+        R[0] = make_float4(chx, chy, (float)(cx - (double)chx), (float)(cy - (double)chy));
+        R[1] = r1f;
+        R[2] = make_float4(ef.x, ef.y, pz, P.opacity[n]);
+        R[3] = make_float4(col[0], col[1], col[2], (float)(s * nv.x));
+        R[4] = make_float4((float)(s * nv.y), (float)(s * nv.z), 0.f, 0.f);
+      }
+    }
+  }
+  rect[n] = rc;
+  tcount[n] = cnt;
+  dkey[n] = key;
+}
+
+// ---------------------------------------------------------------------------
+// Backward.
+
+__global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev cam,
+                                                             const uint32_t* __restrict__ tcount,
+                                                             const float* __restrict__ grec,
+                                                             gs_param_grads G) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= P.n || tcount[n] == 0) return;
+  const float* g = grec + (size_t)n * kGradRec;
+  float gJi11 = g[0], gJi12 = g[1], gJi21 = g[2], gJi22 = g[3];
+  const float ge1 = g[4], ge2 = g[5], gcx = g[6], gcy = g[7], gpz0 = g[8], gop = g[9];
+  const float grgb[3] = {g[10], g[11], g[12]};
+  const V3<float> gnrm = {g[13], g[14], g[15]};
+  // forward intermediates, FP32
+  const float qw0 = P.quat[4 * n], qx0 = P.quat[4 * n + 1], qy0 = P.quat[4 * n + 2], qz0 = P.quat[4 * n + 3];
+  const float qn = sqrtf(qw0 * qw0 + qx0 * qx0 + qy0 * qy0 + qz0 * qz0);
+  const float iqn = 1.f / qn;
+  const float qw = qw0 * iqn, qx = qx0 * iqn, qy = qy0 * iqn, qz = qz0 * iqn;
+  V3<float> r1, r2, r3;
+  quat_cols<float>(qw, qx, qy, qz, r1, r2, r3);
+  const V3<float> mu = {P.mu[3 * n], P.mu[3 * n + 1], P.mu[3 * n + 2]};
+  V3<float> p = rot<float>(cam.R, mu);
+  p.x += (float)cam.t[0]; p.y += (float)cam.t[1]; p.z += (float)cam.t[2];
+  const V3<float> tu = rot<float>(cam.R, r1), tv = rot<float>(cam.R, r2), nv = rot<float>(cam.R, r3);
+  const float su = P.scale[2 * n], sv = P.scale[2 * n + 1];
+  const V3<float> a = {su * tu.x, su * tu.y, su * tu.z}, b = {sv * tv.x, sv * tv.y, sv * tv.z};
+  const float fx = (float)cam.fx, fy = (float)cam.fy;
+  const float iz = 1.f / p.z;
+  const float xi = p.x * iz, yi = p.y * iz;
+  const float J11 = fx * (a.x - a.z * xi) * iz, J12 = fx * (b.x - b.z * xi) * iz;
+  const float J21 = fy * (a.y - a.z * yi) * iz, J22 = fy * (b.y - b.z * yi) * iz;
+  const float w1 = a.z * iz, w2 = b.z * iz;
+  const float det = J11 * J22 - J12 * J21;
+  float gJ11 = 0.f, gJ12 = 0.f, gJ21 = 0.f, gJ22 = 0.f, gw1 = 0.f, gw2 = 0.f;
+  if (det != 0.f) {
+    const float id = 1.f / det;
+    const float i11 = J22 * id, i12 = -J12 * id, i21 = -J21 * id, i22 = J11 * id;
+    // e = -Ji^T w
+    gJi11 -= w1 * ge1; gJi12 -= w1 * ge2; gJi21 -= w2 * ge1; gJi22 -= w2 * ge2;
+    gw1 = -(i11 * ge1 + i12 * ge2);
+    gw2 = -(i21 * ge1 + i22 * ge2);
+    // Ji = J^-1:  dJ = -Ji^T dJi Ji^T
+    const float m11 = gJi11 * i11 + gJi12 * i12, m12 = gJi11 * i21 + gJi12 * i22;
+    const float m21 = gJi21 * i11 + gJi22 * i12, m22 = gJi21 * i21 + gJi22 * i22;
+    gJ11 = -(i11 * m11 + i21 * m21);
+    gJ12 = -(i11 * m12 + i21 * m22);
+    gJ21 = -(i12 * m11 + i22 * m21);
+    gJ22 = -(i12 * m12 + i22 * m22);
+  }
+  // J_1k = fx (g_x - g_z xi) / p_z, J_2k = fy (g_y - g_z yi) / p_z, w_k = g_z / p_z
+  const V3<float> ga = {fx * gJ11 * iz, fy * gJ21 * iz, (-fx * xi * gJ11 - fy * yi * gJ21 + gw1) * iz};
+  const V3<float> gb = {fx * gJ12 * iz, fy * gJ22 * iz, (-fx * xi * gJ12 - fy * yi * gJ22 + gw2) * iz};
+  const float gxi = -fx * (a.z * gJ11 + b.z * gJ12) * iz + fx * gcx;
+  const float gyi = -fy * (a.z * gJ21 + b.z * gJ22) * iz + fy * gcy;
+  float gpz = gpz0 - (J11 * gJ11 + J12 * gJ12 + J21 * gJ21 + J22 * gJ22) * iz - (w1 * gw1 + w2 * gw2) * iz;
+  const V3<float> gp = {gxi * iz, gyi * iz, gpz - (xi * gxi + yi * gyi) * iz};
+  V3<float> gmu = rotT<float>(cam.R, gp);
+  const float gsu = ga.x * tu.x + ga.y * tu.y + ga.z * tu.z;
+  const float gsv = gb.x * tv.x + gb.y * tv.y + gb.z * tv.z;
+  const V3<float> gr1 = rotT<float>(cam.R, V3<float>{su * ga.x, su * ga.y, su * ga.z});
+  const V3<float> gr2 = rotT<float>(cam.R, V3<float>{sv * gb.x, sv * gb.y, sv * gb.z});
+  const float sgn = (nv.x * p.x + nv.y * p.y + nv.z * p.z) > 0.f ? -1.f : 1.f;
+  const V3<float> gr3 = rotT<float>(cam.R, V3<float>{sgn * gnrm.x, sgn * gnrm.y, sgn * gnrm.z});
+  // colour
+  const V3<float> dd = {mu.x - (float)cam.campos[0], mu.y - (float)cam.campos[1], mu.z - (float)cam.campos[2]};
+  const float dl = sqrtf(dd.x * dd.x + dd.y * dd.y + dd.z * dd.z);
+  const float il = 1.f / dl;
+  const float dx = dd.x * il, dy = dd.y * il, dz = dd.z * il;
+  const int deg = P.sh_degree;
+  const int K = (deg + 1) * (deg + 1);
+  float Y[16];
+  float3 dY[16];
+  sh_basis(dx, dy, dz, deg, Y);
+  sh_basis_grad(dx, dy, dz, deg, dY);
+  const float* f = P.sh + (size_t)n * K * 3;
+  V3<float> gdir = {0.f, 0.f, 0.f};
+  for (int c = 0; c < 3; ++c) {
+    float acc = 0.f;
+    for (int k = 0; k < K; ++k) acc = fmaf(f[k * 3 + c], Y[k], acc);
+    if (!(acc + 0.5f > 0.f) || grgb[c] == 0.f) continue;  // clamped colour: no gradient
+    const float gc = grgb[c];
+    for (int k = 0; k < K; ++k) {
+      if (G.sh) G.sh[((size_t)n * K + k) * 3 + c] += gc * Y[k];
+      const float fk = f[k * 3 + c] * gc;
+      gdir.x += fk * dY[k].x; gdir.y += fk * dY[k].y; gdir.z += fk * dY[k].z;
+    }
+  }
+  const float gdd = dx * gdir.x + dy * gdir.y + dz * gdir.z;
+  gmu.x += (gdir.x - dx * gdd) * il;
+  gmu.y += (gdir.y - dy * gdd) * il;
+  gmu.z += (gdir.z - dz * gdd) * il;
+  // rotation: dL/dR with columns gr1, gr2, gr3 -> unit quaternion
+  const float R00 = gr1.x, R10 = gr1.y, R20 = gr1.z;
+  const float R01 = gr2.x, R11 = gr2.y, R21 = gr2.z;
+  const float R02 = gr3.x, R12 = gr3.y, R22 = gr3.z;
+  const float dqw = 2.f * (-qz * R01 + qy * R02 + qz * R10 - qx * R12 - qy * R20 + qx * R21);
+  const float dqx = 2.f * (qy * R01 + qz * R02 + qy * R10 - 2.f * qx * R11 - qw * R12 + qz * R20 +
+                           qw * R21 - 2.f * qx * R22);
+  const float dqy = 2.f * (-2.f * qy * R00 + qx * R01 + qw * R02 + qx * R10 + qz * R12 - qw * R20 +
+                           qz * R21 - 2.f * qy * R22);
+  const float dqz = 2.f * (-2.f * qz * R00 - qw * R01 + qx * R02 + qw * R10 - 2.f * qz * R11 +
+                           qy * R12 + qx * R20 + qy * R21);
+  const float qd = qw * dqw + qx * dqx + qy * dqy + qz * dqz;
+  if (G.quat) {
+    G.quat[4 * n] += (dqw - qw * qd) * iqn;
+    G.quat[4 * n + 1] += (dqx - qx * qd) * iqn;
+    G.quat[4 * n + 2] += (dqy - qy * qd) * iqn;
+    G.quat[4 * n + 3] += (dqz - qz * qd) * iqn;
+  }
+  if (G.mu) {
+    G.mu[3 * n] += gmu.x;
+    G.mu[3 * n + 1] += gmu.y;
+    G.mu[3 * n + 2] += gmu.z;
+  }
+  if (G.scale) {
+    G.scale[2 * n] += gsu;
+    G.scale[2 * n + 1] += gsv;
+  }
+  if (G.opacity) G.opacity[n] += gop;
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
+                              float4* rec, uint2* rect, uint32_t* tcount, uint32_t* dkey,
+                              uint32_t* idx, cudaStream_t st) {
+  if (P.n == 0) return cudaSuccess;
+  ProfScope ps(kProfPreprocess, st);
+  preprocess_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, set, rec, rect, tcount, dkey, idx);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_bwd(const ParamsDev& P, const CamDev& cam, const uint32_t* tcount,
+                                  const float* grec, const gs_param_grads& G, cudaStream_t st) {
+  if (P.n == 0) return cudaSuccess;
+  ProfScope ps(kProfPreprocessBwd, st);
+  preprocess_bwd_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, tcount, grec, G);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace gs2d

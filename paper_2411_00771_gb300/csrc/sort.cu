@@ -1,0 +1,303 @@
+// Tile binning and ordering: device-wide scan, key emission, stable LSD
+// radix sort of (key, value) pairs and per-tile ranges.
+//
+// The compositing order (Eq. 1 composites front to back) is (tile, centre
+// depth, surfel index).  It is produced in two levels with the same result
+// as one sort of 64-bit (tile << 32 | depth bits) keys: the surfels are
+// sorted once by depth (32-bit keys, stable, so ties keep index order), the
+// (tile, surfel) instances are emitted in that order, and a stable sort by
+// tile id alone (13-16 bits) groups them per tile.
+#include "gs2d_internal.cuh"
+
+namespace gs2d {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTileItems = kThreads * kItems;  // 4096 items per block
+constexpr int kWarps = kThreads / 32;
+constexpr int kRadixBits = 8;
+constexpr int kBins = 1 << kRadixBits;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive block scan of one value per thread (256 threads).  Returns the
+// exclusive prefix; *total receives the block sum.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t ws[kWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t x = lane < kWarps ? ws[lane] : 0u;
+    const uint32_t xi = warp_incl_scan(x);
+    if (lane < kWarps) ws[lane] = xi - x;
+    if (lane == kWarps - 1) *total = xi;
+  }
+  __syncthreads();
+  const uint32_t r = ws[w] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kThreads) scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+                                                        uint32_t* __restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kTileItems;
+  uint32_t s = 0;
+  for (int i = threadIdx.x; i < kTileItems; i += kThreads) {
+    const int64_t k = base + i;
+    if (k < n) s += in[k];
+  }
+  __shared__ uint32_t tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of nb block sums in place; total to *total.
+__global__ void __launch_bounds__(kThreads) scan_sums(uint32_t* __restrict__ sums, int nb,
+                                                      uint32_t* __restrict__ total) {
+  __shared__ uint32_t tot;
+  uint32_t carry = 0;
+  for (int base = 0; base < nb; base += kThreads * kItems) {
+    // each thread owns kItems consecutive entries of this chunk
+    uint32_t v[kItems];
+    uint32_t s = 0;
+    const int t0 = base + threadIdx.x * kItems;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      v[i] = (t0 + i < nb) ? sums[t0 + i] : 0u;
+      s += v[i];
+    }
+    uint32_t pre = block_excl_scan(s, &tot) + carry;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      if (t0 + i < nb) sums[t0 + i] = pre;
+      pre += v[i];
+    }
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) scan_down(const uint32_t* __restrict__ in,
+                                                      uint32_t* __restrict__ out, int64_t n,
+                                                      const uint32_t* __restrict__ sums) {
+  __shared__ uint32_t tile[kTileItems];
+  const int64_t base = (int64_t)blockIdx.x * kTileItems;
+  // coalesced load into shared memory, then each thread scans kItems
+  // consecutive entries
+  for (int i = threadIdx.x; i < kTileItems; i += kThreads) {
+    const int64_t k = base + i;
+    tile[i] = k < n ? in[k] : 0u;
+  }
+  __syncthreads();
+  uint32_t v[kItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    v[i] = tile[threadIdx.x * kItems + i];
+    s += v[i];
+  }
+  __shared__ uint32_t tot;
+  uint32_t pre = block_excl_scan(s, &tot) + sums[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    tile[threadIdx.x * kItems + i] = pre;
+    pre += v[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kTileItems; i += kThreads) {
+    const int64_t k = base + i;
+    if (k < n) out[k] = tile[i];
+  }
+}
+
+// ---- radix sort -----------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __restrict__ keys,
+                                                          int64_t n, int shift, int nbins,
+                                                          uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kBins];
+  for (int i = threadIdx.x; i < kBins; i += kThreads) h[i] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kTileItems + w * (32 * kItems);
+  const uint32_t mask = (uint32_t)nbins - 1u;
+#pragma unroll 4
+  for (int it = 0; it < kItems; ++it) {
+    const int64_t k = base + it * 32 + lane;
+    const bool valid = k < n;
+    const uint32_t d = valid ? ((keys[k] >> shift) & mask) : 0x100u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (valid && lane == (31 - __clz(peers))) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < nbins; d += kThreads) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
+}
+
+__global__ void __launch_bounds__(kThreads) radix_downsweep(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, int64_t n, int shift, int nbins, const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t wh[kWarps][kBins];
+  for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) (&wh[0][0])[i] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * kTileItems + w * (32 * kItems);
+  const uint32_t mask = (uint32_t)nbins - 1u;
+  uint32_t kk[kItems], vv[kItems], pos[kItems];
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int64_t k = base + it * 32 + lane;
+    const bool valid = k < n;
+    kk[it] = valid ? kin[k] : 0u;
+    vv[it] = valid ? vin[k] : 0u;
+    const uint32_t d = valid ? ((kk[it] >> shift) & mask) : 0x100u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t cur = 0u;
+    if (valid) cur = wh[w][d];
+    __syncwarp();
+    if (valid && lane == (31 - __clz(peers))) wh[w][d] = cur + (uint32_t)__popc(peers);
+    __syncwarp();
+    pos[it] = valid ? cur + (uint32_t)__popc(peers & lt) : 0xFFFFFFFFu;
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < nbins; d += kThreads) {
+    uint32_t run = offs[(int64_t)d * gridDim.x + blockIdx.x];
+#pragma unroll
+    for (int ww = 0; ww < kWarps; ++ww) {
+      const uint32_t t = wh[ww][d];
+      wh[ww][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    if (pos[it] == 0xFFFFFFFFu) continue;
+    const uint32_t d = (kk[it] >> shift) & mask;
+    const uint32_t dst = wh[w][d] + pos[it];
+    kout[dst] = kk[it];
+    vout[dst] = vv[it];
+  }
+}
+
+__global__ void gather_counts_kernel(const uint32_t* __restrict__ order,
+                                     const uint32_t* __restrict__ tcount, uint32_t* __restrict__ out,
+                                     int64_t n) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) out[r] = tcount[order[r]];
+}
+
+__global__ void emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offs,
+                            const uint2* __restrict__ rect, int64_t n, int tiles_x,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint32_t s = order[r];
+  const uint2 rc = rect[s];
+  const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  uint32_t o = offs[r];
+  for (int ty = ty0; ty < ty1; ++ty)
+    for (int tx = tx0; tx < tx1; ++tx) {
+      keys[o] = (uint32_t)(ty * tiles_x + tx);
+      vals[o] = s;
+      ++o;
+    }
+}
+
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t K, int2* __restrict__ ranges) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= K) return;
+  const uint32_t t = keys[i];
+  if (i == 0 || keys[i - 1] != t) ranges[t].x = (int)i;
+  if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (int)(i + 1);
+}
+
+}  // namespace
+
+size_t scan_tmp_words(int64_t n) { return (size_t)div_up(n > 0 ? n : 1, kTileItems) + 1; }
+
+cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
+                        uint32_t* tmp, cudaStream_t st) {
+  if (n <= 0) {
+    return total_dev ? cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), st) : cudaSuccess;
+  }
+  const unsigned nb = div_up(n, kTileItems);
+  count_launch(3);
+  scan_reduce<<<nb, kThreads, 0, st>>>(in, n, tmp);
+  scan_sums<<<1, kThreads, 0, st>>>(tmp, (int)nb, total_dev);
+  scan_down<<<nb, kThreads, 0, st>>>(in, out, n, tmp);
+  return cudaGetLastError();
+}
+
+size_t radix_tmp_words(int64_t n) {
+  const size_t nb = div_up(n > 0 ? n : 1, kTileItems);
+  const size_t h = nb * kBins;
+  return 2 * h + scan_tmp_words((int64_t)h) + 1;
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                             uint32_t* vals_alt, int64_t n, int bits, uint32_t* tmp,
+                             uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st) {
+  *keys_out = keys;
+  *vals_out = vals;
+  if (n <= 1 || bits <= 0) return cudaSuccess;
+  const unsigned nb = div_up(n, kTileItems);
+  const size_t h = (size_t)nb * kBins;
+  uint32_t* hist = tmp;
+  uint32_t* offs = tmp + h;
+  uint32_t* stmp = tmp + 2 * h;
+  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+  for (int shift = 0; shift < bits; shift += kRadixBits) {
+    const int pb = bits - shift < kRadixBits ? bits - shift : kRadixBits;
+    const int nbins = 1 << pb;
+    count_launch(2);
+    radix_upsweep<<<nb, kThreads, 0, st>>>(ki, n, shift, nbins, hist);
+    cudaError_t e = launch_scan(hist, offs, (int64_t)nbins * nb, nullptr, stmp, st);
+    if (e != cudaSuccess) return e;
+    radix_downsweep<<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, shift, nbins, offs);
+    uint32_t* t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+  }
+  *keys_out = ki;
+  *vals_out = vi;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* tcount, uint32_t* out,
+                                 int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  gather_counts_kernel<<<div_up(n, 256), 256, 0, st>>>(order, tcount, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint2* rect,
+                        int64_t n, int tiles_x, uint32_t* keys, uint32_t* vals, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  emit_kernel<<<div_up(n, 256), 256, 0, st>>>(order, offs, rect, n, tiles_x, keys, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint32_t* keys, int64_t K, int2* ranges, int ntiles,
+                          cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)ntiles, st);
+  if (e != cudaSuccess || K <= 0) return e;
+  count_launch();
+  ranges_kernel<<<div_up(K, 256), 256, 0, st>>>(keys, K, ranges);
+  return cudaGetLastError();
+}
+
+}  // namespace gs2d

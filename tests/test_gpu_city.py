@@ -1,0 +1,97 @@
+"""GPU parity at full size: the aerial city block (1M surfels, SH degree 3,
+1600x900) in the launch configuration the benchmark times, against the FP64
+oracle over every pixel and every surfel."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2411_00771_gb300 import synthetic as syn
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+FLAG_ANY = oracle.FLAG_ALPHA | oracle.FLAG_RHO | oracle.FLAG_TSTOP | oracle.FLAG_MEDIAN
+
+
+@pytest.fixture(scope="module")
+def city():
+    scene, info = syn.city_scene(n=1_000_000)
+    cam = syn.aerial_camera()
+    tgt, tinv = syn.city_targets(info, cam)
+    return scene, cam, tgt, tinv
+
+
+def test_city_render_matches_oracle(city):
+    scene, cam, _, _ = city
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
+    ref = oracle.render(scene, cam)
+    bad = (ref["flags"] & FLAG_ANY) != 0
+    assert bad.mean() < 0.01, bad.sum()
+    ok = ~bad
+    branch = (ref["flags"] & oracle.FLAG_BRANCH) != 0
+    g = out.cpu().numpy()
+    err = gu.channel_errors(g, ref["out"], ok)
+    err_nb = gu.channel_errors(g, ref["out"], ok & ~branch)
+    for p, name in enumerate(gu.PLANES):
+        e = err_nb[p] if p in gu.DEPTH_PLANES else err[p]
+        assert e <= gu.TOL_ABS, (name, e)
+    c = cnt.cpu().numpy()
+    assert np.array_equal(c[ok], ref["count"][ok])
+    info = frame.info()
+    pre = oracle.preprocess(scene, cam)
+    assert info["n_visible"] == int((pre["tiles"] > 0).sum())
+    assert info["n_instances"] == int(pre["tiles"].sum())
+
+
+def test_city_backward_matches_oracle(city):
+    scene, cam, _, _ = city
+    H, W = cam["height"], cam["width"]
+    rng = np.random.default_rng(11)
+    adj = (rng.normal(size=(1, 11, H, W)) * 1e-3).astype(np.float32)
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
+    n = scene["mu"].shape[0]
+    grads = {k: torch.zeros_like(v) for k, v in d.items()}
+    screen = torch.zeros((1, n, 2), device="cuda")
+    sc.backward(frame, [torch.from_numpy(adj[0]).cuda()], [0x7FF], grads, screen)
+    torch.cuda.synchronize()
+    ref = oracle.backward(scene, cam, adj.astype(np.float64))
+    for k in ("mu", "quat", "scale", "opacity", "sh"):
+        e = gu.rel_err(grads[k].cpu().numpy(), ref[k].reshape(grads[k].shape))
+        assert e <= 1e-3, (k, e)
+    assert gu.rel_err(screen.cpu().numpy()[0], ref["screen"][0]) <= 1e-3
+
+
+def test_city_loss_and_densify(city):
+    from paper_2411_00771_gb300 import binding as B
+    scene, cam, tgt, tinv = city
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
+    w = (0.8, 0.2, 0.5)
+    H, W = cam["height"], cam["width"]
+    adj_s = torch.zeros((11, H, W), device="cuda")
+    adj_l = torch.zeros((11, H, W), device="cuda")
+    losses, adj_t, _, _ = B.loss(out, torch.from_numpy(tgt).cuda(), torch.from_numpy(tinv).cuda(), w,
+                                 adj_ssim=adj_s, adj_l1=adj_l)
+    n = scene["mu"].shape[0]
+    grads = {k: torch.zeros_like(v) for k, v in d.items()}
+    screen = torch.zeros((3, n, 2), device="cuda")
+    sc.backward(frame, [adj_t, adj_s, adj_l], [0x27, 0x7, 0x7], grads, screen)
+    stats = torch.zeros((n, 4), device="cuda")
+    sc.densify_accumulate(frame, screen, stats)
+    mask, g, k = B.densify_select(stats, d["scale"], 0.9, 0.0002, 0.1)
+    torch.cuda.synchronize()
+    r = oracle.render(scene, cam)
+    L = oracle.loss(r["out"], tgt, tinv, w)
+    l = losses.cpu().numpy()
+    assert abs(l[3] - L["total"]) <= 1e-5 * max(1.0, L["total"])
+    ref = oracle.backward(scene, cam, L["adj"])
+    for k_ in ("mu", "opacity", "sh"):
+        assert gu.rel_err(grads[k_].cpu().numpy(), ref[k_].reshape(grads[k_].shape)) <= 2e-3, k_
+    pre = oracle.preprocess(scene, cam)
+    st = oracle.densify_accumulate(ref["screen"], pre["tiles"] > 0)
+    assert gu.rel_err(stats.cpu().numpy(), st) <= 2e-3
+    m, gg, kk = oracle.densify_select(st, scene["scale"], 0.9, 0.0002, 0.1)
+    assert abs(float(k[0]) - kk) <= 2e-3 * kk
+    gm = g.cpu().numpy()
+    close = np.abs(gg - 0.0002) <= 2e-3 * 0.0002
+    assert (mask.cpu().numpy()[~close] != m[~close]).mean() < 1e-3

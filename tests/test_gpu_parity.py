@@ -1,0 +1,289 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bar (per the definitions in the oracle): tile rectangles, sorted tile lists
+and ranges bit-exact; per-pixel contributor counts bit-exact outside
+flagged pixels; channels within 2e-5 (scaled by |value| above 1);
+gradients within 1e-3 relative.  Flagged pixels are those where the
+oracle saw a decision taken within a hair of a threshold (alpha cutoff,
+3-sigma support, transmittance stop, median pivot); their number is
+reported and bounded.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2411_00771_gb300 import synthetic as syn
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+# pixels whose object/screen branch choice is within a hair are excluded
+# only from the depth-like planes
+FLAG_ANY = oracle.FLAG_ALPHA | oracle.FLAG_RHO | oracle.FLAG_TSTOP | oracle.FLAG_MEDIAN
+
+
+def _flags_ok(flags, frac=0.01):
+    bad = (flags & FLAG_ANY) != 0
+    assert bad.mean() <= frac, f"{bad.sum()} flagged pixels"
+    return ~bad
+
+
+def _compare_render(scene, cam, settings=None, frac=0.01, tol=gu.TOL_ABS):
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam, settings)
+    ref = oracle.render(scene, cam, settings=settings)
+    ok = _flags_ok(ref["flags"], frac)
+    g = out.cpu().numpy()
+    err = gu.channel_errors(g, ref["out"], ok)
+    branch = (ref["flags"] & oracle.FLAG_BRANCH) != 0
+    err_nb = gu.channel_errors(g, ref["out"], ok & ~branch)
+    for p, name in enumerate(gu.PLANES):
+        e = err_nb[p] if p in gu.DEPTH_PLANES else err[p]
+        assert e <= tol, f"plane {name}: max scaled error {e:.3e}"
+    c = cnt.cpu().numpy()
+    assert np.array_equal(c[ok], ref["count"][ok])
+    return sc, d, out, cnt, frame, ref
+
+
+def test_tiny_scene_render_matches_oracle():
+    scene, cam, _, _ = syn.tiny_scene()
+    _compare_render(scene, cam)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2, 3])
+def test_ragged_image_all_sh_degrees(deg):
+    scene, cam, _, _ = syn.tiny_scene(seed=40 + deg, n=1500, width=100, height=75, fx=90.0,
+                                      sh_degree=deg, log_scale_range=(-4.5, -1.5))
+    _compare_render(scene, cam)
+
+
+def test_background_and_transparent_surfels():
+    scene, cam, _, _ = syn.tiny_scene(seed=3, n=400, width=37, height=29, fx=40.0)
+    scene["opacity"][::3] = 0.0
+    _compare_render(scene, cam, settings=dict(bg=(0.2, 0.4, 0.6)))
+
+
+def test_empty_and_offscreen_scenes():
+    cam = syn.identity_camera(33, 17, 30.0)
+    empty = dict(mu=np.zeros((0, 3), np.float32), quat=np.zeros((0, 4), np.float32),
+                 scale=np.zeros((0, 2), np.float32), opacity=np.zeros(0, np.float32),
+                 sh=np.zeros((0, 1, 3), np.float32), sh_degree=0)
+    sc, d, out, cnt, frame = gu.gpu_render(empty, cam)
+    o = out.cpu().numpy()
+    assert np.all(o[11] == 1.0) and np.all(o[:11] == 0.0) and int(cnt.sum()) == 0
+    assert frame.info()["n_instances"] == 0
+    # everything behind the camera or off to the side
+    scene, _, _, _ = syn.tiny_scene(seed=9, n=300)
+    scene["mu"][:150, 2] = -3.0
+    scene["mu"][150:, 0] = 50.0
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
+    assert int(cnt.sum()) == 0 and frame.info()["n_instances"] == 0
+
+
+def test_single_pixel_and_narrow_images():
+    for (W, H) in [(1, 1), (1, 40), (40, 1), (17, 16)]:
+        scene, cam, _, _ = syn.tiny_scene(seed=W * 100 + H, n=200, width=W, height=H, fx=20.0)
+        _compare_render(scene, cam, frac=0.2)
+
+
+def test_large_splats_cover_many_tiles():
+    scene, cam, _, _ = syn.tiny_scene(seed=12, n=60, width=160, height=128, fx=128.0,
+                                      log_scale_range=(-1.0, 0.0))
+    _compare_render(scene, cam)
+
+
+def test_tile_rects_lists_and_ranges_bit_exact():
+    scene, cam, _, _ = syn.tiny_scene(seed=21, n=3000, width=200, height=120, fx=150.0,
+                                      log_scale_range=(-4.0, -1.5))
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
+    vals, ranges, rects = [t.cpu().numpy() for t in frame.lists()]
+    pre = oracle.preprocess(scene, cam)
+    # rectangles: exact except where the FP64 box edge sits within 1e-3 px of
+    # a pixel-centre boundary
+    live = pre["live"] > 0
+    exp_rect = np.where(live[:, None], pre["rect"], 0)
+    exp_rect = np.where((pre["tiles"] > 0)[:, None], exp_rect, 0)
+    bb = pre["bbox"]
+    near = np.any(np.abs((bb - 0.5) - np.round(bb - 0.5)) < 1e-3, axis=1)
+    diff = np.any(rects != exp_rect, axis=1)
+    assert np.all(~diff | near), np.nonzero(diff & ~near)[0][:10]
+    assert diff.sum() == 0
+    # tile lists rebuilt from the GPU rectangles and the centre depth rounded
+    # to FP32 (the compositing order key), ties by surfel index
+    tx = (cam["width"] + 15) // 16
+    ntiles = ranges.shape[0]
+    lists = [[] for _ in range(ntiles)]
+    order = np.lexsort((np.arange(len(pre["zkey"])), pre["zkey"]))
+    for s in order:
+        r = rects[s]
+        if r[2] <= r[0] or r[3] <= r[1]:
+            continue
+        for ty in range(r[1], r[3]):
+            for tx_ in range(r[0], r[2]):
+                lists[ty * tx + tx_].append(s)
+    pos = 0
+    for t in range(ntiles):
+        L = np.asarray(lists[t], np.int32)
+        if len(L) == 0:
+            assert ranges[t, 1] - ranges[t, 0] == 0
+            continue
+        assert ranges[t, 0] == pos and ranges[t, 1] == pos + len(L), t
+        assert np.array_equal(vals[pos:pos + len(L)], L), t
+        pos += len(L)
+    assert pos == len(vals)
+
+
+def _synthetic_render_planes(rng, H, W):
+    out = np.zeros((12, H, W), np.float32)
+    out[0:3] = rng.uniform(0, 1, (3, H, W))
+    out[5] = rng.uniform(0.1, 0.6, (H, W))
+    return out
+
+
+def test_loss_and_adjoints_match_oracle():
+    from paper_2411_00771_gb300 import binding as B
+    rng = np.random.default_rng(5)
+    for (H, W) in [(45, 67), (16, 16), (128, 128)]:
+        out = _synthetic_render_planes(rng, H, W)
+        tgt = rng.uniform(0, 1, (3, H, W)).astype(np.float32)
+        tinv = rng.uniform(0.1, 0.6, (H, W)).astype(np.float32)
+        w = (0.8, 0.2, 0.5)
+        ref = oracle.loss(out, tgt, tinv, w)
+        dt = lambda a: torch.from_numpy(a).cuda()
+        adj_s = torch.zeros((11, H, W), device="cuda")
+        adj_l = torch.zeros((11, H, W), device="cuda")
+        losses, adj_t, _, _ = B.loss(dt(out), dt(tgt), dt(tinv), w, adj_ssim=adj_s, adj_l1=adj_l)
+        l = losses.cpu().numpy()
+        assert abs(l[0] - ref["l1"]) < 1e-6 and abs(l[1] - ref["ssim"]) < 1e-5
+        assert abs(l[2] - ref["depth"]) < 1e-6 and abs(l[3] - ref["total"]) < 1e-5
+        for got, exp in [(adj_t, ref["adj"][0]), (adj_s, ref["adj"][1]), (adj_l, ref["adj"][2])]:
+            g = got.cpu().numpy()
+            scale = np.abs(exp).max()
+            assert np.abs(g - exp).max() <= 1e-4 * scale
+
+
+def _backward_case(scene, cam, adj, masks, settings=None):
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam, settings)
+    n = scene["mu"].shape[0]
+    grads = {k: torch.zeros_like(v) for k, v in d.items()}
+    S = adj.shape[0]
+    screen = torch.zeros((S, n, 2), device="cuda")
+    adj_t = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda() for a in adj]
+    sc.backward(frame, adj_t, masks, grads, screen)
+    torch.cuda.synchronize()
+    ref = oracle.backward(scene, cam, adj, settings=settings)
+    return grads, screen, ref, frame
+
+
+def _assert_grads(grads, screen, ref, tol=1e-3):
+    for k in ("mu", "quat", "scale", "opacity", "sh"):
+        g = grads[k].cpu().numpy().astype(np.float64)
+        r = ref[k].reshape(g.shape)
+        assert gu.rel_err(g, r) <= tol, (k, gu.rel_err(g, r))
+    s = screen.cpu().numpy()
+    for i in range(s.shape[0]):
+        assert gu.rel_err(s[i], ref["screen"][i]) <= tol, ("screen", i, gu.rel_err(s[i], ref["screen"][i]))
+
+
+def test_backward_all_planes_matches_oracle():
+    """Random adjoints on all 11 differentiable planes (colour, alpha,
+    depth, inverse depth, median, normal, distortion)."""
+    scene, cam, _, _ = syn.tiny_scene(seed=31, n=800, width=64, height=48, fx=60.0, sh_degree=2,
+                                      log_scale_range=(-3.5, -1.5))
+    rng = np.random.default_rng(2)
+    adj = rng.normal(size=(1, 11, 48, 64))
+    grads, screen, ref, _ = _backward_case(scene, cam, adj, [0x7FF])
+    _assert_grads(grads, screen, ref)
+
+
+def test_training_loss_gradients_and_densify_stats():
+    """Full step: render, L1 + D-SSIM + depth loss (three adjoint sets),
+    backward, densification statistics, Eq. 2 selection, elongation."""
+    from paper_2411_00771_gb300 import binding as B
+    scene, cam, tgt, tinv = syn.tiny_scene(seed=1, n=2000, sh_degree=3)
+    w = (0.8, 0.2, 0.5)
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
+    H, W = cam["height"], cam["width"]
+    adj_s = torch.zeros((11, H, W), device="cuda")
+    adj_l = torch.zeros((11, H, W), device="cuda")
+    losses, adj_t, _, _ = B.loss(out, torch.from_numpy(tgt).cuda(), torch.from_numpy(tinv).cuda(), w,
+                                 adj_ssim=adj_s, adj_l1=adj_l)
+    n = scene["mu"].shape[0]
+    grads = {k: torch.zeros_like(v) for k, v in d.items()}
+    screen = torch.zeros((3, n, 2), device="cuda")
+    sc.backward(frame, [adj_t, adj_s, adj_l], [0x7 | (1 << 5), 0x7, 0x7], grads, screen)
+    stats = torch.zeros((n, 4), device="cuda")
+    sc.densify_accumulate(frame, screen, stats)
+    mask, g, k = B.densify_select(stats, d["scale"], 0.9, 0.0, 0.1)
+    keep = B.elongation_filter(d["scale"], 0.1)
+    torch.cuda.synchronize()
+    # oracle, end to end on its own render
+    r = oracle.render(scene, cam)
+    L = oracle.loss(r["out"], tgt, tinv, w)
+    assert abs(float(losses[3]) - L["total"]) < 1e-4
+    ref = oracle.backward(scene, cam, L["adj"])
+    _assert_grads(grads, screen, ref, tol=2e-3)
+    pre = oracle.preprocess(scene, cam)
+    st = oracle.densify_accumulate(ref["screen"], pre["tiles"] > 0)
+    assert gu.rel_err(stats.cpu().numpy(), st) <= 1e-3
+    m, gg, kk = oracle.densify_select(st, scene["scale"], 0.9, 0.0, 0.1)
+    assert abs(float(k[0]) - kk) <= 1e-3 * kk
+    assert gu.rel_err(g.cpu().numpy(), gg) <= 1e-3
+    assert np.array_equal(keep.cpu().numpy(), oracle.elongation(scene["scale"], 0.1))
+
+
+def test_densify_select_threshold_decisions():
+    """Selection on seeded statistics: masks identical except where g sits
+    within FP32 rounding of the threshold."""
+    from paper_2411_00771_gb300 import binding as B
+    rng = np.random.default_rng(8)
+    n = 100_003
+    st = np.zeros((n, 4), np.float32)
+    st[:, 3] = rng.integers(0, 5, n)
+    st[:, 0] = rng.uniform(0, 1, n) * st[:, 3]
+    st[:, 1] = rng.uniform(0, 0.5, n) * st[:, 3]
+    st[:, 2] = rng.uniform(0, 1, n) * st[:, 3]
+    sc = np.exp(rng.uniform(-3, 0, (n, 2))).astype(np.float32)
+    mask, g, k = B.densify_select(torch.from_numpy(st).cuda(), torch.from_numpy(sc).cuda(), 0.9, 0.3, 0.1)
+    m_ref, g_ref, k_ref = oracle.densify_select(st.astype(np.float64), sc, 0.9, 0.3, 0.1)
+    gm = g.cpu().numpy()
+    assert abs(float(k[0]) - k_ref) <= 1e-6 * k_ref
+    assert np.abs(gm - g_ref).max() <= 1e-5 * max(1.0, np.abs(g_ref).max())
+    close = np.abs(g_ref - 0.3) < 1e-5
+    assert np.array_equal(mask.cpu().numpy()[~close], m_ref[~close])
+
+
+def test_gradients_against_finite_differences_on_64_surfels():
+    """The GPU gradient against central finite differences of the FP64
+    oracle's loss, on a 64-surfel subset (parameters away from kinks)."""
+    scene, cam, tgt, tinv = syn.tiny_scene(seed=77, n=300, width=48, height=48, fx=48.0,
+                                           sh_degree=1, log_scale_range=(-3.0, -1.5))
+    from paper_2411_00771_gb300 import binding as B
+    w = (0.8, 0.2, 0.5)
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
+    losses, adj_t, _, _ = B.loss(out, torch.from_numpy(tgt).cuda(), torch.from_numpy(tinv).cuda(), w)
+    grads = {k: torch.zeros_like(v) for k, v in d.items()}
+    sc.backward(frame, [adj_t], [0x7 | (1 << 5)], grads)
+    torch.cuda.synchronize()
+    s64 = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in scene.items()}
+    f = lambda s: oracle.loss(oracle.render(s, cam)["out"], tgt, tinv, w)["total"]
+    rng = np.random.default_rng(0)
+    pre = oracle.preprocess(scene, cam)
+    subset = rng.choice(np.nonzero(pre["tiles"] > 0)[0], 64, replace=False)
+    checked = 0
+    for i in subset:
+        for key, comp in (("mu", rng.integers(3)), ("opacity", None), ("scale", rng.integers(2))):
+            a = s64[key]
+            idx = (i,) if comp is None else (i, comp)
+            h = 1e-6 * max(1.0, abs(a[idx]))
+            a[idx] += h
+            lp = f(s64)
+            a[idx] -= 2 * h
+            lm = f(s64)
+            a[idx] += h
+            fd = (lp - lm) / (2 * h)
+            gv = float(grads[key][idx].cpu())
+            assert abs(gv - fd) <= 1e-3 * max(abs(fd), 1e-4), (key, idx, gv, fd)
+            checked += 1
+    assert checked == 192
