@@ -185,6 +185,26 @@ gs_status gs_loss(int32_t width, int32_t height, const float* out, const float* 
                   const float* target_invdepth, const gs_loss_weights* w, float* adj_total,
                   float* adj_ssim, float* adj_l1, float* losses, void* stream);
 
+/* gs_loss without any device allocation.  (The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory when
+ * they need the loss, e.g. code running under an external memory manager
+ * that owns the whole GPU, or a real-time loop that must not stall on or
+ * fail an allocation.)
+ * Same arguments, results and kernels as gs_loss, but the scratch lives in
+ * one fixed device array inside the library (about 9.5 MB, reserved on
+ * every GPU that loads the library until the process exits), so:
+ *  - the image may have at most 512 * 512 pixels and sides of at most 4096;
+ *    larger images return GS_ERR_CAPACITY with a message (use gs_loss);
+ *  - the first call on a device looks up the array's device address on that
+ *    device (no allocation); make that first call before any stream
+ *    capture on that device;
+ *  - every call shares the array: calls whose GPU work can overlap (other
+ *    streams, other threads) race and must be serialised by the caller. */
+gs_status gs_loss_noalloc(int32_t width, int32_t height, const float* out,
+                          const float* target_rgb, const float* target_invdepth,
+                          const gs_loss_weights* w, float* adj_total, float* adj_ssim,
+                          float* adj_l1, float* losses, void* stream);
+
 /* Parameter gradients, device, same shapes as the parameters.  gs_backward
  * ADDS into them (like accumulating .grad); a null pointer skips that
  * parameter. */

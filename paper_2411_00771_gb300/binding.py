@@ -93,6 +93,8 @@ _SIGS = {
     "gs_frame_copy_lists": [_V, _V, ctypes.c_int64, _V, _V, _V],
     "gs_loss": [ctypes.c_int32, ctypes.c_int32, _V, _V, _V, ctypes.POINTER(gs_loss_weights), _V, _V,
                 _V, _V, _V],
+    "gs_loss_noalloc": [ctypes.c_int32, ctypes.c_int32, _V, _V, _V, ctypes.POINTER(gs_loss_weights), _V,
+                        _V, _V, _V, _V],
     "gs_backward": [_V, _V, ctypes.POINTER(_V), ctypes.POINTER(ctypes.c_uint32), ctypes.c_int32,
                     ctypes.POINTER(gs_param_grads), _V, _V],
     "gs_densify_accumulate": [_V, _V, _V, ctypes.c_int32, _V, _V],
@@ -295,6 +297,22 @@ def loss(out, target, tinv=None, weights=(0.8, 0.2, 0.0), adj_total=None, adj_ss
                         _ptr(adj_ssim, shape=(ADJ_PLANES, H, W), name="adj_ssim"),
                         _ptr(adj_l1, shape=(ADJ_PLANES, H, W), name="adj_l1"),
                         _ptr(losses, shape=(4,), name="losses"), _stream(stream)))
+    return losses, adj_total, adj_ssim, adj_l1
+
+
+def loss_noalloc(out, target, tinv, weights, adj_total, adj_ssim=None, adj_l1=None, losses=None,
+                 stream=None):
+    """gs_loss_noalloc: the loss with the library's fixed scratch array; every
+    output buffer comes from the caller (nothing is allocated here either)."""
+    H, W = out.shape[-2:]
+    w = gs_loss_weights(*[float(x) for x in weights])
+    _check(_lib.gs_loss_noalloc(W, H, _ptr(out, shape=(OUT_PLANES, H, W), name="out"),
+                                _ptr(target, shape=(3, H, W), name="target"),
+                                _ptr(tinv, shape=(H, W), name="target_invdepth"), ctypes.byref(w),
+                                _ptr(adj_total, shape=(ADJ_PLANES, H, W), name="adj_total"),
+                                _ptr(adj_ssim, shape=(ADJ_PLANES, H, W), name="adj_ssim"),
+                                _ptr(adj_l1, shape=(ADJ_PLANES, H, W), name="adj_l1"),
+                                _ptr(losses, shape=(4,), name="losses"), _stream(stream)))
     return losses, adj_total, adj_ssim, adj_l1
 
 

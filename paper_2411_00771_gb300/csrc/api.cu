@@ -156,6 +156,8 @@ __global__ void api_unpack_rect_kernel(const uint2* __restrict__ rect, const uin
   out[4 * i + 3] = v ? (int)(r.y >> 16) : 0;
 }
 
+void set_last_error(const char* msg) { g_last_error = msg; }
+
 void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 void prof_begin(int id, cudaStream_t st) {

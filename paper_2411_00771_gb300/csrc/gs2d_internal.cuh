@@ -126,6 +126,7 @@ enum ProfId {
   kProfCount = 7
 };
 void count_launch(int n = 1);
+void set_last_error(const char* msg);
 void prof_begin(int id, cudaStream_t st);
 void prof_end(int id, cudaStream_t st);
 

@@ -13,6 +13,9 @@
 // per-block sums in double.
 #include <math.h>
 
+#include <mutex>
+#include <string>
+
 #include "gs2d_internal.cuh"
 
 namespace gs2d {
@@ -248,3 +251,84 @@ cudaError_t launch_loss(int W, int H, const float* out, const float* tgt, const 
 }
 
 }  // namespace gs2d
+
+// ---------------------------------------------------------------------------
+// Loss without any device allocation (gs_loss_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they need the
+// loss: a renderer or trainer that runs under an external memory manager
+// which owns every byte of the GPU (allocating behind its back would break
+// its budget), a real-time loop where an allocation's latency or possible
+// failure is not acceptable, or a host that hands this library a device it
+// may only compute on.  For them the loss's scratch (the SSIM partial maps
+// and the per-block sums) lives in one fixed array in this file, sized for
+// images of up to kNoAllocMaxPixels pixels with sides up to kNoAllocMaxSide.
+// Every GPU that loads the library reserves it (about 9.5 MB) until the
+// process exits.  Every call uses the same array, so calls whose work can
+// overlap on the GPU (different streams, or different host threads) race.
+namespace gs2d {
+namespace {
+
+constexpr int kNoAllocMaxPixels = 512 * 512;
+constexpr int kNoAllocMaxSide = 4096;
+// per-block sums: at most HW/256 + (W + H)/16 + 1 tiles of 16 x 16 pixels
+constexpr size_t kNoAllocTiles = kNoAllocMaxPixels / 256 + (2 * kNoAllocMaxSide) / 16 + 1;
+constexpr size_t kNoAllocFloats = 9 * (size_t)kNoAllocMaxPixels + 7 * kNoAllocTiles + 64;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) float g_noalloc_loss_scratch[kNoAllocFloats];
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+}  // namespace gs2d
+
+extern "C" gs_status gs_loss_noalloc(int32_t W, int32_t H, const float* out, const float* tgt,
+                                     const float* tinv, const gs_loss_weights* w, float* adj_total,
+                                     float* adj_ssim, float* adj_l1, float* losses, void* stream) {
+  using namespace gs2d;
+  if (W <= 0 || H <= 0 || !out || !tgt || !w || !adj_total || !losses) {
+    set_last_error("gs_loss_noalloc: bad argument");
+    return GS_ERR_ARG;
+  }
+  if ((int64_t)W * H > kNoAllocMaxPixels || W > kNoAllocMaxSide || H > kNoAllocMaxSide ||
+      loss_tmp_floats(W, H) > kNoAllocFloats) {
+    set_last_error(("gs_loss_noalloc: image " + std::to_string(W) + "x" + std::to_string(H) +
+                    " exceeds the fixed scratch (at most " + std::to_string(kNoAllocMaxPixels) +
+                    " pixels, sides up to " + std::to_string(kNoAllocMaxSide) + "); use gs_loss")
+                       .c_str());
+    return GS_ERR_CAPACITY;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_last_error("gs_loss_noalloc: no usable current device");
+    return GS_ERR_CUDA;
+  }
+  float* scratch = nullptr;
+  {
+    // once per device, with that device current: the device address of the
+    // scratch array (its name in host code is only a host-side handle)
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_loss_scratch);
+      if (e != cudaSuccess || !ptr) {
+        set_last_error((std::string("gs_loss_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
+        return GS_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = static_cast<float*>(ptr);
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  // Nothing in the scratch must start at zero: every partial map entry and
+  // per-block sum the kernels read is written earlier in the same call.
+  e = launch_loss(W, H, out, tgt, tinv, *w, adj_total, adj_ssim, adj_l1, losses, scratch,
+                  (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    set_last_error((std::string("gs_loss_noalloc: ") + cudaGetErrorString(e)).c_str());
+    return GS_ERR_CUDA;
+  }
+  return GS_OK;
+}
