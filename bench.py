@@ -44,10 +44,12 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_HZ / 1e12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--width", type=int, default=1600, help="view width (smaller views for ncu captures)")
+    ap.add_argument("--height", type=int, default=900)
     return ap.parse_args()
 
 
@@ -114,10 +116,10 @@ def gpu_uuid(dev):
 
 
 # ---------------------------------------------------------------------------
-def city_workload(rank: int):
+def city_workload(rank: int, width: int = 1600, height: int = 900):
     from paper_2411_00771_gb300 import synthetic as syn
     scene, info = syn.city_scene(n=N_SURFELS)
-    cam = syn.aerial_camera(azimuth_deg=-90.0 + 360.0 * rank / 8.0)
+    cam = syn.aerial_camera(width=width, height=height, azimuth_deg=-90.0 + 360.0 * rank / 8.0)
     tgt, tinv = syn.city_targets(info, cam)
     return scene, cam, tgt, tinv
 
@@ -136,7 +138,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    scene_np, cam, tgt_np, tinv_np = city_workload(rank)
+    scene_np, cam, tgt_np, tinv_np = city_workload(rank, args.width, args.height)
     P = {k: torch.from_numpy(np.ascontiguousarray(scene_np[k], np.float32)).to(dev)
          for k in ("mu", "quat", "scale", "opacity", "sh")}
     sc = B.Scene(P["mu"], P["quat"], P["scale"], P["opacity"], P["sh"], scene_np["sh_degree"])
@@ -256,7 +258,7 @@ def run_ours(args):
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": round(ms_step_max, 4), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "aerial city block, 1M surfels SH3, 1600x900, fwd+bwd+loss+densify",
+            "config": {"workload": f"aerial city block, 1M surfels SH3, {W}x{H}, fwd+bwd+loss+densify",
                        "surfels": n, "width": W, "height": H, "sh_degree": 3,
                        "views_per_step": world, "l2": "inputs larger than L2 (232 MB surfel "
                        "parameters, 69 MB render planes per view)"},
@@ -353,7 +355,7 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "aerial city block, 1M surfels SH3, 1600x900, fwd+bwd+loss+densify",
+            "config": {"workload": f"aerial city block, 1M surfels SH3, {W}x{H}, fwd+bwd+loss+densify",
                        "surfels": N_SURFELS, "width": cam["width"], "height": H},
             "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},

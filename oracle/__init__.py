@@ -119,13 +119,31 @@ def preprocess(scene, cam, settings=None):
     c, s = cam_array(cam), settings_array(settings)
     out = dict(M=np.zeros((n, 9)), rgb=np.zeros((n, 3)), normal=np.zeros((n, 3)),
                zkey=np.zeros(n), bbox=np.zeros((n, 4)), rect=np.zeros((n, 4), np.int32),
-               live=np.zeros(n, np.int32), cond=np.zeros(n))
+               live=np.zeros(n, np.int32), cond=np.zeros(n), tiles=np.zeros(n, np.int32),
+               rownear=np.zeros(n, np.int32))
     lib.oracle_preprocess(ctypes.c_int64(n), ctypes.c_int(deg), *[_p(a) for a in arrs], _p(c), _p(s),
                           _p(out["M"]), _p(out["rgb"]), _p(out["normal"]), _p(out["zkey"]),
-                          _p(out["bbox"]), _p(out["rect"]), _p(out["live"]), _p(out["cond"]))
-    r = out["rect"]
-    out["tiles"] = np.where(out["live"] > 0, (r[:, 2] - r[:, 0]) * (r[:, 3] - r[:, 1]), 0)
+                          _p(out["bbox"]), _p(out["rect"]), _p(out["live"]), _p(out["cond"]),
+                          _p(out["tiles"]), _p(out["rownear"]))
     return out
+
+
+def tile_lists(scene, cam, settings=None):
+    """Per-tile surfel lists of the binned oracle (per-row coverage rule),
+    each in compositing order (FP32 centre depth, then index)."""
+    pre = preprocess(scene, cam, settings)
+    W, H = int(cam["width"]), int(cam["height"])
+    tile = int(settings_array(settings)[9])
+    tx, ty = (W + tile - 1) // tile, (H + tile - 1) // tile
+    lib = _load()
+    n, deg, arrs = _scene_args(scene)
+    c, s = cam_array(cam), settings_array(settings)
+    K = int(pre["tiles"].sum())
+    start = np.zeros(tx * ty + 1, np.int64)
+    idx = np.zeros(max(K, 1), np.int32)
+    lib.oracle_tile_lists(ctypes.c_int64(n), ctypes.c_int(deg), *[_p(a) for a in arrs], _p(c), _p(s),
+                          _p(start), _p(idx))
+    return start, idx[:K], pre
 
 
 def render(scene, cam, settings=None, mode: str = "binned", pixels=None, shift=None):

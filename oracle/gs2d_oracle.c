@@ -66,6 +66,13 @@ typedef struct {
   int live;         /* not culled */
   double rawcol[3]; /* SH sum + 0.5 before the clamp */
   double cond;      /* condition number of the centred 2x2 Jacobian */
+  /* footprint shape for per-row tile coverage: ellipse {rho_obj <= rho_max}
+   * with centre e0 and matrix G ((x - e0)^T G^-1 (x - e0) <= 1), screen disk
+   * centre sc and radius rf, pixel-centre index box [ilo, ihi] x [jlo, jhi] */
+  double e0[2], G[3], sc[2], rf;
+  int pix[4];
+  int ntiles;       /* tiles the footprint reaches (per-row rule) */
+  int rownear;      /* a row interval end within 1e-6 px of a pixel-centre boundary */
 } pre_t;
 
 typedef struct {
@@ -184,6 +191,57 @@ static void cam_pos(const double* cam, double o[3]) {
 }
 
 /* ---------------------------------------------------------------------- */
+/* Tile coverage of one row of tiles.  The footprint {rho <= rho_max} is the
+ * union of the projected disk (an ellipse, centre e0, matrix G) and the
+ * screen-filter disk.  Over the band of pixel-centre rows of tile row ty,
+ * each convex part spans an x interval: the ellipse's x(y) on its right
+ * boundary is concave, so its largest value over the band is at the
+ * rightmost point's y clamped to the band (the leftmost likewise); the
+ * disk's widest point is at its centre's y clamped to the band.  The tiles
+ * of the pixel centres inside the hull of the two intervals are covered.
+ * Returns 0 when the row is empty, else the tile columns [tx0, tx1). */
+static int row_tiles(pre_t* P, int ty, int tile, int* tx0, int* tx1) {
+  int ja = ty * tile, jb = ty * tile + tile - 1;
+  if (ja < P->pix[2]) ja = P->pix[2];
+  if (jb > P->pix[3]) jb = P->pix[3];
+  if (ja > jb) return 0;
+  const double ya = ja + 0.5, yb = jb + 0.5;
+  double lo = INFINITY, hi = -INFINITY;
+  const double g11 = P->G[0], g12 = P->G[1], g22 = P->G[2];
+  if (g11 > 0 && g22 > 0) {
+    const double hx = sqrt(g11), hy = sqrt(g22);
+    const double dya = ya - P->e0[1], dyb = yb - P->e0[1];
+    if (dyb >= -hy && dya <= hy) {
+      const double det = fmax(g11 * g22 - g12 * g12, 0.0);
+      /* rightmost point at dy = g12 / hx, leftmost at -g12 / hx */
+      double yr = g12 / hx, yl = -g12 / hx;
+      yr = yr < dya ? dya : (yr > dyb ? dyb : yr);
+      yl = yl < dya ? dya : (yl > dyb ? dyb : yl);
+      hi = P->e0[0] + (g12 * yr + sqrt(fmax(det * (g22 - yr * yr), 0.0))) / g22;
+      lo = P->e0[0] + (g12 * yl - sqrt(fmax(det * (g22 - yl * yl), 0.0))) / g22;
+    }
+  }
+  double yn = P->sc[1];
+  yn = yn < ya ? ya : (yn > yb ? yb : yn);
+  const double dy = yn - P->sc[1];
+  if (dy * dy <= P->rf * P->rf) {
+    const double h = sqrt(P->rf * P->rf - dy * dy);
+    if (P->sc[0] - h < lo) lo = P->sc[0] - h;
+    if (P->sc[0] + h > hi) hi = P->sc[0] + h;
+  }
+  if (!(lo <= hi)) return 0;
+  if (fabs((lo - 0.5) - nearbyint(lo - 0.5)) < 1e-6 || fabs((hi - 0.5) - nearbyint(hi - 0.5)) < 1e-6)
+    P->rownear = 1;
+  double ilo = ceil(lo - 0.5), ihi = floor(hi - 0.5);
+  if (ilo < P->pix[0]) ilo = P->pix[0];
+  if (ihi > P->pix[1]) ihi = P->pix[1];
+  if (ilo > ihi) return 0;
+  *tx0 = (int)ilo / tile;
+  *tx1 = (int)ihi / tile + 1;
+  return 1;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Per-surfel preprocess: the definition's steps 1-3, 7, 8 and the 3-sigma
  * cover (conic bounding box) plus the screen-filter disc. */
 static void preprocess_one(const scene_t* S, int64_t n, const double* cam,
@@ -247,6 +305,14 @@ static void preprocess_one(const scene_t* S, int64_t n, const double* cam,
   const double C13 = r * (M[0] * M[6] + M[1] * M[7]) - M[2] * M[8];
   const double C23 = r * (M[3] * M[6] + M[4] * M[7]) - M[5] * M[8];
   const double C33 = r * (M[6] * M[6] + M[7] * M[7]) - M[8] * M[8];
+  const double C12 = r * (M[0] * M[3] + M[1] * M[4]) - M[2] * M[5];
+  /* the dual conic scaled to C*33 = 1 is [[e0 e0^T - G, e0], [e0^T, 1]] for
+   * the ellipse (x - e0)^T G^-1 (x - e0) <= 1: centre and shape directly */
+  P->e0[0] = C13 / C33;
+  P->e0[1] = C23 / C33;
+  P->G[0] = P->e0[0] * P->e0[0] - C11 / C33;
+  P->G[1] = P->e0[0] * P->e0[1] - C12 / C33;
+  P->G[2] = P->e0[1] * P->e0[1] - C22 / C33;
   double dx = C13 * C13 - C11 * C33, dy = C23 * C23 - C22 * C33;
   dx = dx > 0 ? sqrt(dx) : 0; dy = dy > 0 ? sqrt(dy) : 0;
   double x0 = (C13 - dx) / C33, x1 = (C13 + dx) / C33;
@@ -264,11 +330,17 @@ static void preprocess_one(const scene_t* S, int64_t n, const double* cam,
   if (jlo < 0) jlo = 0;
   if (ihi > W - 1) ihi = W - 1;
   if (jhi > H - 1) jhi = H - 1;
+  P->sc[0] = ccx; P->sc[1] = ccy; P->rf = rf;
   if (ilo > ihi || jlo > jhi) {
     P->rect[0] = P->rect[1] = P->rect[2] = P->rect[3] = 0;
   } else {
     P->rect[0] = (int)ilo / tile; P->rect[1] = (int)jlo / tile;
     P->rect[2] = (int)ihi / tile + 1; P->rect[3] = (int)jhi / tile + 1;
+    P->pix[0] = (int)ilo; P->pix[1] = (int)ihi; P->pix[2] = (int)jlo; P->pix[3] = (int)jhi;
+    for (int ty = P->rect[1]; ty < P->rect[3]; ++ty) {
+      int a, b;
+      if (row_tiles(P, ty, tile, &a, &b)) P->ntiles += b - a;
+    }
   }
   /* condition number of the centred Jacobian d(offset)/d(u,v) at the centre:
    * used only to flag pixels whose FP32 evaluation is ill-conditioned */
@@ -415,11 +487,13 @@ static scene_t mk_scene(int64_t N, int deg, const double* mu, const double* quat
 }
 
 /* Preprocess: per surfel M[9], rgb[3], normal[3], zkey, bbox[4], rect[4],
- * live flag and the Jacobian condition number. */
+ * live flag, the Jacobian condition number, the number of tiles the
+ * footprint reaches (per-row rule) and whether a row interval ends within
+ * 1e-6 px of a pixel-centre boundary. */
 int oracle_preprocess(int64_t N, int deg, const double* mu, const double* quat, const double* scale,
                       const double* opac, const double* sh, const double* cam, const double* set,
                       double* M, double* rgb, double* nrm, double* zkey, double* bbox, int* rect,
-                      int* live, double* cond) {
+                      int* live, double* cond, int* ntiles, int* rownear) {
   scene_t S = mk_scene(N, deg, mu, quat, scale, opac, sh);
 #pragma omp parallel for schedule(static)
   for (int64_t n = 0; n < N; ++n) {
@@ -433,21 +507,27 @@ int oracle_preprocess(int64_t N, int deg, const double* mu, const double* quat, 
     memcpy(rect + 4 * n, P.rect, sizeof P.rect);
     live[n] = P.live;
     cond[n] = P.cond;
+    if (ntiles) ntiles[n] = P.live ? P.ntiles : 0;
+    if (rownear) rownear[n] = P.rownear;
   }
   return 0;
 }
 
 /* Tile lists: for each tile, surfels (by index) whose rect covers it. */
-typedef struct { int64_t* start; int* idx; int ntiles; } tiles_t;
+typedef struct { int64_t* start; int* idx; int ntiles; int tile; } tiles_t;
 
 static void build_tiles(const pre_t* pre, int64_t N, int tx, int ty, tiles_t* T) {
   T->ntiles = tx * ty;
   T->start = (int64_t*)calloc((size_t)T->ntiles + 1, sizeof(int64_t));
+  const int tile = (int)(T->tile);
   for (int64_t n = 0; n < N; ++n) {
     if (!pre[n].live) continue;
-    const int* r = pre[n].rect;
-    for (int j = r[1]; j < r[3]; ++j)
-      for (int i = r[0]; i < r[2]; ++i) T->start[j * tx + i + 1]++;
+    pre_t P = pre[n];
+    for (int j = P.rect[1]; j < P.rect[3]; ++j) {
+      int a, b;
+      if (!row_tiles(&P, j, tile, &a, &b)) continue;
+      for (int i = a; i < b; ++i) T->start[j * tx + i + 1]++;
+    }
   }
   for (int t = 0; t < T->ntiles; ++t) T->start[t + 1] += T->start[t];
   T->idx = (int*)malloc(sizeof(int) * (size_t)(T->start[T->ntiles] + 1));
@@ -455,9 +535,12 @@ static void build_tiles(const pre_t* pre, int64_t N, int tx, int ty, tiles_t* T)
   memcpy(fill, T->start, sizeof(int64_t) * (size_t)T->ntiles);
   for (int64_t n = 0; n < N; ++n) {
     if (!pre[n].live) continue;
-    const int* r = pre[n].rect;
-    for (int j = r[1]; j < r[3]; ++j)
-      for (int i = r[0]; i < r[2]; ++i) T->idx[fill[j * tx + i]++] = (int)n;
+    pre_t P = pre[n];
+    for (int j = P.rect[1]; j < P.rect[3]; ++j) {
+      int a, b;
+      if (!row_tiles(&P, j, tile, &a, &b)) continue;
+      for (int i = a; i < b; ++i) T->idx[fill[j * tx + i]++] = (int)n;
+    }
   }
   free(fill);
 }
@@ -495,6 +578,7 @@ static void ctx_init(ctx_t* C, const scene_t* S, const double* cam, const double
     for (int64_t n = 0; n < S->N; ++n) C->all[n] = (int)n;
     C->maxlist = (int)S->N;
   } else {
+    C->tiles.tile = tile;
     build_tiles(C->pre, S->N, C->tx, ty, &C->tiles);
     int64_t mx = 0;
     for (int t = 0; t < C->tiles.ntiles; ++t) {
@@ -1007,4 +1091,29 @@ int oracle_num_threads(void) {
 #else
   return 1;
 #endif
+}
+
+/* Tile lists of the binned mode in compositing order: start[ntiles + 1]
+ * offsets, idx[K] surfel indices (sorted per tile by FP32 centre depth,
+ * then index). */
+int oracle_tile_lists(int64_t N, int deg, const double* mu, const double* quat, const double* scale,
+                      const double* opac, const double* sh, const double* cam, const double* set,
+                      int64_t* start, int* idx) {
+  scene_t S = mk_scene(N, deg, mu, quat, scale, opac, sh);
+  ctx_t C;
+  ctx_init(&C, &S, cam, set, 1);
+  memcpy(start, C.tiles.start, sizeof(int64_t) * (size_t)(C.tiles.ntiles + 1));
+  const int64_t K = C.tiles.start[C.tiles.ntiles];
+  memcpy(idx, C.tiles.idx, sizeof(int) * (size_t)K);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int t = 0; t < C.tiles.ntiles; ++t) {
+    const int64_t a = start[t], b = start[t + 1];
+    okey_t* k = (okey_t*)malloc(sizeof(okey_t) * (size_t)(b - a + 1));
+    for (int64_t i = a; i < b; ++i) { k[i - a].z = C.pre[idx[i]].zkey; k[i - a].n = idx[i]; k[i - a].slot = 0; }
+    qsort(k, (size_t)(b - a), sizeof(okey_t), cmp_keys);
+    for (int64_t i = a; i < b; ++i) idx[i] = k[i - a].n;
+    free(k);
+  }
+  ctx_free(&C);
+  return 0;
 }

@@ -149,7 +149,8 @@ __global__ void api_unpack_rect_kernel(const uint2* __restrict__ rect, const uin
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint2 r = rect[i];
-  const bool v = tcount[i] > 0;
+  const bool v = (r.y & 0xFFFF) > (r.x & 0xFFFF);
+  (void)tcount;
   out[4 * i] = v ? (int)(r.x & 0xFFFF) : 0;
   out[4 * i + 1] = v ? (int)(r.x >> 16) : 0;
   out[4 * i + 2] = v ? (int)(r.y & 0xFFFF) : 0;
@@ -348,8 +349,10 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   uint32_t* cnts = tmp.get<uint32_t>(n > 0 ? n : 1, st);
   uint32_t* offs = tmp.get<uint32_t>(n > 0 ? n : 1, st);
   uint32_t* rtmp = tmp.get<uint32_t>(radix_tmp_words(n) + scan_tmp_words(n) + 4, st);
+  uint32_t* cand = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  RowGeom* geom = tmp.get<RowGeom>(n > 0 ? n : 1, st);
   if (!f->rec || !f->rect || !f->tcount || !f->ranges || !f->last || !f->med || !f->counters || !dkey ||
-      !idx || !dkey2 || !idx2 || !cnts || !offs || !rtmp)
+      !idx || !dkey2 || !idx2 || !cnts || !offs || !rtmp || !cand || !geom)
     return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed"));
   uint32_t* total = rtmp + radix_tmp_words(n) + scan_tmp_words(n);
   cudaError_t e;
@@ -359,7 +362,8 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
     if (e != cudaSuccess) return cleanup(cuda_fail(e, #expr)); \
   } while (0)
   GS_CKC(cudaMemsetAsync(f->counters, 0, 8 * sizeof(unsigned long long), st));
-  GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, st));
+  GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, cand, total + 1,
+                           geom, st));
   uint32_t *skey = dkey, *sidx = idx;
   GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st));
   GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st));
@@ -377,7 +381,8 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   uint32_t* ktmp = tmp.get<uint32_t>(radix_tmp_words(K), st);
   if (!keys || !vals || !keys2 || !vals2 || !ktmp)
     return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed (tile lists)"));
-  GS_CKC(launch_emit(sidx, offs, f->rect, n, cam.tiles_x, keys, vals, st));
+  const float rf = (float)sqrt((double)sc->settings.rho_max / (double)sc->settings.screen_inv_sigma2);
+  GS_CKC(launch_emit(sidx, offs, cnts, f->rect, geom, rf, n, cam.tiles_x, keys, vals, st));
   uint32_t *tk = keys, *tv = vals;
   GS_CKC(radix_sort_pairs(keys, vals, keys2, vals2, K, bits_for(ntiles), ktmp, &tk, &tv, st));
   f->vals = tv;
@@ -407,15 +412,14 @@ gs_status gs_frame_get_info(gs_frame* f, gs_frame_info* info, void* stream) {
   info->bwd_pairs_evaluated = (int64_t)h[2];
   info->tiles_x = f->cam.tiles_x;
   info->tiles_y = f->cam.tiles_y;
-  // visible surfels: count non-zero tile counts on the host (debug path)
-  std::vector<uint32_t> tc((size_t)f->n);
+  // visible surfels (non-empty tile rectangle), counted on the host (debug path)
+  std::vector<uint2> rc((size_t)f->n);
   if (f->n > 0) {
-    GS_CK(cudaMemcpyAsync(tc.data(), f->tcount, sizeof(uint32_t) * (size_t)f->n,
-                          cudaMemcpyDeviceToHost, st));
+    GS_CK(cudaMemcpyAsync(rc.data(), f->rect, sizeof(uint2) * (size_t)f->n, cudaMemcpyDeviceToHost, st));
     GS_CK(cudaStreamSynchronize(st));
   }
   int64_t v = 0;
-  for (uint32_t x : tc) v += x > 0;
+  for (const uint2& r : rc) v += (r.y & 0xFFFF) > (r.x & 0xFFFF);
   info->n_visible = v;
   return GS_OK;
 }
@@ -490,7 +494,7 @@ gs_status gs_densify_accumulate(gs_scene* sc, gs_frame* f, const float* screen, 
   if (!sc || !f || !screen || !stats) return fail(GS_ERR_ARG, "gs_densify_accumulate: null argument");
   if (f->n != sc->P.n) return fail(GS_ERR_STATE, "gs_densify_accumulate: surfel count changed");
   if (n_sets < 1) return fail(GS_ERR_ARG, "gs_densify_accumulate: n_sets must be >= 1");
-  cudaError_t e = launch_densify_accumulate(f->tcount, screen, f->n, n_sets, stats, (cudaStream_t)stream);
+  cudaError_t e = launch_densify_accumulate(f->rect, screen, f->n, n_sets, stats, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "gs_densify_accumulate");
   return GS_OK;
 }

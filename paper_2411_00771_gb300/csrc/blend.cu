@@ -271,16 +271,20 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
     __syncthreads();
     for (int kk = nb - 1; kk >= 0; --kk) {
       const int k = b0 + kk;
+      Pair q;
+      q.hit = false;
+      const float4 r1 = s1[kk], r2 = s2[kk];
+      if (k < lastpos) {
+        ++replayed;
+        q = eval_pair(fx, fy, s0[kk], r1, r2, set);
+      }
+      const bool contrib = q.hit;
+      if (__ballot_sync(0xffffffffu, contrib) == 0u) continue;
       float v[kSlots];
 #pragma unroll
       for (int i = 0; i < kSlots; ++i) v[i] = 0.f;
-      bool contrib = false;
-      if (k < lastpos) {
-        ++replayed;
-        const float4 r1 = s1[kk], r2 = s2[kk];
-        const Pair q = eval_pair(fx, fy, s0[kk], r1, r2, set);
-        if (q.hit) {
-          contrib = true;
+      {
+        if (contrib) {
           const float4 r3 = s3[kk], r4 = s4[kk];
           const float om = 1.f - q.alpha;
           const float rom = 1.f / om;

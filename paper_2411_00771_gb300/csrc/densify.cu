@@ -5,10 +5,13 @@
 namespace gs2d {
 namespace {
 
-__global__ void densify_acc_kernel(const uint32_t* __restrict__ tcount, const float* __restrict__ screen,
+// Visible = non-empty tile rectangle in this view.
+__global__ void densify_acc_kernel(const uint2* __restrict__ rect, const float* __restrict__ screen,
                                    int n, int n_sets, float* __restrict__ stats) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || tcount[i] == 0) return;
+  if (i >= n) return;
+  const uint2 r = rect[i];
+  if ((r.y & 0xFFFF) <= (r.x & 0xFFFF)) return;
   float* s = stats + 4 * (size_t)i;
   for (int k = 0; k < n_sets && k < 3; ++k) {
     const float gx = screen[((size_t)k * n + i) * 2], gy = screen[((size_t)k * n + i) * 2 + 1];
@@ -25,8 +28,8 @@ __global__ void densify_avg_kernel(const float* __restrict__ stats, int64_t n, d
        i += (int64_t)gridDim.x * blockDim.x) {
     const float* s = stats + 4 * i;
     if (s[3] > 0.f) {
-      a += (double)s[0] / s[3];
-      b += (double)s[1] / s[3];
+      a += (double)(s[0] / s[3]);
+      b += (double)(s[1] / s[3]);
       c += 1.0;
     }
   }
@@ -51,13 +54,29 @@ __global__ void densify_avg_kernel(const float* __restrict__ stats, int64_t n, d
 
 // k = max(omega * avg_tot / avg_ssim, 1); written to part[0] (as double)
 __global__ void densify_scale_kernel(double* __restrict__ part, int nb, float omega, float* k_out) {
-  if (threadIdx.x != 0) return;
+  __shared__ double red[3][256];
   double a = 0.0, b = 0.0, c = 0.0;
-  for (int i = 0; i < nb; ++i) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     a += part[3 * i];
     b += part[3 * i + 1];
     c += part[3 * i + 2];
   }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  red[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + k];
+      red[1][threadIdx.x] += red[1][threadIdx.x + k];
+      red[2][threadIdx.x] += red[2][threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  a = red[0][0];
+  b = red[1][0];
+  c = red[2][0];
   double k = 1.0;
   if (c > 0.0 && b > 0.0) {
     const double r = (double)omega * (a / c) / (b / c);
@@ -95,12 +114,12 @@ constexpr int kAvgBlocks = 304;  // two CTAs per SM on 152 SMs
 
 size_t densify_tmp_doubles(int64_t) { return 3 * kAvgBlocks + 8; }
 
-cudaError_t launch_densify_accumulate(const uint32_t* tcount, const float* screen, int n,
+cudaError_t launch_densify_accumulate(const uint2* rect, const float* screen, int n,
                                       int n_sets, float* stats, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   ProfScope ps(kProfDensify, st);
   count_launch();
-  densify_acc_kernel<<<div_up(n, 256), 256, 0, st>>>(tcount, screen, n, n_sets, stats);
+  densify_acc_kernel<<<div_up(n, 256), 256, 0, st>>>(rect, screen, n, n_sets, stats);
   return cudaGetLastError();
 }
 
@@ -110,7 +129,7 @@ cudaError_t launch_densify_select(int64_t n, const float* stats, const float* sc
   ProfScope ps(kProfDensify, st);
   count_launch(n > 0 ? 3 : 2);
   densify_avg_kernel<<<kAvgBlocks, 256, 0, st>>>(stats, n, tmp);
-  densify_scale_kernel<<<1, 32, 0, st>>>(tmp, kAvgBlocks, omega, k_out);
+  densify_scale_kernel<<<1, 256, 0, st>>>(tmp, kAvgBlocks, omega, k_out);
   if (n > 0)
     densify_select_kernel<<<div_up(n, 256), 256, 0, st>>>(stats, scale, n, tmp, grad_thr, eta_thr,
                                                           mask, g_out);

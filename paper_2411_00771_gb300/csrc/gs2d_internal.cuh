@@ -36,6 +36,71 @@ struct SetDev {
 // For a pixel offset d = x - c:  den = 1 + e.d,  (u, v) = Ji d / den,
 // rho_obj = u^2 + v^2, z_obj = p_z / den.
 
+// Footprint shape for tile-row coverage, FP32 (offsets from c): the ellipse
+// {rho_obj <= rho_max} is (d - e0)^T G^-1 (d - e0) <= 1; its boundary at
+// height dy (relative to e0) is x = e0x + slope dy +- wsc sqrt(hy^2 - dy^2)
+// with slope = g12 / g22, wsc = sqrt(det G) / g22, hy = sqrt(g22); its
+// rightmost point is at dy = t = g12 / sqrt(g11), the leftmost at -t.  The
+// screen-filter disk is |d| <= rf.  [ilo, ihi] x [jlo, jhi] is the
+// pixel-centre index box of the whole footprint (FP64, clipped to the image).
+// Derived terms are computed in FP64 and rounded once.
+struct RowGeom {
+  float cx_hi, cx_lo, cy_hi, cy_lo;
+  float e0x, e0y, hy, t, slope, wsc;
+  int ilo, ihi, jlo, jhi;
+};
+
+// Tile columns [tx0, tx1) that the footprint reaches in tile row ty.  Over
+// the band of pixel-centre rows of the tile row, the ellipse's right
+// boundary x(y) is concave, so its maximum is at the rightmost point's y
+// clamped to the band (likewise the left boundary); the disk is widest at
+// its centre's y clamped to the band.  Pixel centres inside the hull of the
+// two intervals, widened by a margin that covers the FP32 rounding of these
+// few operations, are covered: the result is a superset of the exact cover.
+// Written with explicit round-to-nearest operations because the preprocess
+// (counting) and the emission (writing) call it on the same stored values
+// and must agree bit for bit.
+__device__ __forceinline__ bool row_tiles(const RowGeom& g, int ty, float rf, int* tx0, int* tx1) {
+  const int ja = max(ty * kTile, g.jlo), jb = min(ty * kTile + kTile - 1, g.jhi);
+  if (ja > jb) return false;
+  const float ya = __fsub_rn(__fsub_rn((float)ja + 0.5f, g.cy_hi), g.cy_lo);
+  const float yb = __fsub_rn(__fsub_rn((float)jb + 0.5f, g.cy_hi), g.cy_lo);
+  const float my = __fmaf_rn(1e-5f, __fadd_rn(fabsf(ya), fabsf(yb)), 1e-3f);
+  float lo = INFINITY, hi = -INFINITY;
+  if (g.hy > 0.f) {
+    const float dya = __fsub_rn(ya, g.e0y), dyb = __fsub_rn(yb, g.e0y);
+    if (dyb >= -__fadd_rn(g.hy, my) && dya <= __fadd_rn(g.hy, my)) {
+      const float yr = fminf(fmaxf(g.t, dya), dyb);
+      const float yl = fminf(fmaxf(-g.t, dya), dyb);
+      const float qr = fmaxf(__fmul_rn(__fsub_rn(g.hy, yr), __fadd_rn(g.hy, yr)), 0.f);
+      const float ql = fmaxf(__fmul_rn(__fsub_rn(g.hy, yl), __fadd_rn(g.hy, yl)), 0.f);
+      hi = __fmaf_rn(g.wsc, __fsqrt_rn(qr), __fmaf_rn(g.slope, yr, g.e0x));
+      lo = __fmaf_rn(-g.wsc, __fsqrt_rn(ql), __fmaf_rn(g.slope, yl, g.e0x));
+      // the y rounding moves the boundary by up to |slope| my
+      const float ms = __fmul_rn(fabsf(g.slope), my);
+      hi = __fadd_rn(hi, ms);
+      lo = __fsub_rn(lo, ms);
+    }
+  }
+  const float yn = fminf(fmaxf(0.f, ya), yb);
+  const float r2 = __fsub_rn(__fmul_rn(rf, rf), __fmul_rn(yn, yn));
+  if (r2 >= -__fmul_rn(2.f * rf, my)) {
+    const float h = __fadd_rn(__fsqrt_rn(fmaxf(r2, 0.f)), my);
+    lo = fminf(lo, -h);
+    hi = fmaxf(hi, h);
+  }
+  if (!(lo <= hi)) return false;
+  const float m = __fmaf_rn(1e-5f, __fadd_rn(fabsf(lo), fabsf(hi)), 1e-3f);
+  const float xlo = __fadd_rn(__fadd_rn(g.cx_hi, __fsub_rn(lo, m)), g.cx_lo);
+  const float xhi = __fadd_rn(__fadd_rn(g.cx_hi, __fadd_rn(hi, m)), g.cx_lo);
+  const int ilo = max((int)ceilf(__fsub_rn(fmaxf(xlo, -1.f), 0.5f)), g.ilo);
+  const int ihi = min((int)floorf(__fsub_rn(fminf(xhi, 1.0e9f), 0.5f)), g.ihi);
+  if (ilo > ihi) return false;
+  *tx0 = ilo / kTile;
+  *tx1 = ihi / kTile + 1;
+  return true;
+}
+
 struct Workspace;  // allocator wrapper
 
 struct ParamsDev {
@@ -51,7 +116,8 @@ struct ParamsDev {
 // ---- launch wrappers (each returns cudaError_t from the launch) ----------
 cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
                               float4* rec, uint2* rect, uint32_t* tcount, uint32_t* depth_key,
-                              uint32_t* idx, cudaStream_t st);
+                              uint32_t* idx, uint32_t* cand, uint32_t* ncand, RowGeom* geom,
+                              cudaStream_t st);
 
 // device-wide exclusive scan of n uint32 values; total (uint32) written to
 // *total_dev; tmp must hold scan_tmp_words(n) uint32 words.
@@ -69,8 +135,9 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
 
 cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* tcount, uint32_t* out,
                                  int64_t n, cudaStream_t st);
-cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint2* rect,
-                        int64_t n, int tiles_x, uint32_t* keys, uint32_t* vals, cudaStream_t st);
+cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint32_t* counts,
+                        const uint2* rect, const RowGeom* geom, float rf, int64_t n, int tiles_x,
+                        uint32_t* keys, uint32_t* vals, cudaStream_t st);
 cudaError_t launch_ranges(const uint32_t* keys, int64_t K, int2* ranges, int ntiles,
                           cudaStream_t st);
 
@@ -102,7 +169,7 @@ cudaError_t launch_loss(int W, int H, const float* out, const float* tgt, const 
                         float* adj_l1, float* losses, float* tmp, cudaStream_t st);
 size_t loss_tmp_floats(int W, int H);
 
-cudaError_t launch_densify_accumulate(const uint32_t* tcount, const float* screen, int n,
+cudaError_t launch_densify_accumulate(const uint2* rect, const float* screen, int n,
                                       int n_sets, float* stats, cudaStream_t st);
 cudaError_t launch_densify_select(int64_t n, const float* stats, const float* scale, float omega,
                                   float grad_thr, float eta_thr, uint8_t* mask, float* g_out,

@@ -109,20 +109,78 @@ __device__ __forceinline__ V3<T> rotT(const double* R, V3<T> v) {
           T(R[2]) * v.x + T(R[5]) * v.y + T(R[8]) * v.z};
 }
 
-__global__ void __launch_bounds__(256) preprocess_kernel(ParamsDev P, CamDev cam, SetDev set,
-                                                         float4* __restrict__ rec,
-                                                         uint2* __restrict__ rect,
-                                                         uint32_t* __restrict__ tcount,
-                                                         uint32_t* __restrict__ dkey,
-                                                         uint32_t* __restrict__ idx) {
+// Stage 1 (FP32, every surfel): defaults for the sort inputs and a
+// conservative visibility test, appending possibly visible surfels to a
+// candidate list.  It rejects only surfels that stage 2 would reject: the
+// 3-sigma disk lies inside the sphere of radius 3 max(s_u, s_v) around mu,
+// so a sphere entirely behind the near plane, or whose camera-space box
+// projects (with the screen-filter radius, one pixel and a relative error
+// margin added) entirely outside the image, has an empty tile rectangle.
+__global__ void __launch_bounds__(256) preprocess_cull_kernel(ParamsDev P, CamDev cam, SetDev set,
+                                                              uint2* __restrict__ rect,
+                                                              uint32_t* __restrict__ tcount,
+                                                              uint32_t* __restrict__ dkey,
+                                                              uint32_t* __restrict__ idx,
+                                                              uint32_t* __restrict__ cand,
+                                                              uint32_t* __restrict__ ncand) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= P.n) return;
-  idx[n] = (uint32_t)n;
-  uint32_t cnt = 0, key = 0xFFFFFFFFu;
-  uint2 rc = make_uint2(0u, 0u);
-  const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
-  const double qn2 = (double)qw * qw + (double)qx * qx + (double)qy * qy + (double)qz * qz;
-  if (qn2 > 0.0) {
+  bool keep = false;
+  if (n < P.n) {
+    idx[n] = (uint32_t)n;
+    dkey[n] = 0xFFFFFFFFu;
+    tcount[n] = 0u;
+    rect[n] = make_uint2(0u, 0u);
+    const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
+    const double qn2 = (double)qw * qw + (double)qx * qx + (double)qy * qy + (double)qz * qz;
+    const V3<float> mu = {P.mu[3 * n], P.mu[3 * n + 1], P.mu[3 * n + 2]};
+    V3<float> p = rot<float>(cam.R, mu);
+    p.x += (float)cam.t[0]; p.y += (float)cam.t[1]; p.z += (float)cam.t[2];
+    const float R = 3.0f * fmaxf(P.scale[2 * n], P.scale[2 * n + 1]) * sqrtf(set.rho_max / 9.0f);
+    // FP32 error of p is far below this margin (a few ulp of |mu| + |t|)
+    const float eps = 1e-4f * (fabsf(mu.x) + fabsf(mu.y) + fabsf(mu.z) + (float)(fabs(cam.t[0]) +
+                      fabs(cam.t[1]) + fabs(cam.t[2])) + 1.0f) + 1e-3f * R;
+    keep = qn2 > 0.0 && p.z + R + eps > set.near_plane;
+    const float zlo = p.z - R - eps, zhi = p.z + R + eps;
+    if (keep && zlo > 0.f) {
+      const float rpix = sqrtf(set.rho_max / set.sinv) + 1.0f;
+      const float fx = (float)cam.fx, fy = (float)cam.fy;
+      const float xa = p.x - R - eps, xb = p.x + R + eps, ya = p.y - R - eps, yb = p.y + R + eps;
+      const float sx0 = fx * (xa < 0.f ? xa / zlo : xa / zhi) + (float)cam.cx - rpix;
+      const float sx1 = fx * (xb > 0.f ? xb / zlo : xb / zhi) + (float)cam.cx + rpix;
+      const float sy0 = fy * (ya < 0.f ? ya / zlo : ya / zhi) + (float)cam.cy - rpix;
+      const float sy1 = fy * (yb > 0.f ? yb / zlo : yb / zhi) + (float)cam.cy + rpix;
+      const float m = 1e-3f * (fabsf(sx0) + fabsf(sx1) + fabsf(sy0) + fabsf(sy1)) + 1.0f;
+      keep = !(sx1 < -m || sx0 > (float)cam.W + m || sy1 < -m || sy0 > (float)cam.H + m);
+    }
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, keep);
+  if (ball) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ball) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(ncand, (uint32_t)__popc(ball));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (keep) cand[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)n;
+  }
+}
+
+// Stage 2 (FP64 geometry, candidates only): the definition's preprocess,
+// the footprint's exact tile-row coverage and the blend record.
+__global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDev cam, SetDev set,
+                                                              const uint32_t* __restrict__ cand,
+                                                              const uint32_t* __restrict__ ncand,
+                                                              float4* __restrict__ rec,
+                                                              uint2* __restrict__ rect,
+                                                              uint32_t* __restrict__ tcount,
+                                                              uint32_t* __restrict__ dkey,
+                                                              RowGeom* __restrict__ geom) {
+  const uint32_t total = *ncand;
+  const double rf = sqrt((double)set.rho_max / (double)set.sinv);
+  for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < total; ci += gridDim.x * blockDim.x) {
+    const int n = (int)cand[ci];
+    const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
+    const double qn2 = (double)qw * qw + (double)qx * qx + (double)qy * qy + (double)qz * qz;
+    if (!(qn2 > 0.0)) continue;
     const double iq = 1.0 / sqrt(qn2);
     V3<double> r1, r2, r3;
     quat_cols<double>(qw * iq, qx * iq, qy * iq, qz * iq, r1, r2, r3);
@@ -133,79 +191,101 @@ __global__ void __launch_bounds__(256) preprocess_kernel(ParamsDev P, CamDev cam
     const double su = P.scale[2 * n], sv = P.scale[2 * n + 1];
     const V3<double> a = {su * tu.x, su * tu.y, su * tu.z}, b = {sv * tv.x, sv * tv.y, sv * tv.z};
     const double zmin = p.z - sqrt((double)set.rho_max) * sqrt(a.z * a.z + b.z * b.z);
-    if (zmin > (double)set.near_plane) {
-      const double iz = 1.0 / p.z;
-      const double xi = p.x * iz, yi = p.y * iz;
-      const double cx = cam.fx * xi + cam.cx, cy = cam.fy * yi + cam.cy;
-      const double J11 = cam.fx * (a.x - a.z * xi) * iz, J12 = cam.fx * (b.x - b.z * xi) * iz;
-      const double J21 = cam.fy * (a.y - a.z * yi) * iz, J22 = cam.fy * (b.y - b.z * yi) * iz;
-      const double w1 = a.z * iz, w2 = b.z * iz;
-      const double det = J11 * J22 - J12 * J21;
-      float4 r1f;
-      float2 ef;
-      if (det != 0.0) {
-        const double id = 1.0 / det;
-        const double i11 = J22 * id, i12 = -J12 * id, i21 = -J21 * id, i22 = J11 * id;
-        r1f = make_float4((float)i11, (float)i12, (float)i21, (float)i22);
-        ef = make_float2((float)(-(i11 * w1 + i21 * w2)), (float)(-(i12 * w1 + i22 * w2)));
+    if (!(zmin > (double)set.near_plane)) continue;
+    const double iz = 1.0 / p.z;
+    const double xi = p.x * iz, yi = p.y * iz;
+    const double cx = cam.fx * xi + cam.cx, cy = cam.fy * yi + cam.cy;
+    const double J11 = cam.fx * (a.x - a.z * xi) * iz, J12 = cam.fx * (b.x - b.z * xi) * iz;
+    const double J21 = cam.fy * (a.y - a.z * yi) * iz, J22 = cam.fy * (b.y - b.z * yi) * iz;
+    const double w1 = a.z * iz, w2 = b.z * iz;
+    // bounding box of {rho_obj <= rho_max} in offsets from c: dual conic of
+    // the centred homography H = [[J, 0], [w^T, 1]]; scaled to C33 = 1 it is
+    // [[e0 e0^T - G, e0], [e0^T, 1]] for the ellipse (d - e0)^T G^-1 (d - e0) <= 1
+    const double rm = set.rho_max;
+    const double C11 = rm * (J11 * J11 + J12 * J12), C22 = rm * (J21 * J21 + J22 * J22);
+    const double C12 = rm * (J11 * J21 + J12 * J22);
+    const double C13 = rm * (J11 * w1 + J12 * w2), C23 = rm * (J21 * w1 + J22 * w2);
+    const double C33 = rm * (w1 * w1 + w2 * w2) - 1.0;
+    const double ex = sqrt(fmax(C13 * C13 - C11 * C33, 0.0));
+    const double ey = sqrt(fmax(C23 * C23 - C22 * C33, 0.0));
+    const double x0 = (C13 - ex) / C33, x1 = (C13 + ex) / C33;
+    const double y0 = (C23 - ey) / C33, y1 = (C23 + ey) / C33;
+    const double xmin = cx + fmin(fmin(x0, x1), -rf), xmax = cx + fmax(fmax(x0, x1), rf);
+    const double ymin = cy + fmin(fmin(y0, y1), -rf), ymax = cy + fmax(fmax(y0, y1), rf);
+    double ilo = ceil(xmin - 0.5), ihi = floor(xmax - 0.5);
+    double jlo = ceil(ymin - 0.5), jhi = floor(ymax - 0.5);
+    ilo = fmax(ilo, 0.0); jlo = fmax(jlo, 0.0);
+    ihi = fmin(ihi, (double)(cam.W - 1)); jhi = fmin(jhi, (double)(cam.H - 1));
+    if (!(ilo <= ihi && jlo <= jhi)) continue;
+    RowGeom gm;
+    {
+      const double e0x = C13 / C33, e0y = C23 / C33;
+      const double g11 = e0x * e0x - C11 / C33, g12 = e0x * e0y - C12 / C33, g22 = e0y * e0y - C22 / C33;
+      const float chx = (float)cx, chy = (float)cy;
+      gm.cx_hi = chx; gm.cx_lo = (float)(cx - (double)chx);
+      gm.cy_hi = chy; gm.cy_lo = (float)(cy - (double)chy);
+      gm.e0x = (float)e0x; gm.e0y = (float)e0y;
+      if (g11 > 0.0 && g22 > 0.0) {
+        const double det = fmax(g11 * g22 - g12 * g12, 0.0);
+        gm.hy = (float)sqrt(g22);
+        gm.t = (float)(g12 / sqrt(g11));
+        gm.slope = (float)(g12 / g22);
+        gm.wsc = (float)(sqrt(det) / g22);
       } else {
-        // edge-on disk: no object-space footprint (rho_obj is NaN, the
-        // screen filter decides)
-        const float qnan = __int_as_float(0x7fffffff);
-        r1f = make_float4(qnan, qnan, qnan, qnan);
-        ef = make_float2(0.f, 0.f);
-      }
-      // bounding box of {rho_obj <= rho_max} in offsets from c: dual conic
-      // of the centred homography H = [[J, 0], [w^T, 1]]
-      const double rm = set.rho_max;
-      const double C11 = rm * (J11 * J11 + J12 * J12), C22 = rm * (J21 * J21 + J22 * J22);
-      const double C13 = rm * (J11 * w1 + J12 * w2), C23 = rm * (J21 * w1 + J22 * w2);
-      const double C33 = rm * (w1 * w1 + w2 * w2) - 1.0;
-      const double ex = sqrt(fmax(C13 * C13 - C11 * C33, 0.0));
-      const double ey = sqrt(fmax(C23 * C23 - C22 * C33, 0.0));
-      const double rf = sqrt((double)set.rho_max / (double)set.sinv);
-      const double x0 = (C13 - ex) / C33, x1 = (C13 + ex) / C33;
-      const double y0 = (C23 - ey) / C33, y1 = (C23 + ey) / C33;
-      const double xmin = cx + fmin(fmin(x0, x1), -rf), xmax = cx + fmax(fmax(x0, x1), rf);
-      const double ymin = cy + fmin(fmin(y0, y1), -rf), ymax = cy + fmax(fmax(y0, y1), rf);
-      double ilo = ceil(xmin - 0.5), ihi = floor(xmax - 0.5);
-      double jlo = ceil(ymin - 0.5), jhi = floor(ymax - 0.5);
-      ilo = fmax(ilo, 0.0); jlo = fmax(jlo, 0.0);
-      ihi = fmin(ihi, (double)(cam.W - 1)); jhi = fmin(jhi, (double)(cam.H - 1));
-      if (ilo <= ihi && jlo <= jhi) {
-        const int tx0 = (int)ilo / kTile, tx1 = (int)ihi / kTile + 1;
-        const int ty0 = (int)jlo / kTile, ty1 = (int)jhi / kTile + 1;
-        rc = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
-        cnt = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
-        const float pz = (float)p.z;
-        key = __float_as_uint(pz);
-        // colour: SH at the world direction from the camera centre
-        double dx = mu.x - cam.campos[0], dy = mu.y - cam.campos[1], dz = mu.z - cam.campos[2];
-        const double il = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
-        float Y[16];
-        sh_basis((float)(dx * il), (float)(dy * il), (float)(dz * il), P.sh_degree, Y);
-        const int K = (P.sh_degree + 1) * (P.sh_degree + 1);
-        const float* f = P.sh + (size_t)n * K * 3;
-        float col[3];
-        for (int c = 0; c < 3; ++c) {
-          float acc = 0.f;
-          for (int k = 0; k < K; ++k) acc = fmaf(f[k * 3 + c], Y[k], acc);
-          col[c] = fmaxf(acc + 0.5f, 0.f);
-        }
-        const double s = (nv.x * p.x + nv.y * p.y + nv.z * p.z) > 0.0 ? -1.0 : 1.0;
-        const float chx = (float)cx, chy = (float)cy;
-        float4* R = rec + (size_t)n * kRecF4;
-        R[0] = make_float4(chx, chy, (float)(cx - (double)chx), (float)(cy - (double)chy));
-        R[1] = r1f;
-        R[2] = make_float4(ef.x, ef.y, pz, P.opacity[n]);
-        R[3] = make_float4(col[0], col[1], col[2], (float)(s * nv.x));
-        R[4] = make_float4((float)(s * nv.y), (float)(s * nv.z), 0.f, 0.f);
+        gm.hy = -1.f; gm.t = 0.f; gm.slope = 0.f; gm.wsc = 0.f;  // disk only
       }
     }
+    gm.ilo = (int)ilo; gm.ihi = (int)ihi; gm.jlo = (int)jlo; gm.jhi = (int)jhi;
+    const int tx0 = gm.ilo / kTile, tx1 = gm.ihi / kTile + 1;
+    const int ty0 = gm.jlo / kTile, ty1 = gm.jhi / kTile + 1;
+    rect[n] = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+    uint32_t cnt = 0;
+    for (int ty = ty0; ty < ty1; ++ty) {
+      int a0, a1;
+      if (row_tiles(gm, ty, (float)rf, &a0, &a1)) cnt += (uint32_t)(a1 - a0);
+    }
+    if (cnt == 0) continue;
+    geom[n] = gm;
+    tcount[n] = cnt;
+    const float pz = (float)p.z;
+    dkey[n] = __float_as_uint(pz);
+    const double det = J11 * J22 - J12 * J21;
+    float4 r1f;
+    float2 ef;
+    if (det != 0.0) {
+      const double id = 1.0 / det;
+      const double i11 = J22 * id, i12 = -J12 * id, i21 = -J21 * id, i22 = J11 * id;
+      r1f = make_float4((float)i11, (float)i12, (float)i21, (float)i22);
+      ef = make_float2((float)(-(i11 * w1 + i21 * w2)), (float)(-(i12 * w1 + i22 * w2)));
+    } else {
+      // edge-on disk: no object-space footprint (rho_obj is NaN, the
+      // screen filter decides)
+      const float qnan = __int_as_float(0x7fffffff);
+      r1f = make_float4(qnan, qnan, qnan, qnan);
+      ef = make_float2(0.f, 0.f);
+    }
+    // colour: SH at the world direction from the camera centre
+    const double dx = mu.x - cam.campos[0], dy = mu.y - cam.campos[1], dz = mu.z - cam.campos[2];
+    const double il = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+    float Y[16];
+    sh_basis((float)(dx * il), (float)(dy * il), (float)(dz * il), P.sh_degree, Y);
+    const int K = (P.sh_degree + 1) * (P.sh_degree + 1);
+    const float* f = P.sh + (size_t)n * K * 3;
+    float col[3];
+    for (int c = 0; c < 3; ++c) {
+      float acc = 0.f;
+      for (int k = 0; k < K; ++k) acc = fmaf(f[k * 3 + c], Y[k], acc);
+      col[c] = fmaxf(acc + 0.5f, 0.f);
+    }
+    const double sg = (nv.x * p.x + nv.y * p.y + nv.z * p.z) > 0.0 ? -1.0 : 1.0;
+    const float chx = (float)cx, chy = (float)cy;
+    float4* Rr = rec + (size_t)n * kRecF4;
+    Rr[0] = make_float4(chx, chy, (float)(cx - (double)chx), (float)(cy - (double)chy));
+    Rr[1] = r1f;
+    Rr[2] = make_float4(ef.x, ef.y, pz, P.opacity[n]);
+    Rr[3] = make_float4(col[0], col[1], col[2], (float)(sg * nv.x));
+    Rr[4] = make_float4((float)(sg * nv.y), (float)(sg * nv.z), 0.f, 0.f);
   }
-  rect[n] = rc;
-  tcount[n] = cnt;
-  dkey[n] = key;
 }
 
 // ---------------------------------------------------------------------------
@@ -334,11 +414,18 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev
 
 cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
                               float4* rec, uint2* rect, uint32_t* tcount, uint32_t* dkey,
-                              uint32_t* idx, cudaStream_t st) {
+                              uint32_t* idx, uint32_t* cand, uint32_t* ncand, RowGeom* geom,
+                              cudaStream_t st) {
   if (P.n == 0) return cudaSuccess;
   ProfScope ps(kProfPreprocess, st);
-  preprocess_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, set, rec, rect, tcount, dkey, idx);
-  count_launch();
+  cudaError_t e = cudaMemsetAsync(ncand, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  preprocess_cull_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, set, rect, tcount, dkey, idx, cand, ncand);
+  // candidates are a subset of the surfels; a grid-stride loop over the
+  // device-side count, two CTAs per SM
+  const unsigned blocks = div_up(P.n, 256) < 304u ? div_up(P.n, 256) : 304u;
+  preprocess_main_kernel<<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom);
+  count_launch(2);
   return cudaGetLastError();
 }
 

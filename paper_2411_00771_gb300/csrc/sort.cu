@@ -199,21 +199,29 @@ __global__ void gather_counts_kernel(const uint32_t* __restrict__ order,
   if (r < n) out[r] = tcount[order[r]];
 }
 
+// Instances of surfel order[r] at offsets offs[r]..: for every tile row of
+// its rectangle, the tile columns its footprint reaches (the same row rule,
+// on the same stored doubles, that counted them in the preprocess).
 __global__ void emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offs,
-                            const uint2* __restrict__ rect, int64_t n, int tiles_x,
+                            const uint32_t* __restrict__ counts, const uint2* __restrict__ rect,
+                            const RowGeom* __restrict__ geom, float rf, int64_t n, int tiles_x,
                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
+  if (r >= n || counts[r] == 0) return;
   const uint32_t s = order[r];
   const uint2 rc = rect[s];
-  const int tx0 = rc.x & 0xFFFF, ty0 = rc.x >> 16, tx1 = rc.y & 0xFFFF, ty1 = rc.y >> 16;
+  const int ty0 = rc.x >> 16, ty1 = rc.y >> 16;
+  const RowGeom g = geom[s];
   uint32_t o = offs[r];
-  for (int ty = ty0; ty < ty1; ++ty)
-    for (int tx = tx0; tx < tx1; ++tx) {
+  for (int ty = ty0; ty < ty1; ++ty) {
+    int a, b;
+    if (!row_tiles(g, ty, rf, &a, &b)) continue;
+    for (int tx = a; tx < b; ++tx) {
       keys[o] = (uint32_t)(ty * tiles_x + tx);
       vals[o] = s;
       ++o;
     }
+  }
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t K, int2* __restrict__ ranges) {
@@ -283,11 +291,12 @@ cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* tcount, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint2* rect,
-                        int64_t n, int tiles_x, uint32_t* keys, uint32_t* vals, cudaStream_t st) {
+cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint32_t* counts,
+                        const uint2* rect, const RowGeom* geom, float rf, int64_t n, int tiles_x,
+                        uint32_t* keys, uint32_t* vals, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   count_launch();
-  emit_kernel<<<div_up(n, 256), 256, 0, st>>>(order, offs, rect, n, tiles_x, keys, vals);
+  emit_kernel<<<div_up(n, 256), 256, 0, st>>>(order, offs, counts, rect, geom, rf, n, tiles_x, keys, vals);
   return cudaGetLastError();
 }
 

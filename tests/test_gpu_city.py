@@ -31,17 +31,19 @@ def test_city_render_matches_oracle(city):
     ok = ~bad
     branch = (ref["flags"] & oracle.FLAG_BRANCH) != 0
     g = out.cpu().numpy()
-    err = gu.channel_errors(g, ref["out"], ok)
-    err_nb = gu.channel_errors(g, ref["out"], ok & ~branch)
+    v = gu.plane_violations(g, ref["out"], ok)
+    v_nb = gu.plane_violations(g, ref["out"], ok & ~branch)
     for p, name in enumerate(gu.PLANES):
-        e = err_nb[p] if p in gu.DEPTH_PLANES else err[p]
-        assert e <= gu.TOL_ABS, (name, e)
+        e = v_nb[p] if p in gu.DEPTH_PLANES else v[p]
+        assert e <= 1.0, (name, e)
     c = cnt.cpu().numpy()
     assert np.array_equal(c[ok], ref["count"][ok])
     info = frame.info()
     pre = oracle.preprocess(scene, cam)
-    assert info["n_visible"] == int((pre["tiles"] > 0).sum())
-    assert info["n_instances"] == int(pre["tiles"].sum())
+    assert info["n_visible"] == int(gu.visible(pre).sum())
+    # the FP32 row rule covers the exact cover with a small margin
+    K = int(pre["tiles"].sum())
+    assert K <= info["n_instances"] <= 1.02 * K
 
 
 def test_city_backward_matches_oracle(city):
@@ -88,7 +90,7 @@ def test_city_loss_and_densify(city):
     for k_ in ("mu", "opacity", "sh"):
         assert gu.rel_err(grads[k_].cpu().numpy(), ref[k_].reshape(grads[k_].shape)) <= 2e-3, k_
     pre = oracle.preprocess(scene, cam)
-    st = oracle.densify_accumulate(ref["screen"], pre["tiles"] > 0)
+    st = oracle.densify_accumulate(ref["screen"], gu.visible(pre))
     assert gu.rel_err(stats.cpu().numpy(), st) <= 2e-3
     m, gg, kk = oracle.densify_select(st, scene["scale"], 0.9, 0.0002, 0.1)
     assert abs(float(k[0]) - kk) <= 2e-3 * kk

@@ -35,12 +35,12 @@ def _compare_render(scene, cam, settings=None, frac=0.01, tol=gu.TOL_ABS):
     ref = oracle.render(scene, cam, settings=settings)
     ok = _flags_ok(ref["flags"], frac)
     g = out.cpu().numpy()
-    err = gu.channel_errors(g, ref["out"], ok)
     branch = (ref["flags"] & oracle.FLAG_BRANCH) != 0
-    err_nb = gu.channel_errors(g, ref["out"], ok & ~branch)
+    v = gu.plane_violations(g, ref["out"], ok)
+    v_nb = gu.plane_violations(g, ref["out"], ok & ~branch)
     for p, name in enumerate(gu.PLANES):
-        e = err_nb[p] if p in gu.DEPTH_PLANES else err[p]
-        assert e <= tol, f"plane {name}: max scaled error {e:.3e}"
+        e = v_nb[p] if p in gu.DEPTH_PLANES else v[p]
+        assert e <= tol / gu.TOL_ABS, f"plane {name}: error {e:.3f} x its tolerance"
     c = cnt.cpu().numpy()
     assert np.array_equal(c[ok], ref["count"][ok])
     return sc, d, out, cnt, frame, ref
@@ -93,45 +93,44 @@ def test_large_splats_cover_many_tiles():
     _compare_render(scene, cam)
 
 
-def test_tile_rects_lists_and_ranges_bit_exact():
+def test_tile_rects_and_tile_lists():
+    """Tile rectangles bit-exact; every tile list a superset of the exact
+    per-row cover (the oracle's FP64 rule), inside the surfel's rectangle, in
+    compositing order (centre depth rounded to FP32, then index), with a
+    small excess from the FP32 rule's safety margin."""
     scene, cam, _, _ = syn.tiny_scene(seed=21, n=3000, width=200, height=120, fx=150.0,
                                       log_scale_range=(-4.0, -1.5))
+    # a third of the disks elongated (one axis x10-60): long thin footprints
+    rng = np.random.default_rng(21)
+    k = rng.uniform(size=3000) < 0.33
+    scene["scale"][k, 0] *= np.exp(rng.uniform(np.log(10), np.log(60), k.sum())).astype(np.float32)
     sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
     vals, ranges, rects = [t.cpu().numpy() for t in frame.lists()]
-    pre = oracle.preprocess(scene, cam)
-    # rectangles: exact except where the FP64 box edge sits within 1e-3 px of
-    # a pixel-centre boundary
-    live = pre["live"] > 0
-    exp_rect = np.where(live[:, None], pre["rect"], 0)
-    exp_rect = np.where((pre["tiles"] > 0)[:, None], exp_rect, 0)
+    start, idx, pre = oracle.tile_lists(scene, cam)
+    exp_rect = np.where((pre["live"] > 0)[:, None], pre["rect"], 0)
     bb = pre["bbox"]
-    near = np.any(np.abs((bb - 0.5) - np.round(bb - 0.5)) < 1e-3, axis=1)
+    near = np.any(np.abs((bb - 0.5) - np.round(bb - 0.5)) < 1e-6, axis=1)
     diff = np.any(rects != exp_rect, axis=1)
     assert np.all(~diff | near), np.nonzero(diff & ~near)[0][:10]
-    assert diff.sum() == 0
-    # tile lists rebuilt from the GPU rectangles and the centre depth rounded
-    # to FP32 (the compositing order key), ties by surfel index
     tx = (cam["width"] + 15) // 16
     ntiles = ranges.shape[0]
-    lists = [[] for _ in range(ntiles)]
-    order = np.lexsort((np.arange(len(pre["zkey"])), pre["zkey"]))
-    for s in order:
-        r = rects[s]
-        if r[2] <= r[0] or r[3] <= r[1]:
-            continue
-        for ty in range(r[1], r[3]):
-            for tx_ in range(r[0], r[2]):
-                lists[ty * tx + tx_].append(s)
-    pos = 0
+    zk = pre["zkey"]
+    extra = 0
     for t in range(ntiles):
-        L = np.asarray(lists[t], np.int32)
-        if len(L) == 0:
-            assert ranges[t, 1] - ranges[t, 0] == 0
-            continue
-        assert ranges[t, 0] == pos and ranges[t, 1] == pos + len(L), t
-        assert np.array_equal(vals[pos:pos + len(L)], L), t
-        pos += len(L)
-    assert pos == len(vals)
+        exp = idx[start[t]:start[t + 1]]
+        got = vals[ranges[t, 0]:ranges[t, 1]]
+        assert set(exp.tolist()) <= set(got.tolist()), t
+        extra += len(got) - len(exp)
+        # order: (FP32 depth key, index) ascending
+        key = np.stack([zk[got], got.astype(np.float64)], 1)
+        assert np.all((np.diff(key[:, 0]) > 0) | ((np.diff(key[:, 0]) == 0) & (np.diff(key[:, 1]) > 0))), t
+        ty_, tx_ = divmod(t, tx)
+        r = rects[got]
+        assert np.all((r[:, 0] <= tx_) & (tx_ < r[:, 2]) & (r[:, 1] <= ty_) & (ty_ < r[:, 3])), t
+    assert extra <= 0.02 * len(idx), (extra, len(idx))
+    assert int(frame.info()["n_instances"]) == len(vals)
+    nz = ranges[:, 1] > ranges[:, 0]
+    assert ranges[nz, 0].min(initial=0) == 0 and ranges[nz, 1].max(initial=0) == len(vals)
 
 
 def _synthetic_render_planes(rng, H, W):
@@ -225,7 +224,7 @@ def test_training_loss_gradients_and_densify_stats():
     ref = oracle.backward(scene, cam, L["adj"])
     _assert_grads(grads, screen, ref, tol=2e-3)
     pre = oracle.preprocess(scene, cam)
-    st = oracle.densify_accumulate(ref["screen"], pre["tiles"] > 0)
+    st = oracle.densify_accumulate(ref["screen"], gu.visible(pre))
     assert gu.rel_err(stats.cpu().numpy(), st) <= 1e-3
     m, gg, kk = oracle.densify_select(st, scene["scale"], 0.9, 0.0, 0.1)
     assert abs(float(k[0]) - kk) <= 1e-3 * kk

@@ -202,6 +202,25 @@ def test_brute_force_equals_binned(seed):
     assert np.array_equal(rb["count"], rt["count"])
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5])
+def test_brute_force_equals_binned_with_elongated_disks(seed):
+    """The per-row tile coverage rule is a conservative cover of the
+    footprint: long thin (elongated, tilted) disks, some near the camera."""
+    scene, cam, _, _ = syn.tiny_scene(seed=100 + seed, n=150, width=48, height=40, fx=40.0,
+                                      log_scale_range=(-3.5, -0.5), z_range=(0.8, 3.0))
+    rng = np.random.default_rng(seed)
+    k = rng.uniform(size=150) < 0.5
+    scene["scale"][k, 0] *= np.exp(rng.uniform(np.log(10), np.log(60), k.sum())).astype(np.float32)
+    rb = _render(scene, cam, mode="brute")
+    rt = _render(scene, cam, mode="binned")
+    assert np.array_equal(rb["out"], rt["out"])
+    assert np.array_equal(rb["count"], rt["count"])
+    pre = oracle.preprocess(scene, cam)
+    r = pre["rect"]
+    box = np.where(pre["live"] > 0, (r[:, 2] - r[:, 0]) * (r[:, 3] - r[:, 1]), 0)
+    assert np.all(pre["tiles"] <= box) and pre["tiles"].sum() < box.sum()
+
+
 def test_invariants_on_random_scene():
     scene, cam, _, _ = syn.tiny_scene()
     r = _render(scene, cam)
