@@ -269,7 +269,9 @@ def run_ours(args):
             "roofline": roofline,
             "stage_ms": breakdown,
             "work": {"instances": info["n_instances"], "visible": info["n_visible"],
-                     "pairs_evaluated": E, "pairs_blended": Bl, "bwd_pairs_replayed": R},
+                     "pairs_evaluated": E, "pairs_blended": Bl, "bwd_pairs_replayed": R,
+                     "bwd_warp_steps": info["bwd_warp_entries"],
+                     "bwd_lanes_per_step": round(info["bwd_warp_lanes"] / max(1, info["bwd_warp_entries"]), 2)},
             "clocks": clk,
             "cpu_baseline": cpu,
         }

@@ -152,6 +152,8 @@ typedef struct {
   int64_t pairs_evaluated;  /* list entries the forward blend evaluated      */
   int64_t pairs_blended;    /* pairs that entered the composite              */
   int64_t bwd_pairs_evaluated; /* list entries the last backward replayed    */
+  int64_t bwd_warp_entries;    /* (warp, entry) steps with a blended pair     */
+  int64_t bwd_warp_lanes;      /* blended pairs summed over those steps       */
   int32_t tiles_x, tiles_y;
 } gs_frame_info;
 /* Counters of a frame (synchronises `stream`). */

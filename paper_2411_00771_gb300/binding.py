@@ -68,7 +68,8 @@ class gs_scene_desc(ctypes.Structure):
 class gs_frame_info(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_int64), ("n_visible", ctypes.c_int64),
                 ("pairs_evaluated", ctypes.c_int64), ("pairs_blended", ctypes.c_int64),
-                ("bwd_pairs_evaluated", ctypes.c_int64), ("tiles_x", ctypes.c_int32),
+                ("bwd_pairs_evaluated", ctypes.c_int64), ("bwd_warp_entries", ctypes.c_int64),
+                ("bwd_warp_lanes", ctypes.c_int64), ("tiles_x", ctypes.c_int32),
                 ("tiles_y", ctypes.c_int32)]
 
 

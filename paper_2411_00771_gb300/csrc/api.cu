@@ -194,6 +194,7 @@ struct gs_frame {
   Buffers buf;
   float4* rec = nullptr;
   uint2* rect = nullptr;
+  RowGeom* geom = nullptr;
   uint32_t* tcount = nullptr;
   uint32_t* vals = nullptr;
   int2* ranges = nullptr;
@@ -350,7 +351,8 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   uint32_t* offs = tmp.get<uint32_t>(n > 0 ? n : 1, st);
   uint32_t* rtmp = tmp.get<uint32_t>(radix_tmp_words(n) + scan_tmp_words(n) + 4, st);
   uint32_t* cand = tmp.get<uint32_t>(n > 0 ? n : 1, st);
-  RowGeom* geom = tmp.get<RowGeom>(n > 0 ? n : 1, st);
+  RowGeom* geom = f->buf.get<RowGeom>(n > 0 ? n : 1, st);
+  f->geom = geom;
   if (!f->rec || !f->rect || !f->tcount || !f->ranges || !f->last || !f->med || !f->counters || !dkey ||
       !idx || !dkey2 || !idx2 || !cnts || !offs || !rtmp || !cand || !geom)
     return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed"));
@@ -388,8 +390,8 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   f->vals = tv;
   f->buf.release(tv == vals ? vals2 : vals, st);
   GS_CKC(launch_ranges(tk, K, f->ranges, ntiles, st));
-  GS_CKC(launch_blend_fwd(cam, set, f->rec, f->vals, f->ranges, out, n_contrib, f->last, f->med,
-                          f->counters, st));
+  GS_CKC(launch_blend_fwd(cam, set, f->rec, f->geom, f->vals, f->ranges, out, n_contrib, f->last,
+                          f->med, f->counters, st));
 #undef GS_CKC
   tmp.release_all(st);
   if (saved) {
@@ -410,6 +412,8 @@ gs_status gs_frame_get_info(gs_frame* f, gs_frame_info* info, void* stream) {
   info->pairs_evaluated = (int64_t)h[0];
   info->pairs_blended = (int64_t)h[1];
   info->bwd_pairs_evaluated = (int64_t)h[2];
+  info->bwd_warp_entries = (int64_t)h[3];
+  info->bwd_warp_lanes = (int64_t)h[4];
   info->tiles_x = f->cam.tiles_x;
   info->tiles_y = f->cam.tiles_y;
   // visible surfels (non-empty tile rectangle), counted on the host (debug path)
@@ -478,11 +482,11 @@ gs_status gs_backward(gs_scene* sc, gs_frame* f, const float* const* adj_sets,
   float* grec = static_cast<float*>(sc->al.get(sizeof(float) * kGradRec * (size_t)(n > 0 ? n : 1), st));
   if (!grec) return fail(GS_ERR_OOM, "gs_backward: scratch allocation failed");
   cudaError_t e = cudaMemsetAsync(grec, 0, sizeof(float) * kGradRec * (size_t)n, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(f->counters + 2, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->counters + 2, 0, 3 * sizeof(unsigned long long), st);
   const SetDev set = to_dev(sc->settings);
   if (e == cudaSuccess)
-    e = launch_blend_bwd(f->cam, set, f->rec, f->vals, f->ranges, f->out, f->last, f->med, adj, grec,
-                         screen_grads, n, f->counters, st);
+    e = launch_blend_bwd(f->cam, set, f->rec, f->geom, f->vals, f->ranges, f->out, f->last, f->med, adj,
+                         grec, screen_grads, n, f->counters, st);
   if (e == cudaSuccess) e = launch_preprocess_bwd(sc->P, f->cam, f->tcount, grec, *grads, st);
   sc->al.put(grec, sizeof(float) * kGradRec * (size_t)(n > 0 ? n : 1), st);
   if (e != cudaSuccess) return cuda_fail(e, "gs_backward");

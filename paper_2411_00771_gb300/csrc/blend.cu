@@ -1,13 +1,15 @@
 // Per-pixel compositing (forward) and its adjoint (reverse replay).
 //
 // Forward (Eq. 1, Sec. 3.1, with the 2DGS surfel model and the low-pass
-// filter of Sec. 3.2): one CTA per 16 x 16 tile, one thread per pixel.  The
-// tile's depth-sorted surfel list is staged through shared memory in
-// batches of 256 records; each pixel intersects its ray with every surfel
-// plane (rho_obj), takes the screen-space filter (rho_scr) where smaller,
-// and composites front to back until the transmittance would drop below
-// T_min.  Colour, alpha, expected and inverse depth, median depth, normal
-// and the depth-distortion sum are accumulated in registers.
+// filter of Sec. 3.2): one CTA per 16 x 16 tile, one thread per pixel, each
+// warp an 8 x 4 block of pixels.  The tile's depth-sorted surfel list is
+// staged through shared memory in batches of 256 entries; while staging,
+// one thread per entry works out which of the tile's eight warp blocks the
+// entry's footprint reaches (a conservative cover from the stored footprint
+// shape), and warps skip entries that cannot touch them.  Each pixel
+// intersects its ray with the surfel plane (rho_obj), takes the
+// screen-space filter (rho_scr) where smaller, and composites front to back
+// until the transmittance would drop below T_min.
 //
 // Backward: the same tiles replay each pixel's list back to front from the
 // final transmittance, T_before = T_after / (1 - alpha), with suffix sums
@@ -21,6 +23,62 @@
 namespace gs2d {
 namespace {
 
+// Hardware approximations (relative error about 2^-22), the same
+// instructions in both blends so that the replay reproduces the forward's
+// decisions exactly.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -log2(e) / 2
+
+// pixel of thread t within its tile: warp w covers columns 8 (w & 1) .. +7
+// and rows 4 (w >> 1) .. +3
+__device__ __forceinline__ int local_x(int t) { return (((t >> 5) & 1) << 3) | (t & 7); }
+__device__ __forceinline__ int local_y(int t) { return ((t >> 6) << 2) | ((t >> 3) & 3); }
+
+// Staged entry: s0 = (c.x, c.y relative to the tile origin, e.x, e.y),
+// s1 = Ji, s2 = (p_z, opacity, r, g), s3 = (b, n.x, n.y, n.z); wmask bit w
+// set when the footprint may reach warp w's pixel block.
+struct Staged {
+  float4 s0, s1, s2, s3;
+  uint32_t wmask;
+};
+
+__device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
+                                              const RowGeom* __restrict__ geom, uint32_t s,
+                                              int tx0, int ty0, int H, float rf) {
+  const float4* R = rec + (size_t)s * kRecF4;
+  const float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4];
+  Staged e;
+  // centre relative to the tile origin: (c_hi - x0) + c_lo keeps the
+  // offset accurate to its own rounding
+  e.s0 = make_float4(__fadd_rn(__fsub_rn(r0.x, (float)tx0), r0.z),
+                     __fadd_rn(__fsub_rn(r0.y, (float)ty0), r0.w), r2.x, r2.y);
+  e.s1 = r1;
+  e.s2 = make_float4(r2.z, r2.w, r3.x, r3.y);
+  e.s3 = make_float4(r3.z, r3.w, r4.x, r4.y);
+  const RowGeom g = geom[s];
+  uint32_t m = 0u;
+#pragma unroll
+  for (int b = 0; b < kTile / 4; ++b) {
+    const int ja = ty0 + 4 * b;
+    if (ja >= H) break;
+    int ilo, ihi;
+    if (!band_pixels(g, ja, min(ja + 3, H - 1), rf, &ilo, &ihi)) continue;
+    if (ilo <= tx0 + 7 && ihi >= tx0) m |= 1u << (2 * b);
+    if (ilo <= tx0 + 15 && ihi >= tx0 + 8) m |= 1u << (2 * b + 1);
+  }
+  e.wmask = m;
+  return e;
+}
+
 struct Pair {
   float dx, dy;    // pixel offset from the projected centre
   float nu, nv;    // Ji d
@@ -32,38 +90,42 @@ struct Pair {
   bool hit;        // rho <= rho_max and alpha >= alpha_min
 };
 
-// Shared by both blends; written with explicit round-to-nearest intrinsics
-// so that forward and backward take bit-identical decisions.
-__device__ __forceinline__ Pair eval_pair(float px, float py, float4 r0, float4 r1, float4 r2,
+// Shared by both blends; explicit round-to-nearest operations so that the
+// forward and the backward take bit-identical decisions.
+__device__ __forceinline__ Pair eval_pair(float lx, float ly, float4 s0, float4 s1, float opac,
                                           const SetDev& set) {
   Pair q;
-  q.dx = __fsub_rn(__fsub_rn(px, r0.x), r0.z);
-  q.dy = __fsub_rn(__fsub_rn(py, r0.y), r0.w);
-  const float den = __fmaf_rn(r2.x, q.dx, __fmaf_rn(r2.y, q.dy, 1.0f));
-  q.nu = __fmaf_rn(r1.x, q.dx, __fmul_rn(r1.y, q.dy));
-  q.nv = __fmaf_rn(r1.z, q.dx, __fmul_rn(r1.w, q.dy));
-  q.rden = __frcp_rn(den);
+  q.dx = __fsub_rn(lx, s0.x);
+  q.dy = __fsub_rn(ly, s0.y);
+  const float den = __fmaf_rn(s0.z, q.dx, __fmaf_rn(s0.w, q.dy, 1.0f));
+  q.nu = __fmaf_rn(s1.x, q.dx, __fmul_rn(s1.y, q.dy));
+  q.nv = __fmaf_rn(s1.z, q.dx, __fmul_rn(s1.w, q.dy));
+  q.rden = rcp_approx(den);
   const float u = __fmul_rn(q.nu, q.rden), v = __fmul_rn(q.nv, q.rden);
   const float rho_obj = den > 0.f ? __fmaf_rn(u, u, __fmul_rn(v, v)) : INFINITY;
   const float rho_scr = __fmul_rn(set.sinv, __fmaf_rn(q.dx, q.dx, __fmul_rn(q.dy, q.dy)));
   q.obj = rho_obj <= rho_scr;  // false for NaN (edge-on disks)
   q.rho = q.obj ? rho_obj : rho_scr;
-  q.G = __expf(__fmul_rn(-0.5f, q.rho));
-  q.alpha = fminf(set.alpha_max, __fmul_rn(r2.w, q.G));
+  q.G = ex2_approx(__fmul_rn(kNegHalfLog2e, q.rho));
+  q.alpha = fminf(set.alpha_max, __fmul_rn(opac, q.G));
   q.hit = (q.rho <= set.rho_max) && (q.alpha >= set.alpha_min);
   return q;
 }
 
 __global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
-    CamDev cam, SetDev set, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
-    const int2* __restrict__ ranges, float* __restrict__ out, int32_t* __restrict__ n_contrib,
-    int32_t* __restrict__ last, int32_t* __restrict__ med, unsigned long long* __restrict__ counters) {
-  __shared__ float4 s0[kBlock], s1[kBlock], s2[kBlock], s3[kBlock], s4[kBlock];
+    CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
+    const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, float* __restrict__ out,
+    int32_t* __restrict__ n_contrib, int32_t* __restrict__ last, int32_t* __restrict__ med,
+    unsigned long long* __restrict__ counters) {
+  __shared__ float4 s0[kBlock], s1[kBlock], s2[kBlock], s3[kBlock];
+  __shared__ uint32_t sm[kBlock];
   const int tile = blockIdx.y * cam.tiles_x + blockIdx.x;
-  const int px = blockIdx.x * kTile + (threadIdx.x & (kTile - 1));
-  const int py = blockIdx.y * kTile + (threadIdx.x >> 4);
+  const int tx0 = blockIdx.x * kTile, ty0 = blockIdx.y * kTile;
+  const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
+  const int px = tx0 + lxi, py = ty0 + lyi;
+  const int warp = threadIdx.x >> 5;
   const bool inside = px < cam.W && py < cam.H;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const float lx = (float)lxi + 0.5f, ly = (float)lyi + 0.5f;
   const int2 rg = ranges[tile];
   const int len = rg.y - rg.x;
   bool done = !inside;
@@ -79,19 +141,20 @@ __global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
     if (__syncthreads_count(done) == kBlock) break;
     const int j = b0 + threadIdx.x;
     if (j < len) {
-      const float4* R = rec + (size_t)vals[rg.x + j] * kRecF4;
-      s0[threadIdx.x] = R[0];
-      s1[threadIdx.x] = R[1];
-      s2[threadIdx.x] = R[2];
-      s3[threadIdx.x] = R[3];
-      s4[threadIdx.x] = R[4];
+      const Staged e = stage_entry(rec, geom, vals[rg.x + j], tx0, ty0, cam.H, rf);
+      s0[threadIdx.x] = e.s0;
+      s1[threadIdx.x] = e.s1;
+      s2[threadIdx.x] = e.s2;
+      s3[threadIdx.x] = e.s3;
+      sm[threadIdx.x] = e.wmask;
     }
     __syncthreads();
     const int nb = min(kBlock, len - b0);
     for (int k = 0; k < nb && !done; ++k) {
+      if (!((sm[k] >> warp) & 1u)) continue;  // footprint misses this warp's block
       ++evaluated;
-      const float4 r2 = s2[k];
-      const Pair q = eval_pair(fx, fy, s0[k], s1[k], r2, set);
+      const float4 e2 = s2[k];
+      const Pair q = eval_pair(lx, ly, s0[k], s1[k], e2.y, set);
       if (!q.hit) continue;
       const float Tn = T * (1.f - q.alpha);
       if (Tn < set.T_min) {
@@ -99,20 +162,20 @@ __global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
         break;
       }
       const float w = q.alpha * T;
-      const float z = q.obj ? r2.z * q.rden : r2.z;
-      const float4 r3 = s3[k], r4 = s4[k];
-      C0 = fmaf(w, r3.x, C0);
-      C1 = fmaf(w, r3.y, C1);
-      C2 = fmaf(w, r3.z, C2);
+      const float z = q.obj ? e2.x * q.rden : e2.x;
+      const float4 e3 = s3[k];
+      C0 = fmaf(w, e2.z, C0);
+      C1 = fmaf(w, e2.w, C1);
+      C2 = fmaf(w, e3.x, C2);
       if (cnt == 0) zr = z;
       const float zs = z - zr;
       D = fmaf(2.f * w, fmaf(zs, A, -Zs), D);
       A += w;
       Zs = fmaf(w, zs, Zs);
-      I += w / z;
-      N0 = fmaf(w, r3.w, N0);
-      N1 = fmaf(w, r4.x, N1);
-      N2 = fmaf(w, r4.y, N2);
+      I = fmaf(w, rcp_approx(z), I);
+      N0 = fmaf(w, e3.y, N0);
+      N1 = fmaf(w, e3.z, N1);
+      N2 = fmaf(w, e3.w, N2);
       if (T > 0.5f) {
         M = z;
         medpos = b0 + k;
@@ -167,48 +230,82 @@ __global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
 // ---------------------------------------------------------------------------
 // Backward.
 
-constexpr int kSlots = 32;  // padded length of the per-pair gradient vector
 constexpr int kMaxSets = 3;
-// gradient vector layout: [0..15] per-surfel record, [16 + 2 s, 17 + 2 s]
-// screen-space gradient of set s
-constexpr int kAcc = kGradRec + 2 * kMaxSets;  // 22
 
-// Sum of v[q] over the warp for every q; afterwards lane q holds the sum of
-// slot q.  31 shuffles for 32 slots (reduce-scatter by halving).
-__device__ __forceinline__ float warp_reduce_scatter(float (&v)[kSlots]) {
-  const int lane = threadIdx.x & 31;
+// Per-pair gradient vector.  General layout (any adjoint planes):
+//   [0..15] per-surfel record (d Ji, d e, d c, d p_z, d opacity, d rgb,
+//   d normal), [16 + 2 s, 17 + 2 s] screen-space gradient of set s.
+// Loss layout (set 0 on colour and inverse depth only, later sets on
+// colour): the normal slots are dropped, [0..12] record without d normal,
+// [13 + 2 s, 14 + 2 s] screen gradients; the flush maps them back.
+template <bool kLoss>
+struct Layout {
+  static constexpr int kRec = kLoss ? 13 : kGradRec;
+  static constexpr int kN = kRec + 2 * kMaxSets;  // 19 or 22
+};
+
+// Balanced reduce-scatter of N values over the warp: at each halving level
+// the lanes whose bit is clear keep the first ceil(N/2) values and the others
+// the rest, exchanging the halves they do not keep; N values need about
+// N + 5 shuffles.  Afterwards v[0] holds the warp sum of one slot, given by
+// rs_slot() for the lane (or nothing when rs_slot() returns -1).
+template <int O, int N>
+__device__ __forceinline__ void rs_level(float* v, int lane) {
+  constexpr int L = (N + 1) / 2, H = N - L;
+  const bool up = (lane & O) != 0;
 #pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i) {
-      const float send = up ? v[i] : v[i + o];
-      const float keep = up ? v[i + o] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
+  for (int i = 0; i < L; ++i) {
+    const float hi = (i < H) ? v[L + i] : 0.f;
+    const float send = up ? v[i] : hi;
+    const float keep = up ? hi : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
   }
-  return v[0];
+  if constexpr (O > 1) rs_level<O / 2, L>(v, lane);
 }
 
+template <int N>
+__device__ __forceinline__ int rs_slot(int lane) {
+  int n = N, real = N, slot = 0;
+  for (int o = 16; o >= 1; o >>= 1) {
+    const int L = (n + 1) / 2;
+    if (lane & o) {
+      slot += L;
+      real = real - L > 0 ? real - L : 0;
+    } else {
+      real = real < L ? real : L;
+    }
+    n = L;
+  }
+  return real > 0 ? slot : -1;
+}
+
+template <bool kLoss>
 __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
-    CamDev cam, SetDev set, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
-    const int2* __restrict__ ranges, const float* __restrict__ out, const int32_t* __restrict__ last,
-    const int32_t* __restrict__ med, AdjDev adj, float* __restrict__ grec,
-    float* __restrict__ screen, int n, unsigned long long* __restrict__ counters) {
-  __shared__ float4 s0[kBlock], s1[kBlock], s2[kBlock], s3[kBlock], s4[kBlock];
+    CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
+    const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, const float* __restrict__ out,
+    const int32_t* __restrict__ last, const int32_t* __restrict__ med, AdjDev adj,
+    float* __restrict__ grec, float* __restrict__ screen, int n,
+    unsigned long long* __restrict__ counters) {
+  using LY = Layout<kLoss>;
+  constexpr int kN = LY::kN;
+  __shared__ float4 s0[kBlock], s1[kBlock], s2[kBlock], s3[kBlock];
+  __shared__ uint32_t sm[kBlock];
   __shared__ uint32_t sid[kBlock];
-  __shared__ float acc[kBlock][kAcc + 1];
+  __shared__ float acc[kBlock][kN + 1];
   __shared__ int smax;
   const int tile = blockIdx.y * cam.tiles_x + blockIdx.x;
-  const int px = blockIdx.x * kTile + (threadIdx.x & (kTile - 1));
-  const int py = blockIdx.y * kTile + (threadIdx.x >> 4);
+  const int tx0 = blockIdx.x * kTile, ty0 = blockIdx.y * kTile;
+  const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
+  const int px = tx0 + lxi, py = ty0 + lyi;
+  const int warp = threadIdx.x >> 5;
   const bool inside = px < cam.W && py < cam.H;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  const float lx = (float)lxi + 0.5f, ly = (float)lyi + 0.5f;
   const int2 rg = ranges[tile];
   const size_t HW = (size_t)cam.W * cam.H;
   const size_t p = inside ? (size_t)py * cam.W + px : 0;
   const int lane = threadIdx.x & 31;
   const int nsets = adj.n_sets;
+  const int myslot = rs_slot<kN>(lane);
 
   int lastpos = 0, medpos = -1;
   float T = 1.f, A = 0.f, Z = 0.f, Af = 0.f, Zf = 0.f;
@@ -222,10 +319,7 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
   }
   if (inside) {
     lastpos = last[p];
-    medpos = med[p];
     T = out[11 * HW + p];
-    Af = A = out[3 * HW + p];
-    Zf = Z = out[4 * HW + p];
 #pragma unroll
     for (int s = 0; s < kMaxSets; ++s) {
       if (s >= nsets) break;
@@ -237,21 +331,26 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
     }
     const float* a = adj.set[0];
     const uint32_t m = adj.mask[0];
-    if (m & (1u << 3)) gA = a[3 * HW + p];
-    if (m & (1u << 4)) gZ = a[4 * HW + p];
     if (m & (1u << 5)) gI = a[5 * HW + p];
-    if (m & (1u << 6)) gMed = a[6 * HW + p];
-    if (m & (1u << 7)) gN0 = a[7 * HW + p];
-    if (m & (1u << 8)) gN1 = a[8 * HW + p];
-    if (m & (1u << 9)) gN2 = a[9 * HW + p];
-    if (m & (1u << 10)) gD = a[10 * HW + p];
+    if constexpr (!kLoss) {
+      medpos = med[p];
+      Af = A = out[3 * HW + p];
+      Zf = Z = out[4 * HW + p];
+      if (m & (1u << 3)) gA = a[3 * HW + p];
+      if (m & (1u << 4)) gZ = a[4 * HW + p];
+      if (m & (1u << 6)) gMed = a[6 * HW + p];
+      if (m & (1u << 7)) gN0 = a[7 * HW + p];
+      if (m & (1u << 8)) gN1 = a[8 * HW + p];
+      if (m & (1u << 9)) gN2 = a[9 * HW + p];
+      if (m & (1u << 10)) gD = a[10 * HW + p];
+    }
   }
   if (threadIdx.x == 0) smax = 0;
   __syncthreads();
   atomicMax(&smax, lastpos);
   __syncthreads();
   const int maxlast = smax;
-  unsigned replayed = 0;
+  unsigned replayed = 0, wentries = 0, wlanes = 0;
 
   for (int bend = maxlast; bend > 0; bend -= kBlock) {
     const int b0 = bend > kBlock ? bend - kBlock : 0;
@@ -260,120 +359,125 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
     if (threadIdx.x < nb) {
       const uint32_t s = vals[rg.x + b0 + threadIdx.x];
       sid[threadIdx.x] = s;
-      const float4* R = rec + (size_t)s * kRecF4;
-      s0[threadIdx.x] = R[0];
-      s1[threadIdx.x] = R[1];
-      s2[threadIdx.x] = R[2];
-      s3[threadIdx.x] = R[3];
-      s4[threadIdx.x] = R[4];
+      const Staged e = stage_entry(rec, geom, s, tx0, ty0, cam.H, rf);
+      s0[threadIdx.x] = e.s0;
+      s1[threadIdx.x] = e.s1;
+      s2[threadIdx.x] = e.s2;
+      s3[threadIdx.x] = e.s3;
+      sm[threadIdx.x] = e.wmask;
     }
-    for (int i = threadIdx.x; i < nb * (kAcc + 1); i += kBlock) (&acc[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < nb * (kN + 1); i += kBlock) (&acc[0][0])[i] = 0.f;
     __syncthreads();
     for (int kk = nb - 1; kk >= 0; --kk) {
+      if (!((sm[kk] >> warp) & 1u)) continue;  // footprint misses this warp's block
       const int k = b0 + kk;
       Pair q;
       q.hit = false;
-      const float4 r1 = s1[kk], r2 = s2[kk];
+      const float4 e0 = s0[kk], e1 = s1[kk], e2 = s2[kk];
       if (k < lastpos) {
         ++replayed;
-        q = eval_pair(fx, fy, s0[kk], r1, r2, set);
+        q = eval_pair(lx, ly, e0, e1, e2.y, set);
       }
       const bool contrib = q.hit;
-      if (__ballot_sync(0xffffffffu, contrib) == 0u) continue;
-      float v[kSlots];
+      const unsigned ballot = __ballot_sync(0xffffffffu, contrib);
+      if (ballot == 0u) continue;
+      ++wentries;
+      wlanes += __popc(ballot);
+      float v[kN];
 #pragma unroll
-      for (int i = 0; i < kSlots; ++i) v[i] = 0.f;
-      {
-        if (contrib) {
-          const float4 r3 = s3[kk], r4 = s4[kk];
-          const float om = 1.f - q.alpha;
-          const float rom = 1.f / om;
-          T = T * rom;  // transmittance before this pair
-          const float w = q.alpha * T;
-          const float z = q.obj ? r2.z * q.rden : r2.z;
+      for (int i = 0; i < kN; ++i) v[i] = 0.f;
+      if (contrib) {
+        const float4 e3 = s3[kk];
+        const float rom = rcp_approx(1.f - q.alpha);
+        T = T * rom;  // transmittance before this pair
+        const float w = q.alpha * T;
+        const float pz = e2.x;
+        const float z = q.obj ? pz * q.rden : pz;
+        const float rz = rcp_approx(z);
+        float dLdw = gC[0][0] * e2.z + gC[0][1] * e2.w + gC[0][2] * e3.x + gI * rz;
+        float dzv = -w * gI * rz * rz;
+        if constexpr (!kLoss) {
           const float Ap = A - w, Zp = Z - w * z;
           const float dDdw = 2.f * (z * Ap - Zp + (Zf - Z) - z * (Af - A));
-          const float rz = 1.f / z;
-          const float dLdw = gC[0][0] * r3.x + gC[0][1] * r3.y + gC[0][2] * r3.z + gA + gZ * z +
-                             gI * rz + gN0 * r3.w + gN1 * r4.x + gN2 * r4.y + gD * dDdw;
-          float dLda[kMaxSets];
-          dLda[0] = T * dLdw - S[0] * rom;
-          S[0] += w * dLdw;
-#pragma unroll
-          for (int s = 1; s < kMaxSets; ++s) {
-            if (s < nsets) {
-              const float dw = gC[s][0] * r3.x + gC[s][1] * r3.y + gC[s][2] * r3.z;
-              dLda[s] = T * dw - S[s] * rom;
-              S[s] += w * dw;
-            } else {
-              dLda[s] = 0.f;
-            }
-          }
-          const float dzv = w * (gZ - gI * rz * rz) + gD * 2.f * w * (Ap - (Af - A)) +
-                            (k == medpos ? gMed : 0.f);
+          dLdw += gA + gZ * z + gN0 * e3.y + gN1 * e3.z + gN2 * e3.w + gD * dDdw;
+          dzv += w * gZ + gD * 2.f * w * (Ap - (Af - A)) + (k == medpos ? gMed : 0.f);
           A = Ap;
           Z = Zp;
-          // alpha -> rho (zero where alpha is clamped at alpha_max)
-          const bool unclamped = r2.w * q.G < set.alpha_max;
-          const float dadrho = unclamped ? -0.5f * r2.w * q.G : 0.f;
-          const float drho = dLda[0] * dadrho;
-          // d rho / d offset
-          float rx, ry;
-          float gdx, gdy, gpz;
-          if (q.obj) {
-            const float u = q.nu * q.rden, vv = q.nv * q.rden;
-            const float r2d = q.rden * q.rden;
-            rx = 2.f * r2d * (q.nu * r1.x + q.nv * r1.z) - 2.f * q.rho * q.rden * r2.x;
-            ry = 2.f * r2d * (q.nu * r1.y + q.nv * r1.w) - 2.f * q.rho * q.rden * r2.y;
-            const float dLdu = 2.f * u * drho, dLdv = 2.f * vv * drho;
-            const float drden = dLdu * q.nu + dLdv * q.nv + dzv * r2.z;
-            const float dnu = dLdu * q.rden, dnv = dLdv * q.rden;
-            const float dden = -drden * r2d;
-            v[0] = dnu * q.dx;
-            v[1] = dnu * q.dy;
-            v[2] = dnv * q.dx;
-            v[3] = dnv * q.dy;
-            v[4] = dden * q.dx;
-            v[5] = dden * q.dy;
-            gdx = dnu * r1.x + dnv * r1.z + dden * r2.x;
-            gdy = dnu * r1.y + dnv * r1.w + dden * r2.y;
-            gpz = dzv * q.rden;
+        }
+        float dLda[kMaxSets];
+        dLda[0] = T * dLdw - S[0] * rom;
+        S[0] += w * dLdw;
+#pragma unroll
+        for (int s = 1; s < kMaxSets; ++s) {
+          if (s < nsets) {
+            const float dw = gC[s][0] * e2.z + gC[s][1] * e2.w + gC[s][2] * e3.x;
+            dLda[s] = T * dw - S[s] * rom;
+            S[s] += w * dw;
           } else {
-            rx = 2.f * set.sinv * q.dx;
-            ry = 2.f * set.sinv * q.dy;
-            gdx = drho * rx;
-            gdy = drho * ry;
-            gpz = dzv;
+            dLda[s] = 0.f;
           }
-          v[6] = -gdx;
-          v[7] = -gdy;
-          v[8] = gpz;
-          v[9] = unclamped ? dLda[0] * q.G : 0.f;
-          v[10] = w * gC[0][0];
-          v[11] = w * gC[0][1];
-          v[12] = w * gC[0][2];
+        }
+        // alpha -> rho (zero where alpha is clamped at alpha_max)
+        const bool unclamped = e2.y * q.G < set.alpha_max;
+        const float dadrho = unclamped ? -0.5f * q.alpha : 0.f;
+        const float drho = dLda[0] * dadrho;
+        // d rho / d offset
+        float rx, ry, gdx, gdy, gpz;
+        if (q.obj) {
+          const float r2d = q.rden * q.rden;
+          const float tx = q.nu * e1.x + q.nv * e1.z, ty = q.nu * e1.y + q.nv * e1.w;
+          const float c2 = 2.f * q.rho * q.rden;
+          rx = 2.f * r2d * tx - c2 * e0.z;
+          ry = 2.f * r2d * ty - c2 * e0.w;
+          // rho = u^2 + v^2 with (u, v) = (nu, nv) rden, z = p_z rden
+          const float u = q.nu * q.rden, vv = q.nv * q.rden;
+          const float dnu = 2.f * u * q.rden * drho, dnv = 2.f * vv * q.rden * drho;
+          const float drden = 2.f * drho * (u * q.nu + vv * q.nv) + dzv * pz;
+          const float dden = -drden * r2d;
+          v[0] = dnu * q.dx;
+          v[1] = dnu * q.dy;
+          v[2] = dnv * q.dx;
+          v[3] = dnv * q.dy;
+          v[4] = dden * q.dx;
+          v[5] = dden * q.dy;
+          gdx = dnu * e1.x + dnv * e1.z + dden * e0.z;
+          gdy = dnu * e1.y + dnv * e1.w + dden * e0.w;
+          gpz = dzv * q.rden;
+        } else {
+          rx = 2.f * set.sinv * q.dx;
+          ry = 2.f * set.sinv * q.dy;
+          gdx = drho * rx;
+          gdy = drho * ry;
+          gpz = dzv;
+        }
+        v[6] = -gdx;
+        v[7] = -gdy;
+        v[8] = gpz;
+        v[9] = unclamped ? dLda[0] * q.G : 0.f;
+        v[10] = w * gC[0][0];
+        v[11] = w * gC[0][1];
+        v[12] = w * gC[0][2];
+        if constexpr (!kLoss) {
           v[13] = w * gN0;
           v[14] = w * gN1;
           v[15] = w * gN2;
+        }
 #pragma unroll
-          for (int s = 0; s < kMaxSets; ++s) {
-            const float dr = dLda[s] * dadrho;
-            v[kGradRec + 2 * s] = -dr * rx;
-            v[kGradRec + 2 * s + 1] = -dr * ry;
-          }
+        for (int s = 0; s < kMaxSets; ++s) {
+          const float dr = dLda[s] * dadrho;
+          v[LY::kRec + 2 * s] = -dr * rx;
+          v[LY::kRec + 2 * s + 1] = -dr * ry;
         }
       }
-      const unsigned ballot = __ballot_sync(0xffffffffu, contrib);
-      if (ballot == 0u) continue;
       if (__popc(ballot) == 1) {
         if (contrib) {
 #pragma unroll
-          for (int i = 0; i < kAcc; ++i)
+          for (int i = 0; i < kN; ++i)
             if (v[i] != 0.f) atomicAdd(&acc[kk][i], v[i]);
         }
       } else {
-        const float r = warp_reduce_scatter(v);
-        if (lane < kAcc && r != 0.f) atomicAdd(&acc[kk][lane], r);
+        rs_level<16, kN>(v, lane);
+        if (myslot >= 0 && v[0] != 0.f) atomicAdd(&acc[kk][myslot], v[0]);
       }
     }
     __syncthreads();
@@ -382,14 +486,14 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
       const uint32_t s = sid[threadIdx.x];
       float* g = grec + (size_t)s * kGradRec;
 #pragma unroll
-      for (int i = 0; i < kGradRec; ++i) {
+      for (int i = 0; i < LY::kRec; ++i) {
         const float x = acc[threadIdx.x][i];
         if (x != 0.f) atomicAdd(&g[i], x);
       }
       if (screen) {
         for (int st = 0; st < nsets; ++st) {
-          const float x0 = acc[threadIdx.x][kGradRec + 2 * st];
-          const float x1 = acc[threadIdx.x][kGradRec + 2 * st + 1];
+          const float x0 = acc[threadIdx.x][LY::kRec + 2 * st];
+          const float x1 = acc[threadIdx.x][LY::kRec + 2 * st + 1];
           float* sg = screen + ((size_t)st * n + s) * 2;
           if (x0 != 0.f) atomicAdd(&sg[0], x0);
           if (x1 != 0.f) atomicAdd(&sg[1], x1);
@@ -401,33 +505,47 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
     unsigned e = replayed;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if (lane == 0) atomicAdd(&counters[2], (unsigned long long)e);
+    if (lane == 0) {
+      atomicAdd(&counters[2], (unsigned long long)e);
+      atomicAdd(&counters[3], (unsigned long long)wentries);
+      atomicAdd(&counters[4], (unsigned long long)wlanes);
+    }
   }
 }
 
 }  // namespace
 
 cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const float4* rec,
-                             const uint32_t* vals, const int2* ranges, float* out,
+                             const RowGeom* geom, const uint32_t* vals, const int2* ranges, float* out,
                              int32_t* n_contrib, int32_t* last, int32_t* med,
                              unsigned long long* counters, cudaStream_t st) {
   const dim3 grid(cam.tiles_x, cam.tiles_y);
+  const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
   ProfScope ps(kProfBlendFwd, st);
-  blend_fwd_kernel<<<grid, kBlock, 0, st>>>(cam, set, rec, vals, ranges, out, n_contrib, last, med,
-                                            counters);
+  blend_fwd_kernel<<<grid, kBlock, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, n_contrib, last,
+                                            med, counters);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const float4* rec,
-                             const uint32_t* vals, const int2* ranges, const float* out,
+                             const RowGeom* geom, const uint32_t* vals, const int2* ranges, const float* out,
                              const int32_t* last, const int32_t* med, const AdjDev& adj,
                              float* grec, float* screen, int n, unsigned long long* counters,
                              cudaStream_t st) {
   const dim3 grid(cam.tiles_x, cam.tiles_y);
+  const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
+  // the training loss drives set 0 through colour and inverse depth only and
+  // the other sets through colour: a leaner kernel for that layout
+  bool loss_layout = (adj.mask[0] & ~(GS_MASK_RGB | (1u << GS_PLANE_INVDEPTH))) == 0u;
+  for (int s = 1; s < adj.n_sets; ++s) loss_layout = loss_layout && (adj.mask[s] & ~GS_MASK_RGB) == 0u;
   ProfScope ps(kProfBlendBwd, st);
-  blend_bwd_kernel<<<grid, kBlock, 0, st>>>(cam, set, rec, vals, ranges, out, last, med, adj, grec,
-                                            screen, n, counters);
+  if (loss_layout)
+    blend_bwd_kernel<true><<<grid, kBlock, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, last, med,
+                                                    adj, grec, screen, n, counters);
+  else
+    blend_bwd_kernel<false><<<grid, kBlock, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, last, med,
+                                                     adj, grec, screen, n, counters);
   count_launch();
   return cudaGetLastError();
 }

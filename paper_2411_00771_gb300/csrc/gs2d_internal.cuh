@@ -50,18 +50,20 @@ struct RowGeom {
   int ilo, ihi, jlo, jhi;
 };
 
-// Tile columns [tx0, tx1) that the footprint reaches in tile row ty.  Over
-// the band of pixel-centre rows of the tile row, the ellipse's right
-// boundary x(y) is concave, so its maximum is at the rightmost point's y
-// clamped to the band (likewise the left boundary); the disk is widest at
-// its centre's y clamped to the band.  Pixel centres inside the hull of the
-// two intervals, widened by a margin that covers the FP32 rounding of these
-// few operations, are covered: the result is a superset of the exact cover.
-// Written with explicit round-to-nearest operations because the preprocess
-// (counting) and the emission (writing) call it on the same stored values
-// and must agree bit for bit.
-__device__ __forceinline__ bool row_tiles(const RowGeom& g, int ty, float rf, int* tx0, int* tx1) {
-  const int ja = max(ty * kTile, g.jlo), jb = min(ty * kTile + kTile - 1, g.jhi);
+// Pixel columns [*ilo, *ihi] that the footprint reaches in the band of
+// pixel rows ja..jb.  Over the band, the ellipse's right boundary x(y) is
+// concave, so its maximum is at the rightmost point's y clamped to the band
+// (likewise the left boundary); the disk is widest at its centre's y
+// clamped to the band.  Pixel centres inside the hull of the two intervals,
+// widened by a margin that covers the FP32 rounding of these few
+// operations, are reported: the result is a superset of the exact cover,
+// clipped to the footprint's pixel box.  Written with explicit
+// round-to-nearest operations because several kernels evaluate it on the
+// same stored values and must agree bit for bit.
+__device__ __forceinline__ bool band_pixels(const RowGeom& g, int ja, int jb, float rf, int* pilo,
+                                            int* pihi) {
+  ja = max(ja, g.jlo);
+  jb = min(jb, g.jhi);
   if (ja > jb) return false;
   const float ya = __fsub_rn(__fsub_rn((float)ja + 0.5f, g.cy_hi), g.cy_lo);
   const float yb = __fsub_rn(__fsub_rn((float)jb + 0.5f, g.cy_hi), g.cy_lo);
@@ -96,6 +98,16 @@ __device__ __forceinline__ bool row_tiles(const RowGeom& g, int ty, float rf, in
   const int ilo = max((int)ceilf(__fsub_rn(fmaxf(xlo, -1.f), 0.5f)), g.ilo);
   const int ihi = min((int)floorf(__fsub_rn(fminf(xhi, 1.0e9f), 0.5f)), g.ihi);
   if (ilo > ihi) return false;
+  *pilo = ilo;
+  *pihi = ihi;
+  return true;
+}
+
+// Tile columns [tx0, tx1) that the footprint reaches in tile row ty (the
+// preprocess counts with it, the emission writes with it).
+__device__ __forceinline__ bool row_tiles(const RowGeom& g, int ty, float rf, int* tx0, int* tx1) {
+  int ilo, ihi;
+  if (!band_pixels(g, ty * kTile, ty * kTile + kTile - 1, rf, &ilo, &ihi)) return false;
   *tx0 = ilo / kTile;
   *tx1 = ihi / kTile + 1;
   return true;
@@ -142,7 +154,7 @@ cudaError_t launch_ranges(const uint32_t* keys, int64_t K, int2* ranges, int nti
                           cudaStream_t st);
 
 cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const float4* rec,
-                             const uint32_t* vals, const int2* ranges, float* out,
+                             const RowGeom* geom, const uint32_t* vals, const int2* ranges, float* out,
                              int32_t* n_contrib, int32_t* last, int32_t* med,
                              unsigned long long* counters, cudaStream_t st);
 
@@ -156,7 +168,7 @@ struct AdjDev {
 constexpr int kGradRec = 16;  // Ji(4) e(2) c(2) p_z(1) opacity(1) rgb(3) n(3)
 
 cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const float4* rec,
-                             const uint32_t* vals, const int2* ranges, const float* out,
+                             const RowGeom* geom, const uint32_t* vals, const int2* ranges, const float* out,
                              const int32_t* last, const int32_t* med, const AdjDev& adj,
                              float* grec, float* screen, int n, unsigned long long* counters,
                              cudaStream_t st);
