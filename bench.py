@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--width", type=int, default=1600, help="view width (smaller views for ncu captures)")
     ap.add_argument("--height", type=int, default=900)
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-seconds", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -251,6 +253,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene_np, cam, tgt_np, tinv_np, budget_s=20.0)
+    serving = None
+    if not args.no_serving:
+        del grads, screen, stats, adj_t, adj_s, adj_l
+        torch.cuda.empty_cache()
+        serving = run_serving(args, dev, sc, P, rank)
 
     if rank == 0:
         line = {
@@ -274,10 +281,124 @@ def run_ours(args):
                      "bwd_lanes_per_step": round(info["bwd_warp_lanes"] / max(1, info["bwd_warp_entries"]), 2)},
             "clocks": clk,
             "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+SERVE_RES = [(256, 256), (800, 600), (1600, 900), (1920, 1080), (3840, 2160)]
+
+
+def run_serving(args, dev, scene1m, params1m, rank):
+    """Served renders: 3 resident city scenes (1M, 4M, 10M surfels, SH 3),
+    requests from 64 client threads with Poisson arrivals, each a random pose
+    on a 150-250 m orbit and a resolution drawn from SERVE_RES.  Reports the
+    one-request-at-a-time throughput on the same request stream, then the
+    continuous-batching server at 0.5x, 0.9x and 1.2x that rate and
+    saturated, with p50/p99 latency from submission to completion."""
+    import numpy as np
+    import torch
+
+    from paper_2411_00771_gb300 import binding as B
+    from paper_2411_00771_gb300 import synthetic as syn
+
+    rng = np.random.default_rng(20241101 + 4)
+    scenes = [scene1m]
+    keep = [params1m]
+    for n, ext, nb in ((4_000_000, (500.0, 500.0), 200), (10_000_000, (1000.0, 1000.0), 800)):
+        s_np, _ = syn.city_scene(seed=20241101 + 40 + n // 1_000_000, n=n, extent=ext, n_boxes=nb)
+        Pn = {k: torch.from_numpy(np.ascontiguousarray(s_np[k], np.float32)).to(dev)
+              for k in ("mu", "quat", "scale", "opacity", "sh")}
+        keep.append(Pn)
+        scenes.append(B.Scene(Pn["mu"], Pn["quat"], Pn["scale"], Pn["opacity"], Pn["sh"], 3))
+        del s_np
+
+    def make_req():
+        sid = int(rng.integers(3))
+        W, H = SERVE_RES[int(rng.integers(len(SERVE_RES)))]
+        az = rng.uniform(0, 2 * math.pi)
+        r = rng.uniform(150.0, 250.0)
+        ext = 250.0 if sid < 2 else 500.0
+        tgt = (rng.uniform(-0.3, 0.3) * ext, rng.uniform(-0.3, 0.3) * ext, 0.0)
+        cam = syn.look_at((tgt[0] + r * math.cos(az), tgt[1] + r * math.sin(az), rng.uniform(150.0, 250.0)),
+                          tgt, W, H, 0.5 * W / math.tan(math.radians(30.0)))
+        return sid, cam
+
+    reqs = [make_req() for _ in range(400)]
+    outs = {}
+
+    def out_for(key, cam):
+        if key not in outs:
+            outs[key] = torch.empty((12, cam["height"], cam["width"]), device=dev)
+        return outs[key]
+
+    # one request at a time: render, wait, next
+    for sid, cam in reqs[:5]:
+        scenes[sid].render(cam, out=out_for(("seq", cam["width"]), cam), save=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_lat = []
+    nseq = 0
+    for sid, cam in reqs:
+        a = time.perf_counter()
+        scenes[sid].render(cam, out=out_for(("seq", cam["width"]), cam), save=False)
+        torch.cuda.synchronize()
+        seq_lat.append((time.perf_counter() - a) * 1e3)
+        nseq += 1
+        if time.perf_counter() - t0 > args.serving_seconds:
+            break
+    seq_vps = nseq / (time.perf_counter() - t0)
+
+    free, _ = torch.cuda.mem_get_info(dev)
+    srv = B.Server(budget_bytes=int(0.7 * free), max_slots=8)
+    ids = [srv.add_scene(s) for s in scenes]
+
+    def run(rate, duration, clients=64):
+        stop_at = time.perf_counter() + duration
+        srv.stats(reset=True)
+        done = [0]
+        lock = threading.Lock()
+
+        def client(c):
+            crng = np.random.default_rng(1000 + c)
+            i = c
+            while time.perf_counter() < stop_at:
+                if rate:
+                    time.sleep(crng.exponential(clients / rate))
+                sid, cam = reqs[i % len(reqs)]
+                i += clients
+                t = srv.submit(ids[sid], cam, out_for(("c", c, cam["width"]), cam))
+                srv.wait(t, 600000)
+                with lock:
+                    done[0] += 1
+
+        th = [threading.Thread(target=client, args=(c,)) for c in range(clients)]
+        a = time.perf_counter()
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        el = time.perf_counter() - a
+        st = srv.stats()
+        return {"offered_views_per_s": round(rate, 2) if rate else None,
+                "views_per_s": round(done[0] / el, 2), "completed": done[0],
+                "p50_ms": round(st["latency_p50_ms"], 3), "p99_ms": round(st["latency_p99_ms"], 3),
+                "views_per_blend_launch": round(st["batched_views"] / max(1, st["batches"]), 2)}
+
+    runs = {"saturated": run(None, args.serving_seconds)}
+    for f in (0.5, 0.9, 1.2):
+        runs[f"{f}x"] = run(f * seq_vps, args.serving_seconds / 2)
+    srv.close()
+    seq_sorted = sorted(seq_lat)
+    return {"scenes_surfels": [1_000_000, 4_000_000, 10_000_000], "resolutions": SERVE_RES,
+            "clients": 64, "one_at_a_time": {"views_per_s": round(seq_vps, 2),
+                                             "p50_ms": round(seq_sorted[len(seq_sorted) // 2], 3),
+                                             "p99_ms": round(seq_sorted[int(0.99 * (len(seq_sorted) - 1))], 3)},
+            "served": runs, "p50_ms": runs["0.9x"]["p50_ms"], "p99_ms": runs["0.9x"]["p99_ms"],
+            "speedup_saturated": round(runs["saturated"]["views_per_s"] / seq_vps, 3)}
 
 
 # ---------------------------------------------------------------------------

@@ -258,6 +258,51 @@ gs_status gs_densify_select(int64_t n, const float* stats, const float* scale, f
 gs_status gs_elongation_filter(int64_t n, const float* scale, float eta_thr, uint8_t* keep,
                                void* stream);
 
+/* ---- Serving: continuous batching of forward renders ------------------
+ * (the serving loop built on the rasterizer; the paper has no serving
+ * component of its own.)
+ * A server owns a worker thread, `max_slots` CUDA streams on the device
+ * current at creation, and device buffers (per-surfel records, sort buffers,
+ * tile lists) that stay resident between requests and grow on demand; their
+ * total never exceeds `budget_bytes`.  Requests are queued in submission
+ * order and admitted into free slots when their buffers fit the budget;
+ * stages of different requests overlap on the device and the views whose
+ * tile lists are ready are blended together by one persistent launch.  A
+ * request that cannot fit even alone fails with GS_ERR_CAPACITY.  Results
+ * equal gs_render's for the same scene and camera.
+ *  alloc:  device allocator for the server's buffers (NULL: cudaMallocAsync).
+ * Scenes are registered with gs_server_add_scene before requests name them
+ * and must outlive the server; their parameters must not change while
+ * requests are in flight. */
+typedef struct gs_server gs_server;
+typedef struct {
+  int32_t scene;       /* id from gs_server_add_scene                        */
+  gs_camera camera;    /* copied at submission                               */
+  float* out;          /* device [GS_OUT_PLANES][H][W], caller-owned; written */
+                       /* when gs_server_wait returns GS_OK                    */
+  int32_t* n_contrib;  /* device [H][W] or NULL                              */
+} gs_request;
+typedef struct {
+  int64_t completed, failed, queued, in_flight;
+  int64_t batches, batched_views;   /* blend launches and views they carried */
+  int64_t bytes_in_use;             /* resident device buffers               */
+  double latency_p50_ms, latency_p99_ms, latency_mean_ms; /* submit to done  */
+} gs_server_stats_t;
+gs_status gs_server_create(gs_server** out, size_t budget_bytes, int32_t max_slots,
+                           const gs_allocator* alloc);
+gs_status gs_server_add_scene(gs_server* server, gs_scene* scene, int32_t* scene_id);
+/* Thread-safe.  Returns a ticket for gs_server_wait. */
+gs_status gs_server_submit(gs_server* server, const gs_request* request, int64_t* ticket);
+/* Blocks until the request is done (GS_OK), failed (its error), or
+ * timeout_ms passed (GS_ERR_TIMEOUT; the ticket stays valid).  A finished
+ * ticket is consumed. */
+gs_status gs_server_wait(gs_server* server, int64_t ticket, int32_t timeout_ms);
+/* Counters and latency percentiles of requests completed since the last
+ * reset (reset != 0 clears them after reading). */
+gs_status gs_server_stats(gs_server* server, gs_server_stats_t* out, int32_t reset);
+/* Stops the worker after the work in flight; queued requests are dropped. */
+gs_status gs_server_destroy(gs_server* server);
+
 /* Diagnostics.
  * gs_kernel_launches: number of CUDA kernels this library has launched in
  *   this process (all entry points, all devices).

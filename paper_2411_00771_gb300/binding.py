@@ -73,6 +73,19 @@ class gs_frame_info(ctypes.Structure):
                 ("tiles_y", ctypes.c_int32)]
 
 
+class gs_request(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_int32), ("camera", gs_camera), ("out", ctypes.c_void_p),
+                ("n_contrib", ctypes.c_void_p)]
+
+
+class gs_server_stats_t(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("batched_views", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_mean_ms", ctypes.c_double)]
+
+
 class gs_loss_weights(ctypes.Structure):
     _fields_ = [("w_l1", ctypes.c_float), ("w_ssim", ctypes.c_float), ("w_depth", ctypes.c_float)]
 
@@ -104,6 +117,12 @@ _SIGS = {
     "gs_elongation_filter": [ctypes.c_int64, _V, ctypes.c_float, _V, _V],
     "gs_sync": [_V, ctypes.c_int32],
     "gs_profile_enable": [ctypes.c_int32],
+    "gs_server_create": [ctypes.POINTER(_V), ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(gs_allocator)],
+    "gs_server_add_scene": [_V, _V, ctypes.POINTER(ctypes.c_int32)],
+    "gs_server_submit": [_V, ctypes.POINTER(gs_request), ctypes.POINTER(ctypes.c_int64)],
+    "gs_server_wait": [_V, ctypes.c_int64, ctypes.c_int32],
+    "gs_server_stats": [_V, ctypes.POINTER(gs_server_stats_t), ctypes.c_int32],
+    "gs_server_destroy": [_V],
     "gs_profile_read": [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)],
 }
 for _name, _args in _SIGS.items():
@@ -274,6 +293,60 @@ class Scene:
         if self._handle:
             _lib.gs_destroy_scene(self._handle)
             self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching render server (gs_server_*).  Scenes must stay
+    alive while the server runs; output tensors belong to the caller until
+    wait() returns."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 8, allocator: gs_allocator = None):
+        self._h = ctypes.c_void_p()
+        self._alloc = allocator  # keeps callbacks alive
+        _check(_lib.gs_server_create(ctypes.byref(self._h), int(budget_bytes), int(max_slots),
+                                     ctypes.byref(allocator) if allocator is not None else None))
+        self.scenes = []
+        self._pending = {}
+
+    def add_scene(self, scene: "Scene") -> int:
+        sid = ctypes.c_int32()
+        _check(_lib.gs_server_add_scene(self._h, scene._handle, ctypes.byref(sid)))
+        self.scenes.append(scene)
+        return sid.value
+
+    def submit(self, scene_id: int, cam: dict, out, n_contrib=None) -> int:
+        H, W = int(cam["height"]), int(cam["width"])
+        r = gs_request()
+        r.scene = int(scene_id)
+        r.camera = make_camera(cam)
+        r.out = _ptr(out, shape=(OUT_PLANES, H, W), name="out")
+        r.n_contrib = _ptr(n_contrib, torch.int32, (H, W), "n_contrib")
+        t = ctypes.c_int64()
+        _check(_lib.gs_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._pending[t.value] = (out, n_contrib)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        code = _lib.gs_server_wait(self._h, int(ticket), int(timeout_ms))
+        if code != -5:
+            self._pending.pop(ticket, None)
+        _check(code)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = gs_server_stats_t()
+        _check(_lib.gs_server_stats(self._h, ctypes.byref(st), 1 if reset else 0))
+        return {k: getattr(st, k) for k, _ in gs_server_stats_t._fields_}
+
+    def close(self):
+        if self._h:
+            _lib.gs_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:

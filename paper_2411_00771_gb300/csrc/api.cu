@@ -204,6 +204,11 @@ struct gs_frame {
   const float* out = nullptr;
 };
 
+namespace gs2d {
+const ParamsDev& scene_params(const gs_scene* sc) { return sc->P; }
+const gs_settings& scene_settings(const gs_scene* sc) { return sc->settings; }
+}  // namespace gs2d
+
 extern "C" {
 
 uint64_t gs_kernel_launches(void) { return gs2d::g_launches.load(); }

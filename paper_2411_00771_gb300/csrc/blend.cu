@@ -112,15 +112,26 @@ __device__ __forceinline__ Pair eval_pair(float lx, float ly, float4 s0, float4 
   return q;
 }
 
-__global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
-    CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
-    const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, float* __restrict__ out,
-    int32_t* __restrict__ n_contrib, int32_t* __restrict__ last, int32_t* __restrict__ med,
-    unsigned long long* __restrict__ counters) {
-  __shared__ float4 s0[kBlock], s1[kBlock], s2[kBlock], s3[kBlock];
-  __shared__ uint32_t sm[kBlock];
-  const int tile = blockIdx.y * cam.tiles_x + blockIdx.x;
-  const int tx0 = blockIdx.x * kTile, ty0 = blockIdx.y * kTile;
+// Shared-memory staging area of one CTA.
+struct FwdSmem {
+  float4 s0[kBlock], s1[kBlock], s2[kBlock], s3[kBlock];
+  uint32_t sm[kBlock];
+  unsigned long long tot[2];
+};
+
+// Forward blend of tile (bx, by) of one view by the whole CTA.
+__device__ __forceinline__ void blend_fwd_tile(
+    FwdSmem& sh, const CamDev& cam, const SetDev& set, float rf, const float4* __restrict__ rec,
+    const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
+    float* __restrict__ out, int32_t* __restrict__ n_contrib, int32_t* __restrict__ last,
+    int32_t* __restrict__ med, unsigned long long* __restrict__ counters, int bx, int by) {
+  float4* s0 = sh.s0;
+  float4* s1 = sh.s1;
+  float4* s2 = sh.s2;
+  float4* s3 = sh.s3;
+  uint32_t* sm = sh.sm;
+  const int tile = by * cam.tiles_x + bx;
+  const int tx0 = bx * kTile, ty0 = by * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
   const int px = tx0 + lxi, py = ty0 + lyi;
   const int warp = threadIdx.x >> 5;
@@ -206,7 +217,7 @@ __global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
   }
   if (counters) {
     // per-tile totals of evaluated and blended pairs (performance counters)
-    __shared__ unsigned long long tot[2];
+    unsigned long long* tot = sh.tot;
     if (threadIdx.x == 0) tot[0] = tot[1] = 0ull;
     __syncthreads();
     unsigned e = evaluated, c = (unsigned)cnt;
@@ -224,6 +235,38 @@ __global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
       atomicAdd(&counters[0], tot[0]);
       atomicAdd(&counters[1], tot[1]);
     }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
+    CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
+    const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, float* __restrict__ out,
+    int32_t* __restrict__ n_contrib, int32_t* __restrict__ last, int32_t* __restrict__ med,
+    unsigned long long* __restrict__ counters) {
+  __shared__ FwdSmem sh;
+  blend_fwd_tile(sh, cam, set, rf, rec, geom, vals, ranges, out, n_contrib, last, med, counters,
+                 blockIdx.x, blockIdx.y);
+}
+
+// Persistent forward blend over the tiles of several views (serving): each
+// CTA takes (view, tile) work items from a device counter until all tiles
+// of all views in the batch are done; views of different sizes and scenes
+// share one launch.
+__global__ void __launch_bounds__(kBlock) blend_fwd_batched_kernel(BlendBatch batch) {
+  __shared__ FwdSmem sh;
+  __shared__ int item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item = (int)atomicAdd(batch.counter, 1u);
+    __syncthreads();
+    const int t = item;
+    if (t >= batch.total_tiles) break;
+    int j = 0;
+    while (j + 1 < batch.njobs && batch.job[j + 1].tile_begin <= t) ++j;
+    const BlendJob& jb = batch.job[j];
+    const int local = t - jb.tile_begin;
+    blend_fwd_tile(sh, jb.cam, jb.set, jb.rf, jb.rec, jb.geom, jb.vals, jb.ranges, jb.out, jb.n_contrib,
+                   nullptr, nullptr, nullptr, local % jb.cam.tiles_x, local / jb.cam.tiles_x);
   }
 }
 
@@ -524,6 +567,13 @@ cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const float4*
   ProfScope ps(kProfBlendFwd, st);
   blend_fwd_kernel<<<grid, kBlock, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, n_contrib, last,
                                             med, counters);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend_fwd_batched(const BlendBatch& batch, int grid, cudaStream_t st) {
+  ProfScope ps(kProfBlendFwd, st);
+  blend_fwd_batched_kernel<<<grid, kBlock, 0, st>>>(batch);
   count_launch();
   return cudaGetLastError();
 }

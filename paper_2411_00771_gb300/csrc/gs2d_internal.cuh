@@ -158,6 +158,28 @@ cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const float4*
                              int32_t* n_contrib, int32_t* last, int32_t* med,
                              unsigned long long* counters, cudaStream_t st);
 
+// One view of a batched (serving) forward blend.
+struct BlendJob {
+  CamDev cam;
+  SetDev set;
+  float rf;
+  int tile_begin;  // first work item of this view in the batch
+  const float4* rec;
+  const RowGeom* geom;
+  const uint32_t* vals;
+  const int2* ranges;
+  float* out;
+  int32_t* n_contrib;
+};
+constexpr int kMaxBatch = 16;
+struct BlendBatch {
+  BlendJob job[kMaxBatch];
+  int njobs;
+  int total_tiles;
+  unsigned* counter;  // zeroed before the launch
+};
+cudaError_t launch_blend_fwd_batched(const BlendBatch& batch, int grid, cudaStream_t st);
+
 struct AdjDev {
   const float* set[3];
   uint32_t mask[3];

@@ -187,8 +187,9 @@ __global__ void __launch_bounds__(kT* kT) ssim_bwd_kernel(
 __global__ void loss_reduce_kernel(const float* __restrict__ bsum, int nb, const float* __restrict__ dsum,
                                    int nd, int W, int H, gs_loss_weights wt, int has_depth,
                                    float* __restrict__ losses) {
-  __shared__ double red[3][256];
-  double a = 0.0, b = 0.0, d = 0.0;
+  __shared__ double red[3][1024];
+  // per-thread partial sums in FP32 (a few dozen terms each), the tree in FP64
+  float a = 0.f, b = 0.f, d = 0.f;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     a += bsum[2 * i];
     b += bsum[2 * i + 1];
@@ -245,7 +246,7 @@ cudaError_t launch_loss(int W, int H, const float* out, const float* tgt, const 
   ssim_fwd_kernel<<<grid, blk, 0, st>>>(W, H, out, tgt, g, part, bsum);
   ssim_bwd_kernel<<<grid, blk, 0, st>>>(W, H, out, tgt, tinv, g, w, part, adj_total, adj_ssim,
                                         adj_l1, dsum);
-  loss_reduce_kernel<<<1, 256, 0, st>>>(bsum, 3 * gx * gy, dsum, gx * gy, W, H, w, tinv != nullptr,
+  loss_reduce_kernel<<<1, 1024, 0, st>>>(bsum, 3 * gx * gy, dsum, gx * gy, W, H, w, tinv != nullptr,
                                         losses);
   return cudaGetLastError();
 }

@@ -153,19 +153,27 @@ __global__ void __launch_bounds__(256) preprocess_cull_kernel(ParamsDev P, CamDe
       keep = !(sx1 < -m || sx0 > (float)cam.W + m || sy1 < -m || sy0 > (float)cam.H + m);
     }
   }
+  // block-aggregated append: one global atomic per block
+  __shared__ uint32_t wcount[8], wbase[8], bbase;
   const unsigned ball = __ballot_sync(0xffffffffu, keep);
-  if (ball) {
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(ball) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(ncand, (uint32_t)__popc(ball));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (keep) cand[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)n;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wcount[w] = (uint32_t)__popc(ball);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int i = 0; i < 8; ++i) {
+      wbase[i] = t;
+      t += wcount[i];
+    }
+    bbase = t ? atomicAdd(ncand, t) : 0u;
   }
+  __syncthreads();
+  if (keep) cand[bbase + wbase[w] + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)n;
 }
 
 // Stage 2 (FP64 geometry, candidates only): the definition's preprocess,
 // the footprint's exact tile-row coverage and the blend record.
+template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDev cam, SetDev set,
                                                               const uint32_t* __restrict__ cand,
                                                               const uint32_t* __restrict__ ncand,
@@ -267,16 +275,19 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     // colour: SH at the world direction from the camera centre
     const double dx = mu.x - cam.campos[0], dy = mu.y - cam.campos[1], dz = mu.z - cam.campos[2];
     const double il = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+    constexpr int K = (DEG + 1) * (DEG + 1);
     float Y[16];
-    sh_basis((float)(dx * il), (float)(dy * il), (float)(dz * il), P.sh_degree, Y);
-    const int K = (P.sh_degree + 1) * (P.sh_degree + 1);
+    sh_basis((float)(dx * il), (float)(dy * il), (float)(dz * il), DEG, Y);
     const float* f = P.sh + (size_t)n * K * 3;
-    float col[3];
-    for (int c = 0; c < 3; ++c) {
-      float acc = 0.f;
-      for (int k = 0; k < K; ++k) acc = fmaf(f[k * 3 + c], Y[k], acc);
-      col[c] = fmaxf(acc + 0.5f, 0.f);
+    float col[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      col[0] = fmaf(f[k * 3], Y[k], col[0]);
+      col[1] = fmaf(f[k * 3 + 1], Y[k], col[1]);
+      col[2] = fmaf(f[k * 3 + 2], Y[k], col[2]);
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c] + 0.5f, 0.f);
     const double sg = (nv.x * p.x + nv.y * p.y + nv.z * p.z) > 0.0 ? -1.0 : 1.0;
     const float chx = (float)cx, chy = (float)cy;
     float4* Rr = rec + (size_t)n * kRecF4;
@@ -291,6 +302,7 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
 // ---------------------------------------------------------------------------
 // Backward.
 
+template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev cam,
                                                              const uint32_t* __restrict__ tcount,
                                                              const float* __restrict__ grec,
@@ -357,24 +369,38 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev
   const float dl = sqrtf(dd.x * dd.x + dd.y * dd.y + dd.z * dd.z);
   const float il = 1.f / dl;
   const float dx = dd.x * il, dy = dd.y * il, dz = dd.z * il;
-  const int deg = P.sh_degree;
-  const int K = (deg + 1) * (deg + 1);
+  constexpr int K = (DEG + 1) * (DEG + 1);
   float Y[16];
   float3 dY[16];
-  sh_basis(dx, dy, dz, deg, Y);
-  sh_basis_grad(dx, dy, dz, deg, dY);
+  sh_basis(dx, dy, dz, DEG, Y);
+  sh_basis_grad(dx, dy, dz, DEG, dY);
   const float* f = P.sh + (size_t)n * K * 3;
+  float fv[K * 3];
+#pragma unroll
+  for (int i = 0; i < K * 3; ++i) fv[i] = f[i];
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = fmaf(fv[k * 3 + c], Y[k], acc[c]);
+  float gc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) gc[c] = (acc[c] + 0.5f > 0.f) ? grgb[c] : 0.f;  // clamped: no gradient
   V3<float> gdir = {0.f, 0.f, 0.f};
-  for (int c = 0; c < 3; ++c) {
-    float acc = 0.f;
-    for (int k = 0; k < K; ++k) acc = fmaf(f[k * 3 + c], Y[k], acc);
-    if (!(acc + 0.5f > 0.f) || grgb[c] == 0.f) continue;  // clamped colour: no gradient
-    const float gc = grgb[c];
-    for (int k = 0; k < K; ++k) {
-      if (G.sh) G.sh[((size_t)n * K + k) * 3 + c] += gc * Y[k];
-      const float fk = f[k * 3 + c] * gc;
-      gdir.x += fk * dY[k].x; gdir.y += fk * dY[k].y; gdir.z += fk * dY[k].z;
-    }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float fk = fv[k * 3] * gc[0] + fv[k * 3 + 1] * gc[1] + fv[k * 3 + 2] * gc[2];
+    gdir.x += fk * dY[k].x;
+    gdir.y += fk * dY[k].y;
+    gdir.z += fk * dY[k].z;
+  }
+  if (G.sh) {
+    float* gs = G.sh + (size_t)n * K * 3;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (gc[c] != 0.f) gs[k * 3 + c] += gc[c] * Y[k];
   }
   const float gdd = dx * gdir.x + dy * gdir.y + dz * gdir.z;
   gmu.x += (gdir.x - dx * gdd) * il;
@@ -424,7 +450,12 @@ cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDe
   // candidates are a subset of the surfels; a grid-stride loop over the
   // device-side count, two CTAs per SM
   const unsigned blocks = div_up(P.n, 256) < 304u ? div_up(P.n, 256) : 304u;
-  preprocess_main_kernel<<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom);
+  switch (P.sh_degree) {
+    case 0: preprocess_main_kernel<0><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom); break;
+    case 1: preprocess_main_kernel<1><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom); break;
+    case 2: preprocess_main_kernel<2><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom); break;
+    default: preprocess_main_kernel<3><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom); break;
+  }
   count_launch(2);
   return cudaGetLastError();
 }
@@ -433,7 +464,13 @@ cudaError_t launch_preprocess_bwd(const ParamsDev& P, const CamDev& cam, const u
                                   const float* grec, const gs_param_grads& G, cudaStream_t st) {
   if (P.n == 0) return cudaSuccess;
   ProfScope ps(kProfPreprocessBwd, st);
-  preprocess_bwd_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, tcount, grec, G);
+  const unsigned blocks = div_up(P.n, 256);
+  switch (P.sh_degree) {
+    case 0: preprocess_bwd_kernel<0><<<blocks, 256, 0, st>>>(P, cam, tcount, grec, G); break;
+    case 1: preprocess_bwd_kernel<1><<<blocks, 256, 0, st>>>(P, cam, tcount, grec, G); break;
+    case 2: preprocess_bwd_kernel<2><<<blocks, 256, 0, st>>>(P, cam, tcount, grec, G); break;
+    default: preprocess_bwd_kernel<3><<<blocks, 256, 0, st>>>(P, cam, tcount, grec, G); break;
+  }
   count_launch();
   return cudaGetLastError();
 }

@@ -162,14 +162,28 @@ def city_scene(seed: int = SEED_BASE + 2, n: int = 1_000_000, sh_degree: int = 3
     albedo_ground = np.array([0.45, 0.47, 0.42])
     box_albedo = rng.uniform(0.2, 0.85, (nb, 3))
     mus, nrms, cols = [], [], []
-    # ground (rejection against footprints)
+    # ground (rejection against footprints): a 0.5 m grid of box ids finds
+    # the one box a point can fall in (boxes keep 2 m gaps), then the exact
+    # test against that box
+    cell = 0.5
+    gx, gy = int(math.ceil(ex / cell)) + 1, int(math.ceil(ey / cell)) + 1
+    grid = np.full((gx, gy), -1, np.int32)
+    for bi, b in enumerate(boxes):
+        i0, i1 = int((b[0] + ex / 2) // cell), int((b[1] + ex / 2) // cell)
+        j0, j1 = int((b[2] + ey / 2) // cell), int((b[3] + ey / 2) // cell)
+        grid[max(i0, 0):min(i1 + 1, gx), max(j0, 0):min(j1 + 1, gy)] = bi
     k = counts[0]
     pts = np.empty((0, 2))
     while pts.shape[0] < k:
         c = rng.uniform([-ex / 2, -ey / 2], [ex / 2, ey / 2], (int(1.3 * (k - pts.shape[0])) + 16, 2))
+        ci = np.clip(((c[:, 0] + ex / 2) // cell).astype(np.int64), 0, gx - 1)
+        cj = np.clip(((c[:, 1] + ey / 2) // cell).astype(np.int64), 0, gy - 1)
+        bid = grid[ci, cj]
         inside = np.zeros(c.shape[0], bool)
-        for b in boxes:
-            inside |= (c[:, 0] > b[0]) & (c[:, 0] < b[1]) & (c[:, 1] > b[2]) & (c[:, 1] < b[3])
+        m = bid >= 0
+        if m.any():
+            b = boxes[bid[m]]
+            inside[m] = (c[m, 0] > b[:, 0]) & (c[m, 0] < b[:, 1]) & (c[m, 1] > b[:, 2]) & (c[m, 1] < b[:, 3])
         pts = np.concatenate([pts, c[~inside]])
     pts = pts[:k]
     mus.append(np.column_stack([pts, np.zeros(k)]))
