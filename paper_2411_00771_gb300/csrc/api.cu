@@ -161,8 +161,13 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 
 void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
+// Scopes of one group may nest (a sort calls a scan); only the outermost
+// scope of each group records.
+thread_local int g_prof_depth[kProfCount] = {};
+
 void prof_begin(int id, cudaStream_t st) {
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  if (g_prof_depth[id]++ > 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEvent_t e = prof_event();
   if (e && cudaEventRecord(e, st) == cudaSuccess) g_prof_open[id] = e;
@@ -170,6 +175,7 @@ void prof_begin(int id, cudaStream_t st) {
 }
 
 void prof_end(int id, cudaStream_t st) {
+  if (g_prof_depth[id] > 0 && --g_prof_depth[id] > 0) return;
   if (!g_prof_on.load(std::memory_order_relaxed) || !g_prof_open[id]) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEvent_t e = prof_event();
@@ -369,12 +375,14 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
     if (e != cudaSuccess) return cleanup(cuda_fail(e, #expr)); \
   } while (0)
   GS_CKC(cudaMemsetAsync(f->counters, 0, 8 * sizeof(unsigned long long), st));
-  GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, cand, total + 1,
-                           geom, st));
+  // candidates (possibly visible surfels) in index order; only they are sorted
+  uint32_t* ncand = total + 1;
+  GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, cand, ncand, geom,
+                           cnts, rtmp + radix_tmp_words(n), st));
   uint32_t *skey = dkey, *sidx = idx;
-  GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st));
-  GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st));
-  GS_CKC(launch_scan(cnts, offs, n, total, rtmp + radix_tmp_words(n), st));
+  GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st, ncand));
+  GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st, ncand));
+  GS_CKC(launch_scan(cnts, offs, n, total, rtmp + radix_tmp_words(n), st, ncand));
   uint32_t Kh = 0;
   GS_CKC(cudaMemcpyAsync(&Kh, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   GS_CKC(cudaStreamSynchronize(st));
@@ -389,7 +397,7 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   if (!keys || !vals || !keys2 || !vals2 || !ktmp)
     return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed (tile lists)"));
   const float rf = (float)sqrt((double)sc->settings.rho_max / (double)sc->settings.screen_inv_sigma2);
-  GS_CKC(launch_emit(sidx, offs, cnts, f->rect, geom, rf, n, cam.tiles_x, keys, vals, st));
+  GS_CKC(launch_emit(sidx, offs, cnts, f->rect, geom, rf, n, cam.tiles_x, keys, vals, st, ncand));
   uint32_t *tk = keys, *tv = vals;
   GS_CKC(radix_sort_pairs(keys, vals, keys2, vals2, K, bits_for(ntiles), ktmp, &tk, &tv, st));
   f->vals = tv;

@@ -126,16 +126,21 @@ struct ParamsDev {
 };
 
 // ---- launch wrappers (each returns cudaError_t from the launch) ----------
+// Writes, for the ncand candidates (device count) in surfel-index order,
+// depth_key[i] (FP32 depth bits, or all ones when not visible) and idx[i]
+// (surfel index); per surfel: rec, rect, tcount, geom.  flags and scan_tmp
+// are scratch (n and scan_tmp_words(n) words).
 cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
                               float4* rec, uint2* rect, uint32_t* tcount, uint32_t* depth_key,
                               uint32_t* idx, uint32_t* cand, uint32_t* ncand, RowGeom* geom,
-                              cudaStream_t st);
+                              uint32_t* flags, uint32_t* scan_tmp, cudaStream_t st);
 
 // device-wide exclusive scan of n uint32 values; total (uint32) written to
 // *total_dev; tmp must hold scan_tmp_words(n) uint32 words.
 size_t scan_tmp_words(int64_t n);
+// n_dev (optional): device-side item count <= n (n sizes the grid).
 cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
-                        uint32_t* tmp, cudaStream_t st);
+                        uint32_t* tmp, cudaStream_t st, const uint32_t* n_dev = nullptr);
 
 // LSD radix sort of (key, value) pairs over key bits [0, bits); stable.
 // Result ends in (keys_out, vals_out) (double-buffering through the alt
@@ -143,13 +148,14 @@ cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
 size_t radix_tmp_words(int64_t n);
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, uint32_t* tmp,
-                             uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st);
+                             uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st,
+                             const uint32_t* n_dev = nullptr);
 
 cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* tcount, uint32_t* out,
-                                 int64_t n, cudaStream_t st);
+                                 int64_t n, cudaStream_t st, const uint32_t* n_dev = nullptr);
 cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint32_t* counts,
                         const uint2* rect, const RowGeom* geom, float rf, int64_t n, int tiles_x,
-                        uint32_t* keys, uint32_t* vals, cudaStream_t st);
+                        uint32_t* keys, uint32_t* vals, cudaStream_t st, const uint32_t* n_dev = nullptr);
 cudaError_t launch_ranges(const uint32_t* keys, int64_t K, int2* ranges, int ntiles,
                           cudaStream_t st);
 

@@ -116,18 +116,41 @@ __device__ __forceinline__ V3<T> rotT(const double* R, V3<T> v) {
 // so a sphere entirely behind the near plane, or whose camera-space box
 // projects (with the screen-filter radius, one pixel and a relative error
 // margin added) entirely outside the image, has an empty tile rectangle.
+// Double-precision reciprocal, reciprocal square root and square root by
+// Newton-Raphson refinement of the single-precision hardware estimates
+// (x_{k+1} = x_k (2 - a x_k) for 1/a, y_{k+1} = y_k (3 - a y_k^2) / 2 for
+// 1/sqrt(a)); each step squares the relative error, two steps take the
+// 2^-22 estimate to double precision.  Arguments outside the float range of
+// the estimate fall back to the division / square root.
+__device__ __forceinline__ double rcp_nr(double a) {
+  const float af = (float)a;
+  if (!(fabsf(af) > 1e-30f && fabsf(af) < 1e30f)) return 1.0 / a;
+  float e;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(af));
+  double x = (double)e;
+  x = x * fma(-a, x, 2.0);
+  x = x * fma(-a, x, 2.0);
+  return x;
+}
+__device__ __forceinline__ double rsqrt_nr(double a) {
+  const float af = (float)a;
+  if (!(af > 1e-30f && af < 1e30f)) return 1.0 / sqrt(a);
+  float e;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(af));
+  double y = (double)e;
+  y = y * fma(-0.5 * a * y, y, 1.5);
+  y = y * fma(-0.5 * a * y, y, 1.5);
+  return y;
+}
+__device__ __forceinline__ double sqrt_nr(double a) { return a > 0.0 ? a * rsqrt_nr(a) : 0.0; }
+
 __global__ void __launch_bounds__(256) preprocess_cull_kernel(ParamsDev P, CamDev cam, SetDev set,
                                                               uint2* __restrict__ rect,
                                                               uint32_t* __restrict__ tcount,
-                                                              uint32_t* __restrict__ dkey,
-                                                              uint32_t* __restrict__ idx,
-                                                              uint32_t* __restrict__ cand,
-                                                              uint32_t* __restrict__ ncand) {
+                                                              uint32_t* __restrict__ flags) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   bool keep = false;
   if (n < P.n) {
-    idx[n] = (uint32_t)n;
-    dkey[n] = 0xFFFFFFFFu;
     tcount[n] = 0u;
     rect[n] = make_uint2(0u, 0u);
     const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
@@ -153,22 +176,16 @@ __global__ void __launch_bounds__(256) preprocess_cull_kernel(ParamsDev P, CamDe
       keep = !(sx1 < -m || sx0 > (float)cam.W + m || sy1 < -m || sy0 > (float)cam.H + m);
     }
   }
-  // block-aggregated append: one global atomic per block
-  __shared__ uint32_t wcount[8], wbase[8], bbase;
-  const unsigned ball = __ballot_sync(0xffffffffu, keep);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) wcount[w] = (uint32_t)__popc(ball);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int i = 0; i < 8; ++i) {
-      wbase[i] = t;
-      t += wcount[i];
-    }
-    bbase = t ? atomicAdd(ncand, t) : 0u;
-  }
-  __syncthreads();
-  if (keep) cand[bbase + wbase[w] + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)n;
+  if (n < P.n) flags[n] = keep ? 1u : 0u;
+}
+
+// Candidates in surfel-index order (the compositing order breaks depth ties
+// by index, and the stable depth sort keeps this order for equal keys).
+__global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict__ flags,
+                                                      const uint32_t* __restrict__ pos, int n,
+                                                      uint32_t* __restrict__ cand) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flags[i]) cand[pos[i]] = (uint32_t)i;
 }
 
 // Stage 2 (FP64 geometry, candidates only): the definition's preprocess,
@@ -181,15 +198,18 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
                                                               uint2* __restrict__ rect,
                                                               uint32_t* __restrict__ tcount,
                                                               uint32_t* __restrict__ dkey,
+                                                              uint32_t* __restrict__ idx,
                                                               RowGeom* __restrict__ geom) {
   const uint32_t total = *ncand;
   const double rf = sqrt((double)set.rho_max / (double)set.sinv);
   for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < total; ci += gridDim.x * blockDim.x) {
     const int n = (int)cand[ci];
+    idx[ci] = (uint32_t)n;
+    dkey[ci] = 0xFFFFFFFFu;  // not visible unless set below
     const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
     const double qn2 = (double)qw * qw + (double)qx * qx + (double)qy * qy + (double)qz * qz;
     if (!(qn2 > 0.0)) continue;
-    const double iq = 1.0 / sqrt(qn2);
+    const double iq = rsqrt_nr(qn2);
     V3<double> r1, r2, r3;
     quat_cols<double>(qw * iq, qx * iq, qy * iq, qz * iq, r1, r2, r3);
     const V3<double> mu = {(double)P.mu[3 * n], (double)P.mu[3 * n + 1], (double)P.mu[3 * n + 2]};
@@ -198,9 +218,9 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     const V3<double> tu = rot<double>(cam.R, r1), tv = rot<double>(cam.R, r2), nv = rot<double>(cam.R, r3);
     const double su = P.scale[2 * n], sv = P.scale[2 * n + 1];
     const V3<double> a = {su * tu.x, su * tu.y, su * tu.z}, b = {sv * tv.x, sv * tv.y, sv * tv.z};
-    const double zmin = p.z - sqrt((double)set.rho_max) * sqrt(a.z * a.z + b.z * b.z);
+    const double zmin = p.z - sqrt_nr((double)set.rho_max * (a.z * a.z + b.z * b.z));
     if (!(zmin > (double)set.near_plane)) continue;
-    const double iz = 1.0 / p.z;
+    const double iz = rcp_nr(p.z);
     const double xi = p.x * iz, yi = p.y * iz;
     const double cx = cam.fx * xi + cam.cx, cy = cam.fy * yi + cam.cy;
     const double J11 = cam.fx * (a.x - a.z * xi) * iz, J12 = cam.fx * (b.x - b.z * xi) * iz;
@@ -214,10 +234,11 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     const double C12 = rm * (J11 * J21 + J12 * J22);
     const double C13 = rm * (J11 * w1 + J12 * w2), C23 = rm * (J21 * w1 + J22 * w2);
     const double C33 = rm * (w1 * w1 + w2 * w2) - 1.0;
-    const double ex = sqrt(fmax(C13 * C13 - C11 * C33, 0.0));
-    const double ey = sqrt(fmax(C23 * C23 - C22 * C33, 0.0));
-    const double x0 = (C13 - ex) / C33, x1 = (C13 + ex) / C33;
-    const double y0 = (C23 - ey) / C33, y1 = (C23 + ey) / C33;
+    const double ex = sqrt_nr(fmax(C13 * C13 - C11 * C33, 0.0));
+    const double ey = sqrt_nr(fmax(C23 * C23 - C22 * C33, 0.0));
+    const double i33 = rcp_nr(C33);
+    const double x0 = (C13 - ex) * i33, x1 = (C13 + ex) * i33;
+    const double y0 = (C23 - ey) * i33, y1 = (C23 + ey) * i33;
     const double xmin = cx + fmin(fmin(x0, x1), -rf), xmax = cx + fmax(fmax(x0, x1), rf);
     const double ymin = cy + fmin(fmin(y0, y1), -rf), ymax = cy + fmax(fmax(y0, y1), rf);
     double ilo = ceil(xmin - 0.5), ihi = floor(xmax - 0.5);
@@ -227,18 +248,20 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     if (!(ilo <= ihi && jlo <= jhi)) continue;
     RowGeom gm;
     {
-      const double e0x = C13 / C33, e0y = C23 / C33;
-      const double g11 = e0x * e0x - C11 / C33, g12 = e0x * e0y - C12 / C33, g22 = e0y * e0y - C22 / C33;
+      const double e0x = C13 * i33, e0y = C23 * i33;
+      const double g11 = e0x * e0x - C11 * i33, g12 = e0x * e0y - C12 * i33, g22 = e0y * e0y - C22 * i33;
       const float chx = (float)cx, chy = (float)cy;
       gm.cx_hi = chx; gm.cx_lo = (float)(cx - (double)chx);
       gm.cy_hi = chy; gm.cy_lo = (float)(cy - (double)chy);
       gm.e0x = (float)e0x; gm.e0y = (float)e0y;
       if (g11 > 0.0 && g22 > 0.0) {
-        const double det = fmax(g11 * g22 - g12 * g12, 0.0);
-        gm.hy = (float)sqrt(g22);
-        gm.t = (float)(g12 / sqrt(g11));
-        gm.slope = (float)(g12 / g22);
-        gm.wsc = (float)(sqrt(det) / g22);
+        // rounded once to FP32; the row rule's margin covers their error
+        const float det = (float)fmax(g11 * g22 - g12 * g12, 0.0);
+        const float f11 = (float)g11, f12 = (float)g12, f22 = (float)g22;
+        gm.hy = sqrtf(f22);
+        gm.t = f12 * rsqrtf(f11);
+        gm.slope = f12 / f22;
+        gm.wsc = sqrtf(det) / f22;
       } else {
         gm.hy = -1.f; gm.t = 0.f; gm.slope = 0.f; gm.wsc = 0.f;  // disk only
       }
@@ -256,12 +279,12 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     geom[n] = gm;
     tcount[n] = cnt;
     const float pz = (float)p.z;
-    dkey[n] = __float_as_uint(pz);
+    dkey[ci] = __float_as_uint(pz);
     const double det = J11 * J22 - J12 * J21;
     float4 r1f;
     float2 ef;
     if (det != 0.0) {
-      const double id = 1.0 / det;
+      const double id = rcp_nr(det);
       const double i11 = J22 * id, i12 = -J12 * id, i21 = -J21 * id, i22 = J11 * id;
       r1f = make_float4((float)i11, (float)i12, (float)i21, (float)i22);
       ef = make_float2((float)(-(i11 * w1 + i21 * w2)), (float)(-(i12 * w1 + i22 * w2)));
@@ -273,11 +296,12 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
       ef = make_float2(0.f, 0.f);
     }
     // colour: SH at the world direction from the camera centre
-    const double dx = mu.x - cam.campos[0], dy = mu.y - cam.campos[1], dz = mu.z - cam.campos[2];
-    const double il = 1.0 / sqrt(dx * dx + dy * dy + dz * dz);
+    const float dx = (float)(mu.x - cam.campos[0]), dy = (float)(mu.y - cam.campos[1]),
+                dz = (float)(mu.z - cam.campos[2]);
+    const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
     constexpr int K = (DEG + 1) * (DEG + 1);
     float Y[16];
-    sh_basis((float)(dx * il), (float)(dy * il), (float)(dz * il), DEG, Y);
+    sh_basis(dx * il, dy * il, dz * il, DEG, Y);
     const float* f = P.sh + (size_t)n * K * 3;
     float col[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -441,20 +465,24 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev
 cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
                               float4* rec, uint2* rect, uint32_t* tcount, uint32_t* dkey,
                               uint32_t* idx, uint32_t* cand, uint32_t* ncand, RowGeom* geom,
-                              cudaStream_t st) {
-  if (P.n == 0) return cudaSuccess;
+                              uint32_t* flags, uint32_t* scan_tmp, cudaStream_t st) {
+  if (P.n == 0) return cudaMemsetAsync(ncand, 0, sizeof(uint32_t), st);
   ProfScope ps(kProfPreprocess, st);
-  cudaError_t e = cudaMemsetAsync(ncand, 0, sizeof(uint32_t), st);
+  preprocess_cull_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, set, rect, tcount, flags);
+  count_launch();
+  // positions of the candidates: exclusive scan of the flags (into cand's
+  // second half is not needed: dkey is free until the main pass writes it)
+  cudaError_t e = launch_scan(flags, dkey, P.n, ncand, scan_tmp, st);
   if (e != cudaSuccess) return e;
-  preprocess_cull_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, set, rect, tcount, dkey, idx, cand, ncand);
+  compact_kernel<<<div_up(P.n, 256), 256, 0, st>>>(flags, dkey, P.n, cand);
   // candidates are a subset of the surfels; a grid-stride loop over the
   // device-side count, two CTAs per SM
   const unsigned blocks = div_up(P.n, 256) < 304u ? div_up(P.n, 256) : 304u;
   switch (P.sh_degree) {
-    case 0: preprocess_main_kernel<0><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom); break;
-    case 1: preprocess_main_kernel<1><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom); break;
-    case 2: preprocess_main_kernel<2><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom); break;
-    default: preprocess_main_kernel<3><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, geom); break;
+    case 0: preprocess_main_kernel<0><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
+    case 1: preprocess_main_kernel<1><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
+    case 2: preprocess_main_kernel<2><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
+    default: preprocess_main_kernel<3><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
   }
   count_launch(2);
   return cudaGetLastError();

@@ -83,6 +83,7 @@ struct Slot {
   float rf = 0.f;
   int64_t K = 0;
   uint32_t* sidx = nullptr;  // sorted surfel order (one of idx / idx2)
+  uint32_t* ncand = nullptr; // device count of sorted candidates
   uint32_t* vals_final = nullptr;
   size_t bytes() const {
     return rec.bytes + geom.bytes + rect.bytes + tcount.bytes + dkey.bytes + idx.bytes + dkey2.bytes +
@@ -220,16 +221,21 @@ gs_status stage_a(gs_server* s, Slot& sl, std::string* msg) {
   }
   uint32_t* rtmp = (uint32_t*)sl.rtmp.p;
   uint32_t* total = rtmp + radix_tmp_words(n) + scan_tmp_words(n);
+  uint32_t* ncand = total + 1;
+  sl.ncand = ncand;
   cudaError_t e = launch_preprocess(sl.P, sl.cam, sl.set, (float4*)sl.rec.p, (uint2*)sl.rect.p,
                                     (uint32_t*)sl.tcount.p, (uint32_t*)sl.dkey.p, (uint32_t*)sl.idx.p,
-                                    (uint32_t*)sl.cand.p, total + 1, (RowGeom*)sl.geom.p, st);
+                                    (uint32_t*)sl.cand.p, ncand, (RowGeom*)sl.geom.p, (uint32_t*)sl.cnts.p,
+                                    rtmp + radix_tmp_words(n), st);
   uint32_t *skey = nullptr, *sidx = nullptr;
   if (e == cudaSuccess)
     e = radix_sort_pairs((uint32_t*)sl.dkey.p, (uint32_t*)sl.idx.p, (uint32_t*)sl.dkey2.p,
-                         (uint32_t*)sl.idx2.p, n, 32, rtmp, &skey, &sidx, st);
-  if (e == cudaSuccess) e = launch_gather_counts(sidx, (uint32_t*)sl.tcount.p, (uint32_t*)sl.cnts.p, n, st);
+                         (uint32_t*)sl.idx2.p, n, 32, rtmp, &skey, &sidx, st, ncand);
   if (e == cudaSuccess)
-    e = launch_scan((uint32_t*)sl.cnts.p, (uint32_t*)sl.offs.p, n, total, rtmp + radix_tmp_words(n), st);
+    e = launch_gather_counts(sidx, (uint32_t*)sl.tcount.p, (uint32_t*)sl.cnts.p, n, st, ncand);
+  if (e == cudaSuccess)
+    e = launch_scan((uint32_t*)sl.cnts.p, (uint32_t*)sl.offs.p, n, total, rtmp + radix_tmp_words(n), st,
+                    ncand);
   if (e == cudaSuccess) e = cudaMemcpyAsync(sl.k_host, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(sl.ev_a, st);
   if (e != cudaSuccess) {
@@ -262,7 +268,7 @@ int stage_b(gs_server* s, Slot& sl, std::string* msg) {
   while ((int64_t(1) << bits) < ntiles) ++bits;
   cudaError_t e = launch_emit(sl.sidx, (uint32_t*)sl.offs.p, (uint32_t*)sl.cnts.p, (uint2*)sl.rect.p,
                               (RowGeom*)sl.geom.p, sl.rf, sl.P.n, sl.cam.tiles_x, (uint32_t*)sl.keys.p,
-                              (uint32_t*)sl.vals.p, st);
+                              (uint32_t*)sl.vals.p, st, sl.ncand);
   uint32_t *tk = nullptr, *tv = nullptr;
   if (e == cudaSuccess)
     e = radix_sort_pairs((uint32_t*)sl.keys.p, (uint32_t*)sl.vals.p, (uint32_t*)sl.keys2.p,

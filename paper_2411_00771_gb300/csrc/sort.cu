@@ -19,6 +19,14 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kRadixBits = 8;
 constexpr int kBins = 1 << kRadixBits;
 
+// Item count: a host bound, lowered to a device-side count when one is given
+// (the grid is sized for the bound; blocks past the count do nothing).
+__device__ __forceinline__ int64_t item_count(int64_t n_max, const uint32_t* n_dev) {
+  if (!n_dev) return n_max;
+  const int64_t d = (int64_t)*n_dev;
+  return d < n_max ? d : n_max;
+}
+
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -49,8 +57,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
   return r;
 }
 
-__global__ void __launch_bounds__(kThreads) scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+__global__ void __launch_bounds__(kThreads) scan_reduce(const uint32_t* __restrict__ in, int64_t n_max,
+                                                        const uint32_t* __restrict__ n_dev,
                                                         uint32_t* __restrict__ sums) {
+  const int64_t n = item_count(n_max, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kTileItems;
   uint32_t s = 0;
   for (int i = threadIdx.x; i < kTileItems; i += kThreads) {
@@ -90,9 +100,11 @@ __global__ void __launch_bounds__(kThreads) scan_sums(uint32_t* __restrict__ sum
 }
 
 __global__ void __launch_bounds__(kThreads) scan_down(const uint32_t* __restrict__ in,
-                                                      uint32_t* __restrict__ out, int64_t n,
+                                                      uint32_t* __restrict__ out, int64_t n_max,
+                                                      const uint32_t* __restrict__ n_dev,
                                                       const uint32_t* __restrict__ sums) {
   __shared__ uint32_t tile[kTileItems];
+  const int64_t n = item_count(n_max, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kTileItems;
   // coalesced load into shared memory, then each thread scans kItems
   // consecutive entries
@@ -125,8 +137,10 @@ __global__ void __launch_bounds__(kThreads) scan_down(const uint32_t* __restrict
 // ---- radix sort -----------------------------------------------------------
 
 __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __restrict__ keys,
-                                                          int64_t n, int shift, int nbins,
+                                                          int64_t n_max, const uint32_t* __restrict__ n_dev,
+                                                          int shift, int nbins,
                                                           uint32_t* __restrict__ hist) {
+  const int64_t n = item_count(n_max, n_dev);
   __shared__ uint32_t h[kBins];
   for (int i = threadIdx.x; i < kBins; i += kThreads) h[i] = 0u;
   __syncthreads();
@@ -147,7 +161,9 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __rest
 
 __global__ void __launch_bounds__(kThreads) radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, int64_t n, int shift, int nbins, const uint32_t* __restrict__ offs) {
+    uint32_t* __restrict__ vout, int64_t n_max, const uint32_t* __restrict__ n_dev, int shift, int nbins,
+    const uint32_t* __restrict__ offs) {
+  const int64_t n = item_count(n_max, n_dev);
   __shared__ uint32_t wh[kWarps][kBins];
   for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) (&wh[0][0])[i] = 0u;
   __syncthreads();
@@ -194,7 +210,8 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
 
 __global__ void gather_counts_kernel(const uint32_t* __restrict__ order,
                                      const uint32_t* __restrict__ tcount, uint32_t* __restrict__ out,
-                                     int64_t n) {
+                                     int64_t n_max, const uint32_t* __restrict__ n_dev) {
+  const int64_t n = item_count(n_max, n_dev);
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < n) out[r] = tcount[order[r]];
 }
@@ -204,8 +221,10 @@ __global__ void gather_counts_kernel(const uint32_t* __restrict__ order,
 // on the same stored doubles, that counted them in the preprocess).
 __global__ void emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offs,
                             const uint32_t* __restrict__ counts, const uint2* __restrict__ rect,
-                            const RowGeom* __restrict__ geom, float rf, int64_t n, int tiles_x,
+                            const RowGeom* __restrict__ geom, float rf, int64_t n_max,
+                            const uint32_t* __restrict__ n_dev, int tiles_x,
                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t n = item_count(n_max, n_dev);
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n || counts[r] == 0) return;
   const uint32_t s = order[r];
@@ -237,15 +256,16 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t K, int2
 size_t scan_tmp_words(int64_t n) { return (size_t)div_up(n > 0 ? n : 1, kTileItems) + 1; }
 
 cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
-                        uint32_t* tmp, cudaStream_t st) {
+                        uint32_t* tmp, cudaStream_t st, const uint32_t* n_dev) {
   if (n <= 0) {
     return total_dev ? cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), st) : cudaSuccess;
   }
   const unsigned nb = div_up(n, kTileItems);
+  ProfScope ps(kProfSort, st);
   count_launch(3);
-  scan_reduce<<<nb, kThreads, 0, st>>>(in, n, tmp);
+  scan_reduce<<<nb, kThreads, 0, st>>>(in, n, n_dev, tmp);
   scan_sums<<<1, kThreads, 0, st>>>(tmp, (int)nb, total_dev);
-  scan_down<<<nb, kThreads, 0, st>>>(in, out, n, tmp);
+  scan_down<<<nb, kThreads, 0, st>>>(in, out, n, n_dev, tmp);
   return cudaGetLastError();
 }
 
@@ -257,10 +277,12 @@ size_t radix_tmp_words(int64_t n) {
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, uint32_t* tmp,
-                             uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st) {
+                             uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st,
+                             const uint32_t* n_dev) {
   *keys_out = keys;
   *vals_out = vals;
   if (n <= 1 || bits <= 0) return cudaSuccess;
+  ProfScope ps(kProfSort, st);
   const unsigned nb = div_up(n, kTileItems);
   const size_t h = (size_t)nb * kBins;
   uint32_t* hist = tmp;
@@ -271,10 +293,10 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
     const int pb = bits - shift < kRadixBits ? bits - shift : kRadixBits;
     const int nbins = 1 << pb;
     count_launch(2);
-    radix_upsweep<<<nb, kThreads, 0, st>>>(ki, n, shift, nbins, hist);
-    cudaError_t e = launch_scan(hist, offs, (int64_t)nbins * nb, nullptr, stmp, st);
+    radix_upsweep<<<nb, kThreads, 0, st>>>(ki, n, n_dev, shift, nbins, hist);
+    cudaError_t e = launch_scan(hist, offs, (int64_t)nbins * nb, nullptr, stmp, st, nullptr);
     if (e != cudaSuccess) return e;
-    radix_downsweep<<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, shift, nbins, offs);
+    radix_downsweep<<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, nbins, offs);
     uint32_t* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
   }
@@ -284,24 +306,28 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
 }
 
 cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* tcount, uint32_t* out,
-                                 int64_t n, cudaStream_t st) {
+                                 int64_t n, cudaStream_t st, const uint32_t* n_dev) {
   if (n <= 0) return cudaSuccess;
+  ProfScope ps(kProfSort, st);
   count_launch();
-  gather_counts_kernel<<<div_up(n, 256), 256, 0, st>>>(order, tcount, out, n);
+  gather_counts_kernel<<<div_up(n, 256), 256, 0, st>>>(order, tcount, out, n, n_dev);
   return cudaGetLastError();
 }
 
 cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint32_t* counts,
                         const uint2* rect, const RowGeom* geom, float rf, int64_t n, int tiles_x,
-                        uint32_t* keys, uint32_t* vals, cudaStream_t st) {
+                        uint32_t* keys, uint32_t* vals, cudaStream_t st, const uint32_t* n_dev) {
   if (n <= 0) return cudaSuccess;
+  ProfScope ps(kProfSort, st);
   count_launch();
-  emit_kernel<<<div_up(n, 256), 256, 0, st>>>(order, offs, counts, rect, geom, rf, n, tiles_x, keys, vals);
+  emit_kernel<<<div_up(n, 256), 256, 0, st>>>(order, offs, counts, rect, geom, rf, n, n_dev, tiles_x, keys,
+                                               vals);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(const uint32_t* keys, int64_t K, int2* ranges, int ntiles,
                           cudaStream_t st) {
+  ProfScope ps(kProfSort, st);
   cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)ntiles, st);
   if (e != cudaSuccess || K <= 0) return e;
   count_launch();
