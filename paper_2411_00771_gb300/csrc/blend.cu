@@ -1,27 +1,33 @@
 // Per-pixel compositing (forward) and its adjoint (reverse replay).
 //
 // Forward (Eq. 1, Sec. 3.1, with the 2DGS surfel model and the low-pass
-// filter of Sec. 3.2): one CTA per 16 x 16 tile, one thread per pixel, each
-// warp an 8 x 4 block of pixels.  The tile's depth-sorted surfel list is
-// staged through shared memory in batches of 256 entries; while staging,
-// one thread per entry works out which of the tile's eight warp blocks the
-// entry's footprint reaches (a conservative cover from the stored footprint
-// shape), and warps skip entries that cannot touch them.  Each pixel
+// filter of Sec. 3.2): one CTA of 128 threads per 16 x 16 tile; each warp
+// covers an 8 x 8 block of pixels and each thread two pixels of one column,
+// four rows apart, so that an entry read from shared memory serves two
+// pixels and the two per-pixel dependency chains interleave.  The tile's
+// depth-sorted surfel list is staged through shared memory in batches of
+// 256 entries; while staging, each entry's footprint is tested against the
+// tile's four warp blocks (a conservative cover from the stored footprint
+// shape) and warps skip entries that cannot touch them.  Each pixel
 // intersects its ray with the surfel plane (rho_obj), takes the
 // screen-space filter (rho_scr) where smaller, and composites front to back
 // until the transmittance would drop below T_min.
 //
 // Backward: the same tiles replay each pixel's list back to front from the
 // final transmittance, T_before = T_after / (1 - alpha), with suffix sums
-// for d L / d alpha.  Per-pair gradients are reduced across each warp with a
-// reduce-scatter of shuffles, summed per tile in shared memory, and added
-// to global memory once per (surfel, tile).
+// for d L / d alpha.  A thread adds the gradients of its two pixels, the
+// warp reduces them with a reduce-scatter of shuffles (one reduction per 64
+// pixels), the tile sums them in shared memory, and they reach global
+// memory once per (surfel, tile).
 #include <math.h>
 
 #include "gs2d_internal.cuh"
 
 namespace gs2d {
 namespace {
+
+constexpr int kThreads = 128;  // threads per tile CTA, two pixels each
+constexpr int kBatch = 256;    // list entries staged per batch
 
 // Hardware approximations (relative error about 2^-22), the same
 // instructions in both blends so that the replay reproduces the forward's
@@ -38,10 +44,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 constexpr float kNegHalfLog2e = -0.72134752044448170f;  // -log2(e) / 2
 
-// pixel of thread t within its tile: warp w covers columns 8 (w & 1) .. +7
-// and rows 4 (w >> 1) .. +3
+// Pixels of thread t within its tile: warp w covers columns 8 (w & 1) .. +7
+// and rows 8 (w >> 1) .. +7; lane l takes column l & 7 and rows l >> 3 and
+// (l >> 3) + 4 of that block.
 __device__ __forceinline__ int local_x(int t) { return (((t >> 5) & 1) << 3) | (t & 7); }
-__device__ __forceinline__ int local_y(int t) { return ((t >> 6) << 2) | ((t >> 3) & 3); }
+__device__ __forceinline__ int local_y(int t) { return ((t >> 6) << 3) | ((t >> 3) & 3); }
 
 // Staged entry: s0 = (c.x, c.y relative to the tile origin, e.x, e.y),
 // s1 = Ji, s2 = (p_z, opacity, r, g), s3 = (b, n.x, n.y, n.z); wmask bit w
@@ -67,11 +74,11 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
   const RowGeom g = geom[s];
   uint32_t m = 0u;
 #pragma unroll
-  for (int b = 0; b < kTile / 4; ++b) {
-    const int ja = ty0 + 4 * b;
+  for (int b = 0; b < 2; ++b) {
+    const int ja = ty0 + 8 * b;
     if (ja >= H) break;
     int ilo, ihi;
-    if (!band_pixels(g, ja, min(ja + 3, H - 1), rf, &ilo, &ihi)) continue;
+    if (!band_pixels(g, ja, min(ja + 7, H - 1), rf, &ilo, &ihi)) continue;
     if (ilo <= tx0 + 7 && ihi >= tx0) m |= 1u << (2 * b);
     if (ilo <= tx0 + 15 && ihi >= tx0 + 8) m |= 1u << (2 * b + 1);
   }
@@ -112,10 +119,92 @@ __device__ __forceinline__ Pair eval_pair(float lx, float ly, float4 s0, float4 
   return q;
 }
 
+// ---------------------------------------------------------------------------
+// Forward.
+
+// Running sums of one pixel.  Z is accumulated relative to zr, the depth of
+// the first blended pair: sum w (z - zr) keeps the distortion terms z A - Z
+// free of the cancellation between depths of hundreds of metres (both are
+// invariant under a common shift of z), and sum w z = sum w (z - zr) + zr A.
+struct FwdPix {
+  float T, C0, C1, C2, A, Zs, zr, I, N0, N1, N2, D, M;
+  int cnt, lastpos, medpos;
+  unsigned evaluated;
+  bool done;
+};
+
+__device__ __forceinline__ void fwd_init(FwdPix& p, bool inside) {
+  p.T = 1.f;
+  p.C0 = p.C1 = p.C2 = p.A = p.Zs = p.zr = p.I = p.N0 = p.N1 = p.N2 = p.D = p.M = 0.f;
+  p.cnt = 0;
+  p.lastpos = 0;
+  p.medpos = -1;
+  p.evaluated = 0;
+  p.done = !inside;
+}
+
+// One list entry (position pos) against one pixel.
+__device__ __forceinline__ void fwd_step(FwdPix& p, float lx, float ly, float4 e0, float4 e1, float4 e2,
+                                         const float4* s3, int kk, int pos, const SetDev& set) {
+  ++p.evaluated;
+  const Pair q = eval_pair(lx, ly, e0, e1, e2.y, set);
+  if (!q.hit) return;
+  const float Tn = p.T * (1.f - q.alpha);
+  if (Tn < set.T_min) {
+    p.done = true;
+    return;
+  }
+  const float w = q.alpha * p.T;
+  const float z = q.obj ? e2.x * q.rden : e2.x;
+  const float4 e3 = s3[kk];
+  p.C0 = fmaf(w, e2.z, p.C0);
+  p.C1 = fmaf(w, e2.w, p.C1);
+  p.C2 = fmaf(w, e3.x, p.C2);
+  if (p.cnt == 0) p.zr = z;
+  const float zs = z - p.zr;
+  p.D = fmaf(2.f * w, fmaf(zs, p.A, -p.Zs), p.D);
+  p.A += w;
+  p.Zs = fmaf(w, zs, p.Zs);
+  p.I = fmaf(w, rcp_approx(z), p.I);
+  p.N0 = fmaf(w, e3.y, p.N0);
+  p.N1 = fmaf(w, e3.z, p.N1);
+  p.N2 = fmaf(w, e3.w, p.N2);
+  if (p.T > 0.5f) {
+    p.M = z;
+    p.medpos = pos;
+  }
+  p.T = Tn;
+  ++p.cnt;
+  p.lastpos = pos + 1;
+}
+
+__device__ __forceinline__ void fwd_store(const FwdPix& p, const CamDev& cam, const SetDev& set, int px,
+                                          int py, float* __restrict__ out, int32_t* __restrict__ n_contrib,
+                                          int32_t* __restrict__ last, int32_t* __restrict__ med) {
+  if (px >= cam.W || py >= cam.H) return;
+  const size_t HW = (size_t)cam.W * cam.H;
+  const size_t i = (size_t)py * cam.W + px;
+  out[i] = p.C0 + p.T * set.bg[0];
+  out[HW + i] = p.C1 + p.T * set.bg[1];
+  out[2 * HW + i] = p.C2 + p.T * set.bg[2];
+  out[3 * HW + i] = p.A;
+  out[4 * HW + i] = fmaf(p.zr, p.A, p.Zs);
+  out[5 * HW + i] = p.I;
+  out[6 * HW + i] = p.M;
+  out[7 * HW + i] = p.N0;
+  out[8 * HW + i] = p.N1;
+  out[9 * HW + i] = p.N2;
+  out[10 * HW + i] = p.D;
+  out[11 * HW + i] = p.T;
+  if (n_contrib) n_contrib[i] = p.cnt;
+  if (last) last[i] = p.lastpos;
+  if (med) med[i] = p.medpos;
+}
+
 // Shared-memory staging area of one CTA.
 struct FwdSmem {
-  float4 s0[kBlock], s1[kBlock], s2[kBlock], s3[kBlock];
-  uint32_t sm[kBlock];
+  float4 s0[kBatch], s1[kBatch], s2[kBatch], s3[kBatch];
+  uint32_t sm[kBatch];
   unsigned long long tot[2];
 };
 
@@ -125,102 +214,48 @@ __device__ __forceinline__ void blend_fwd_tile(
     const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
     float* __restrict__ out, int32_t* __restrict__ n_contrib, int32_t* __restrict__ last,
     int32_t* __restrict__ med, unsigned long long* __restrict__ counters, int bx, int by) {
-  float4* s0 = sh.s0;
-  float4* s1 = sh.s1;
-  float4* s2 = sh.s2;
-  float4* s3 = sh.s3;
-  uint32_t* sm = sh.sm;
   const int tile = by * cam.tiles_x + bx;
   const int tx0 = bx * kTile, ty0 = by * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
-  const int px = tx0 + lxi, py = ty0 + lyi;
+  const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
   const int warp = threadIdx.x >> 5;
-  const bool inside = px < cam.W && py < cam.H;
-  const float lx = (float)lxi + 0.5f, ly = (float)lyi + 0.5f;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
   const int2 rg = ranges[tile];
   const int len = rg.y - rg.x;
-  bool done = !inside;
-  // Z is accumulated relative to zr, the depth of the first blended pair:
-  // sum w (z - zr) keeps the distortion terms z A - Z free of the
-  // cancellation between depths of hundreds of metres (both are invariant
-  // under a common shift of z), and sum w z = sum w (z - zr) + zr A.
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f, Zs = 0.f, zr = 0.f, I = 0.f;
-  float N0 = 0.f, N1 = 0.f, N2 = 0.f, D = 0.f, M = 0.f;
-  int cnt = 0, lastpos = 0, medpos = -1;
-  unsigned evaluated = 0;
-  for (int b0 = 0; b0 < len; b0 += kBlock) {
-    if (__syncthreads_count(done) == kBlock) break;
-    const int j = b0 + threadIdx.x;
-    if (j < len) {
-      const Staged e = stage_entry(rec, geom, vals[rg.x + j], tx0, ty0, cam.H, rf);
-      s0[threadIdx.x] = e.s0;
-      s1[threadIdx.x] = e.s1;
-      s2[threadIdx.x] = e.s2;
-      s3[threadIdx.x] = e.s3;
-      sm[threadIdx.x] = e.wmask;
+  FwdPix a, b;
+  fwd_init(a, px < cam.W && pyA < cam.H);
+  fwd_init(b, px < cam.W && pyB < cam.H);
+  for (int b0 = 0; b0 < len; b0 += kBatch) {
+    if (__syncthreads_count(a.done && b.done) == kThreads) break;
+#pragma unroll
+    for (int h = 0; h < kBatch / kThreads; ++h) {
+      const int t = threadIdx.x + h * kThreads;
+      if (b0 + t < len) {
+        const Staged e = stage_entry(rec, geom, vals[rg.x + b0 + t], tx0, ty0, cam.H, rf);
+        sh.s0[t] = e.s0;
+        sh.s1[t] = e.s1;
+        sh.s2[t] = e.s2;
+        sh.s3[t] = e.s3;
+        sh.sm[t] = e.wmask;
+      }
     }
     __syncthreads();
-    const int nb = min(kBlock, len - b0);
-    for (int k = 0; k < nb && !done; ++k) {
-      if (!((sm[k] >> warp) & 1u)) continue;  // footprint misses this warp's block
-      ++evaluated;
-      const float4 e2 = s2[k];
-      const Pair q = eval_pair(lx, ly, s0[k], s1[k], e2.y, set);
-      if (!q.hit) continue;
-      const float Tn = T * (1.f - q.alpha);
-      if (Tn < set.T_min) {
-        done = true;
-        break;
-      }
-      const float w = q.alpha * T;
-      const float z = q.obj ? e2.x * q.rden : e2.x;
-      const float4 e3 = s3[k];
-      C0 = fmaf(w, e2.z, C0);
-      C1 = fmaf(w, e2.w, C1);
-      C2 = fmaf(w, e3.x, C2);
-      if (cnt == 0) zr = z;
-      const float zs = z - zr;
-      D = fmaf(2.f * w, fmaf(zs, A, -Zs), D);
-      A += w;
-      Zs = fmaf(w, zs, Zs);
-      I = fmaf(w, rcp_approx(z), I);
-      N0 = fmaf(w, e3.y, N0);
-      N1 = fmaf(w, e3.z, N1);
-      N2 = fmaf(w, e3.w, N2);
-      if (T > 0.5f) {
-        M = z;
-        medpos = b0 + k;
-      }
-      T = Tn;
-      ++cnt;
-      lastpos = b0 + k + 1;
+    const int nb = min(kBatch, len - b0);
+    for (int k = 0; k < nb && !(a.done && b.done); ++k) {
+      if (!((sh.sm[k] >> warp) & 1u)) continue;  // footprint misses this warp's block
+      const float4 e0 = sh.s0[k], e1 = sh.s1[k], e2 = sh.s2[k];
+      if (!a.done) fwd_step(a, lx, lyA, e0, e1, e2, sh.s3, k, b0 + k, set);
+      if (!b.done) fwd_step(b, lx, lyB, e0, e1, e2, sh.s3, k, b0 + k, set);
     }
   }
-  if (inside) {
-    const size_t HW = (size_t)cam.W * cam.H;
-    const size_t p = (size_t)py * cam.W + px;
-    out[p] = C0 + T * set.bg[0];
-    out[HW + p] = C1 + T * set.bg[1];
-    out[2 * HW + p] = C2 + T * set.bg[2];
-    out[3 * HW + p] = A;
-    out[4 * HW + p] = fmaf(zr, A, Zs);
-    out[5 * HW + p] = I;
-    out[6 * HW + p] = M;
-    out[7 * HW + p] = N0;
-    out[8 * HW + p] = N1;
-    out[9 * HW + p] = N2;
-    out[10 * HW + p] = D;
-    out[11 * HW + p] = T;
-    if (n_contrib) n_contrib[p] = cnt;
-    if (last) last[p] = lastpos;
-    if (med) med[p] = medpos;
-  }
+  fwd_store(a, cam, set, px, pyA, out, n_contrib, last, med);
+  fwd_store(b, cam, set, px, pyB, out, n_contrib, last, med);
   if (counters) {
     // per-tile totals of evaluated and blended pairs (performance counters)
     unsigned long long* tot = sh.tot;
     if (threadIdx.x == 0) tot[0] = tot[1] = 0ull;
     __syncthreads();
-    unsigned e = evaluated, c = (unsigned)cnt;
+    unsigned e = a.evaluated + b.evaluated, c = (unsigned)(a.cnt + b.cnt);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -238,7 +273,7 @@ __device__ __forceinline__ void blend_fwd_tile(
   }
 }
 
-__global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
+__global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
     CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
     const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, float* __restrict__ out,
     int32_t* __restrict__ n_contrib, int32_t* __restrict__ last, int32_t* __restrict__ med,
@@ -252,7 +287,7 @@ __global__ void __launch_bounds__(kBlock) blend_fwd_kernel(
 // CTA takes (view, tile) work items from a device counter until all tiles
 // of all views in the batch are done; views of different sizes and scenes
 // share one launch.
-__global__ void __launch_bounds__(kBlock) blend_fwd_batched_kernel(BlendBatch batch) {
+__global__ void __launch_bounds__(kThreads) blend_fwd_batched_kernel(BlendBatch batch) {
   __shared__ FwdSmem sh;
   __shared__ int item;
   for (;;) {
@@ -322,8 +357,151 @@ __device__ __forceinline__ int rs_slot(int lane) {
   return real > 0 ? slot : -1;
 }
 
+// Per-pixel state of the reverse replay: transmittance, suffix sums S of
+// each adjoint set, the pixel's adjoints, and (general layout) the running
+// opacity A and depth sum Z with their final values for the distortion.
+struct BwdPix {
+  float T, A, Z, Af, Zf;
+  float S[kMaxSets];
+  float gC[kMaxSets][3];
+  float gA, gZ, gI, gMed, gD, gN0, gN1, gN2;
+  int last, med;
+};
+
 template <bool kLoss>
-__global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
+__device__ __forceinline__ void bwd_init(BwdPix& p, bool inside, size_t pix, size_t HW,
+                                         const float* __restrict__ out, const int32_t* __restrict__ last,
+                                         const int32_t* __restrict__ med, const AdjDev& adj,
+                                         const SetDev& set) {
+  p.T = 1.f;
+  p.A = p.Z = p.Af = p.Zf = 0.f;
+  p.gA = p.gZ = p.gI = p.gMed = p.gD = p.gN0 = p.gN1 = p.gN2 = 0.f;
+  p.last = 0;
+  p.med = -1;
+#pragma unroll
+  for (int s = 0; s < kMaxSets; ++s) {
+    p.gC[s][0] = p.gC[s][1] = p.gC[s][2] = 0.f;
+    p.S[s] = 0.f;
+  }
+  if (!inside) return;
+  p.last = last[pix];
+  p.T = out[11 * HW + pix];
+#pragma unroll
+  for (int s = 0; s < kMaxSets; ++s) {
+    if (s >= adj.n_sets) break;
+    const float* a = adj.set[s];
+    const uint32_t m = adj.mask[s];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p.gC[s][c] = (m >> c) & 1u ? a[c * HW + pix] : 0.f;
+    p.S[s] = p.T * (p.gC[s][0] * set.bg[0] + p.gC[s][1] * set.bg[1] + p.gC[s][2] * set.bg[2]);
+  }
+  const float* a = adj.set[0];
+  const uint32_t m = adj.mask[0];
+  if (m & (1u << 5)) p.gI = a[5 * HW + pix];
+  if constexpr (!kLoss) {
+    p.med = med[pix];
+    p.Af = p.A = out[3 * HW + pix];
+    p.Zf = p.Z = out[4 * HW + pix];
+    if (m & (1u << 3)) p.gA = a[3 * HW + pix];
+    if (m & (1u << 4)) p.gZ = a[4 * HW + pix];
+    if (m & (1u << 6)) p.gMed = a[6 * HW + pix];
+    if (m & (1u << 7)) p.gN0 = a[7 * HW + pix];
+    if (m & (1u << 8)) p.gN1 = a[8 * HW + pix];
+    if (m & (1u << 9)) p.gN2 = a[9 * HW + pix];
+    if (m & (1u << 10)) p.gD = a[10 * HW + pix];
+  }
+}
+
+// Gradient of one blended pair at list position k, added into v
+// (gradient-vector layout); advances the pixel's replay state.
+template <bool kLoss>
+__device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, float4 e1, float4 e2,
+                                         float4 e3, int k, int nsets, const SetDev& set, float* v) {
+  using LY = Layout<kLoss>;
+  const float rom = rcp_approx(1.f - q.alpha);
+  p.T = p.T * rom;  // transmittance before this pair
+  const float w = q.alpha * p.T;
+  const float pz = e2.x;
+  const float z = q.obj ? pz * q.rden : pz;
+  const float rz = rcp_approx(z);
+  float dLdw = p.gC[0][0] * e2.z + p.gC[0][1] * e2.w + p.gC[0][2] * e3.x + p.gI * rz;
+  float dzv = -w * p.gI * rz * rz;
+  if constexpr (!kLoss) {
+    const float Ap = p.A - w, Zp = p.Z - w * z;
+    const float dDdw = 2.f * (z * Ap - Zp + (p.Zf - p.Z) - z * (p.Af - p.A));
+    dLdw += p.gA + p.gZ * z + p.gN0 * e3.y + p.gN1 * e3.z + p.gN2 * e3.w + p.gD * dDdw;
+    dzv += w * p.gZ + p.gD * 2.f * w * (Ap - (p.Af - p.A)) + (k == p.med ? p.gMed : 0.f);
+    p.A = Ap;
+    p.Z = Zp;
+  }
+  float dLda[kMaxSets];
+  dLda[0] = p.T * dLdw - p.S[0] * rom;
+  p.S[0] += w * dLdw;
+#pragma unroll
+  for (int s = 1; s < kMaxSets; ++s) {
+    if (s < nsets) {
+      const float dw = p.gC[s][0] * e2.z + p.gC[s][1] * e2.w + p.gC[s][2] * e3.x;
+      dLda[s] = p.T * dw - p.S[s] * rom;
+      p.S[s] += w * dw;
+    } else {
+      dLda[s] = 0.f;
+    }
+  }
+  // alpha -> rho (zero where alpha is clamped at alpha_max)
+  const bool unclamped = e2.y * q.G < set.alpha_max;
+  const float dadrho = unclamped ? -0.5f * q.alpha : 0.f;
+  const float drho = dLda[0] * dadrho;
+  // d rho / d offset
+  float rx, ry, gdx, gdy, gpz;
+  if (q.obj) {
+    const float r2d = q.rden * q.rden;
+    const float tx = q.nu * e1.x + q.nv * e1.z, ty = q.nu * e1.y + q.nv * e1.w;
+    const float c2 = 2.f * q.rho * q.rden;
+    rx = 2.f * r2d * tx - c2 * e0.z;
+    ry = 2.f * r2d * ty - c2 * e0.w;
+    // rho = u^2 + v^2 with (u, v) = (nu, nv) rden, z = p_z rden
+    const float u = q.nu * q.rden, vv = q.nv * q.rden;
+    const float dnu = 2.f * u * q.rden * drho, dnv = 2.f * vv * q.rden * drho;
+    const float drden = 2.f * drho * (u * q.nu + vv * q.nv) + dzv * pz;
+    const float dden = -drden * r2d;
+    v[0] += dnu * q.dx;
+    v[1] += dnu * q.dy;
+    v[2] += dnv * q.dx;
+    v[3] += dnv * q.dy;
+    v[4] += dden * q.dx;
+    v[5] += dden * q.dy;
+    gdx = dnu * e1.x + dnv * e1.z + dden * e0.z;
+    gdy = dnu * e1.y + dnv * e1.w + dden * e0.w;
+    gpz = dzv * q.rden;
+  } else {
+    rx = 2.f * set.sinv * q.dx;
+    ry = 2.f * set.sinv * q.dy;
+    gdx = drho * rx;
+    gdy = drho * ry;
+    gpz = dzv;
+  }
+  v[6] -= gdx;
+  v[7] -= gdy;
+  v[8] += gpz;
+  if (unclamped) v[9] += dLda[0] * q.G;
+  v[10] += w * p.gC[0][0];
+  v[11] += w * p.gC[0][1];
+  v[12] += w * p.gC[0][2];
+  if constexpr (!kLoss) {
+    v[13] += w * p.gN0;
+    v[14] += w * p.gN1;
+    v[15] += w * p.gN2;
+  }
+#pragma unroll
+  for (int s = 0; s < kMaxSets; ++s) {
+    const float dr = dLda[s] * dadrho;
+    v[LY::kRec + 2 * s] -= dr * rx;
+    v[LY::kRec + 2 * s + 1] -= dr * ry;
+  }
+}
+
+template <bool kLoss>
+__global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
     CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
     const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, const float* __restrict__ out,
     const int32_t* __restrict__ last, const int32_t* __restrict__ med, AdjDev adj,
@@ -331,97 +509,69 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
     unsigned long long* __restrict__ counters) {
   using LY = Layout<kLoss>;
   constexpr int kN = LY::kN;
-  __shared__ float4 s0[kBlock], s1[kBlock], s2[kBlock], s3[kBlock];
-  __shared__ uint32_t sm[kBlock];
-  __shared__ uint32_t sid[kBlock];
-  __shared__ float acc[kBlock][kN + 1];
+  __shared__ float4 s0[kBatch], s1[kBatch], s2[kBatch], s3[kBatch];
+  __shared__ uint32_t sm[kBatch];
+  __shared__ uint32_t sid[kBatch];
+  __shared__ float acc[kBatch][kN + 1];
   __shared__ int smax;
   const int tile = blockIdx.y * cam.tiles_x + blockIdx.x;
   const int tx0 = blockIdx.x * kTile, ty0 = blockIdx.y * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
-  const int px = tx0 + lxi, py = ty0 + lyi;
+  const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
   const int warp = threadIdx.x >> 5;
-  const bool inside = px < cam.W && py < cam.H;
-  const float lx = (float)lxi + 0.5f, ly = (float)lyi + 0.5f;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
   const int2 rg = ranges[tile];
   const size_t HW = (size_t)cam.W * cam.H;
-  const size_t p = inside ? (size_t)py * cam.W + px : 0;
   const int lane = threadIdx.x & 31;
   const int nsets = adj.n_sets;
   const int myslot = rs_slot<kN>(lane);
-
-  int lastpos = 0, medpos = -1;
-  float T = 1.f, A = 0.f, Z = 0.f, Af = 0.f, Zf = 0.f;
-  float gC[kMaxSets][3];
-  float gA = 0.f, gZ = 0.f, gI = 0.f, gMed = 0.f, gD = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
-  float S[kMaxSets];
-#pragma unroll
-  for (int s = 0; s < kMaxSets; ++s) {
-    gC[s][0] = gC[s][1] = gC[s][2] = 0.f;
-    S[s] = 0.f;
-  }
-  if (inside) {
-    lastpos = last[p];
-    T = out[11 * HW + p];
-#pragma unroll
-    for (int s = 0; s < kMaxSets; ++s) {
-      if (s >= nsets) break;
-      const float* a = adj.set[s];
-      const uint32_t m = adj.mask[s];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) gC[s][c] = (m >> c) & 1u ? a[c * HW + p] : 0.f;
-      S[s] = T * (gC[s][0] * set.bg[0] + gC[s][1] * set.bg[1] + gC[s][2] * set.bg[2]);
-    }
-    const float* a = adj.set[0];
-    const uint32_t m = adj.mask[0];
-    if (m & (1u << 5)) gI = a[5 * HW + p];
-    if constexpr (!kLoss) {
-      medpos = med[p];
-      Af = A = out[3 * HW + p];
-      Zf = Z = out[4 * HW + p];
-      if (m & (1u << 3)) gA = a[3 * HW + p];
-      if (m & (1u << 4)) gZ = a[4 * HW + p];
-      if (m & (1u << 6)) gMed = a[6 * HW + p];
-      if (m & (1u << 7)) gN0 = a[7 * HW + p];
-      if (m & (1u << 8)) gN1 = a[8 * HW + p];
-      if (m & (1u << 9)) gN2 = a[9 * HW + p];
-      if (m & (1u << 10)) gD = a[10 * HW + p];
-    }
-  }
+  const bool inA = px < cam.W && pyA < cam.H, inB = px < cam.W && pyB < cam.H;
+  BwdPix a, b;
+  bwd_init<kLoss>(a, inA, inA ? (size_t)pyA * cam.W + px : 0, HW, out, last, med, adj, set);
+  bwd_init<kLoss>(b, inB, inB ? (size_t)pyB * cam.W + px : 0, HW, out, last, med, adj, set);
   if (threadIdx.x == 0) smax = 0;
   __syncthreads();
-  atomicMax(&smax, lastpos);
+  atomicMax(&smax, max(a.last, b.last));
   __syncthreads();
   const int maxlast = smax;
   unsigned replayed = 0, wentries = 0, wlanes = 0;
 
-  for (int bend = maxlast; bend > 0; bend -= kBlock) {
-    const int b0 = bend > kBlock ? bend - kBlock : 0;
+  for (int bend = maxlast; bend > 0; bend -= kBatch) {
+    const int b0 = bend > kBatch ? bend - kBatch : 0;
     const int nb = bend - b0;
     __syncthreads();
-    if (threadIdx.x < nb) {
-      const uint32_t s = vals[rg.x + b0 + threadIdx.x];
-      sid[threadIdx.x] = s;
-      const Staged e = stage_entry(rec, geom, s, tx0, ty0, cam.H, rf);
-      s0[threadIdx.x] = e.s0;
-      s1[threadIdx.x] = e.s1;
-      s2[threadIdx.x] = e.s2;
-      s3[threadIdx.x] = e.s3;
-      sm[threadIdx.x] = e.wmask;
+#pragma unroll
+    for (int h = 0; h < kBatch / kThreads; ++h) {
+      const int t = threadIdx.x + h * kThreads;
+      if (t < nb) {
+        const uint32_t s = vals[rg.x + b0 + t];
+        sid[t] = s;
+        const Staged e = stage_entry(rec, geom, s, tx0, ty0, cam.H, rf);
+        s0[t] = e.s0;
+        s1[t] = e.s1;
+        s2[t] = e.s2;
+        s3[t] = e.s3;
+        sm[t] = e.wmask;
+      }
     }
-    for (int i = threadIdx.x; i < nb * (kN + 1); i += kBlock) (&acc[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < nb * (kN + 1); i += kThreads) (&acc[0][0])[i] = 0.f;
     __syncthreads();
     for (int kk = nb - 1; kk >= 0; --kk) {
       if (!((sm[kk] >> warp) & 1u)) continue;  // footprint misses this warp's block
       const int k = b0 + kk;
-      Pair q;
-      q.hit = false;
       const float4 e0 = s0[kk], e1 = s1[kk], e2 = s2[kk];
-      if (k < lastpos) {
+      Pair qa, qb;
+      qa.hit = false;
+      qb.hit = false;
+      if (k < a.last) {
         ++replayed;
-        q = eval_pair(lx, ly, e0, e1, e2.y, set);
+        qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
       }
-      const bool contrib = q.hit;
+      if (k < b.last) {
+        ++replayed;
+        qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+      }
+      const bool contrib = qa.hit || qb.hit;
       const unsigned ballot = __ballot_sync(0xffffffffu, contrib);
       if (ballot == 0u) continue;
       ++wentries;
@@ -429,89 +579,9 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
       float v[kN];
 #pragma unroll
       for (int i = 0; i < kN; ++i) v[i] = 0.f;
-      if (contrib) {
-        const float4 e3 = s3[kk];
-        const float rom = rcp_approx(1.f - q.alpha);
-        T = T * rom;  // transmittance before this pair
-        const float w = q.alpha * T;
-        const float pz = e2.x;
-        const float z = q.obj ? pz * q.rden : pz;
-        const float rz = rcp_approx(z);
-        float dLdw = gC[0][0] * e2.z + gC[0][1] * e2.w + gC[0][2] * e3.x + gI * rz;
-        float dzv = -w * gI * rz * rz;
-        if constexpr (!kLoss) {
-          const float Ap = A - w, Zp = Z - w * z;
-          const float dDdw = 2.f * (z * Ap - Zp + (Zf - Z) - z * (Af - A));
-          dLdw += gA + gZ * z + gN0 * e3.y + gN1 * e3.z + gN2 * e3.w + gD * dDdw;
-          dzv += w * gZ + gD * 2.f * w * (Ap - (Af - A)) + (k == medpos ? gMed : 0.f);
-          A = Ap;
-          Z = Zp;
-        }
-        float dLda[kMaxSets];
-        dLda[0] = T * dLdw - S[0] * rom;
-        S[0] += w * dLdw;
-#pragma unroll
-        for (int s = 1; s < kMaxSets; ++s) {
-          if (s < nsets) {
-            const float dw = gC[s][0] * e2.z + gC[s][1] * e2.w + gC[s][2] * e3.x;
-            dLda[s] = T * dw - S[s] * rom;
-            S[s] += w * dw;
-          } else {
-            dLda[s] = 0.f;
-          }
-        }
-        // alpha -> rho (zero where alpha is clamped at alpha_max)
-        const bool unclamped = e2.y * q.G < set.alpha_max;
-        const float dadrho = unclamped ? -0.5f * q.alpha : 0.f;
-        const float drho = dLda[0] * dadrho;
-        // d rho / d offset
-        float rx, ry, gdx, gdy, gpz;
-        if (q.obj) {
-          const float r2d = q.rden * q.rden;
-          const float tx = q.nu * e1.x + q.nv * e1.z, ty = q.nu * e1.y + q.nv * e1.w;
-          const float c2 = 2.f * q.rho * q.rden;
-          rx = 2.f * r2d * tx - c2 * e0.z;
-          ry = 2.f * r2d * ty - c2 * e0.w;
-          // rho = u^2 + v^2 with (u, v) = (nu, nv) rden, z = p_z rden
-          const float u = q.nu * q.rden, vv = q.nv * q.rden;
-          const float dnu = 2.f * u * q.rden * drho, dnv = 2.f * vv * q.rden * drho;
-          const float drden = 2.f * drho * (u * q.nu + vv * q.nv) + dzv * pz;
-          const float dden = -drden * r2d;
-          v[0] = dnu * q.dx;
-          v[1] = dnu * q.dy;
-          v[2] = dnv * q.dx;
-          v[3] = dnv * q.dy;
-          v[4] = dden * q.dx;
-          v[5] = dden * q.dy;
-          gdx = dnu * e1.x + dnv * e1.z + dden * e0.z;
-          gdy = dnu * e1.y + dnv * e1.w + dden * e0.w;
-          gpz = dzv * q.rden;
-        } else {
-          rx = 2.f * set.sinv * q.dx;
-          ry = 2.f * set.sinv * q.dy;
-          gdx = drho * rx;
-          gdy = drho * ry;
-          gpz = dzv;
-        }
-        v[6] = -gdx;
-        v[7] = -gdy;
-        v[8] = gpz;
-        v[9] = unclamped ? dLda[0] * q.G : 0.f;
-        v[10] = w * gC[0][0];
-        v[11] = w * gC[0][1];
-        v[12] = w * gC[0][2];
-        if constexpr (!kLoss) {
-          v[13] = w * gN0;
-          v[14] = w * gN1;
-          v[15] = w * gN2;
-        }
-#pragma unroll
-        for (int s = 0; s < kMaxSets; ++s) {
-          const float dr = dLda[s] * dadrho;
-          v[LY::kRec + 2 * s] = -dr * rx;
-          v[LY::kRec + 2 * s + 1] = -dr * ry;
-        }
-      }
+      const float4 e3 = s3[kk];
+      if (qa.hit) bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
+      if (qb.hit) bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
       if (__popc(ballot) == 1) {
         if (contrib) {
 #pragma unroll
@@ -525,18 +595,18 @@ __global__ void __launch_bounds__(kBlock) blend_bwd_kernel(
     }
     __syncthreads();
     // flush this batch: one (surfel, tile) gradient record per entry
-    if (threadIdx.x < nb) {
-      const uint32_t s = sid[threadIdx.x];
+    for (int t = threadIdx.x; t < nb; t += kThreads) {
+      const uint32_t s = sid[t];
       float* g = grec + (size_t)s * kGradRec;
 #pragma unroll
       for (int i = 0; i < LY::kRec; ++i) {
-        const float x = acc[threadIdx.x][i];
+        const float x = acc[t][i];
         if (x != 0.f) atomicAdd(&g[i], x);
       }
       if (screen) {
         for (int st = 0; st < nsets; ++st) {
-          const float x0 = acc[threadIdx.x][LY::kRec + 2 * st];
-          const float x1 = acc[threadIdx.x][LY::kRec + 2 * st + 1];
+          const float x0 = acc[t][LY::kRec + 2 * st];
+          const float x1 = acc[t][LY::kRec + 2 * st + 1];
           float* sg = screen + ((size_t)st * n + s) * 2;
           if (x0 != 0.f) atomicAdd(&sg[0], x0);
           if (x1 != 0.f) atomicAdd(&sg[1], x1);
@@ -565,15 +635,15 @@ cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const float4*
   const dim3 grid(cam.tiles_x, cam.tiles_y);
   const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
   ProfScope ps(kProfBlendFwd, st);
-  blend_fwd_kernel<<<grid, kBlock, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, n_contrib, last,
-                                            med, counters);
+  blend_fwd_kernel<<<grid, kThreads, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, n_contrib, last,
+                                              med, counters);
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_blend_fwd_batched(const BlendBatch& batch, int grid, cudaStream_t st) {
   ProfScope ps(kProfBlendFwd, st);
-  blend_fwd_batched_kernel<<<grid, kBlock, 0, st>>>(batch);
+  blend_fwd_batched_kernel<<<grid, kThreads, 0, st>>>(batch);
   count_launch();
   return cudaGetLastError();
 }
@@ -591,11 +661,11 @@ cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const float4*
   for (int s = 1; s < adj.n_sets; ++s) loss_layout = loss_layout && (adj.mask[s] & ~GS_MASK_RGB) == 0u;
   ProfScope ps(kProfBlendBwd, st);
   if (loss_layout)
-    blend_bwd_kernel<true><<<grid, kBlock, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, last, med,
-                                                    adj, grec, screen, n, counters);
+    blend_bwd_kernel<true><<<grid, kThreads, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, last, med,
+                                                      adj, grec, screen, n, counters);
   else
-    blend_bwd_kernel<false><<<grid, kBlock, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, last, med,
-                                                     adj, grec, screen, n, counters);
+    blend_bwd_kernel<false><<<grid, kThreads, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, last, med,
+                                                       adj, grec, screen, n, counters);
   count_launch();
   return cudaGetLastError();
 }

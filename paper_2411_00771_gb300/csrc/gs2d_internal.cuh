@@ -9,7 +9,6 @@
 namespace gs2d {
 
 constexpr int kTile = 16;              // 16 x 16 pixel tiles
-constexpr int kBlock = kTile * kTile;  // one thread per pixel
 constexpr int kRecF4 = 5;              // per-surfel blend record, 5 x float4
 
 // Camera as the kernels see it (by value).  Geometry that decides where a

@@ -323,11 +323,11 @@ bool launch_batch(gs_server* s, const std::vector<int>& ready, std::string* msg)
   b.counter = s->counters + bi;
   cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s->blend_st);
   if (e == cudaSuccess) {
-    // persistent grid: three CTAs per SM (the blend's occupancy), no more
+    // persistent grid: four CTAs per SM (the blend's occupancy), no more
     // CTAs than tiles
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    e = launch_blend_fwd_batched(b, std::max(1, std::min(3 * sms, tiles)), s->blend_st);
+    e = launch_blend_fwd_batched(b, std::max(1, std::min(4 * sms, tiles)), s->blend_st);
   }
   Batch bt;
   bt.ev = get_event(s);
