@@ -248,7 +248,9 @@ def run_ours(args):
                 "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
                 "ms_per_launch": round(per_launch[dom], 4),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"}
-    breakdown = {k: round(v, 4) for k, v in per_launch.items()}
+    # per step: a group may record several scopes per step (the sort group
+    # covers every scan, radix pass, emit and range pass of a render)
+    breakdown = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -143,24 +143,24 @@ __device__ __forceinline__ void fwd_init(FwdPix& p, bool inside) {
   p.done = !inside;
 }
 
-// One list entry (position pos) against one pixel.
-__device__ __forceinline__ void fwd_step(FwdPix& p, float lx, float ly, float4 e0, float4 e1, float4 e2,
-                                         const float4* s3, int kk, int pos, const SetDev& set) {
-  ++p.evaluated;
-  const Pair q = eval_pair(lx, ly, e0, e1, e2.y, set);
-  if (!q.hit) return;
+// One list entry (position pos, already evaluated as q) against one pixel.
+// Branch-free, so that the two pixels of a thread interleave: a pair that is
+// not blended updates the sums with weight 0 (and a finite depth of 1), which
+// leaves them unchanged.
+__device__ __forceinline__ void fwd_step(FwdPix& p, const Pair& q, float4 e2, float4 e3, int pos,
+                                         const SetDev& set) {
+  p.evaluated += p.done ? 0u : 1u;
+  const bool h = !p.done && q.hit;
   const float Tn = p.T * (1.f - q.alpha);
-  if (Tn < set.T_min) {
-    p.done = true;
-    return;
-  }
-  const float w = q.alpha * p.T;
-  const float z = q.obj ? e2.x * q.rden : e2.x;
-  const float4 e3 = s3[kk];
+  const bool stop = h && Tn < set.T_min;
+  const bool bl = h && !stop;
+  p.done = p.done || stop;
+  const float w = bl ? q.alpha * p.T : 0.f;
+  const float z = bl ? (q.obj ? e2.x * q.rden : e2.x) : 1.f;
   p.C0 = fmaf(w, e2.z, p.C0);
   p.C1 = fmaf(w, e2.w, p.C1);
   p.C2 = fmaf(w, e3.x, p.C2);
-  if (p.cnt == 0) p.zr = z;
+  p.zr = (bl && p.cnt == 0) ? z : p.zr;
   const float zs = z - p.zr;
   p.D = fmaf(2.f * w, fmaf(zs, p.A, -p.Zs), p.D);
   p.A += w;
@@ -169,13 +169,12 @@ __device__ __forceinline__ void fwd_step(FwdPix& p, float lx, float ly, float4 e
   p.N0 = fmaf(w, e3.y, p.N0);
   p.N1 = fmaf(w, e3.z, p.N1);
   p.N2 = fmaf(w, e3.w, p.N2);
-  if (p.T > 0.5f) {
-    p.M = z;
-    p.medpos = pos;
-  }
-  p.T = Tn;
-  ++p.cnt;
-  p.lastpos = pos + 1;
+  const bool m = bl && p.T > 0.5f;
+  p.M = m ? z : p.M;
+  p.medpos = m ? pos : p.medpos;
+  p.T = bl ? Tn : p.T;
+  p.cnt += bl ? 1 : 0;
+  p.lastpos = bl ? pos + 1 : p.lastpos;
 }
 
 __device__ __forceinline__ void fwd_store(const FwdPix& p, const CamDev& cam, const SetDev& set, int px,
@@ -243,9 +242,11 @@ __device__ __forceinline__ void blend_fwd_tile(
     const int nb = min(kBatch, len - b0);
     for (int k = 0; k < nb && !(a.done && b.done); ++k) {
       if (!((sh.sm[k] >> warp) & 1u)) continue;  // footprint misses this warp's block
-      const float4 e0 = sh.s0[k], e1 = sh.s1[k], e2 = sh.s2[k];
-      if (!a.done) fwd_step(a, lx, lyA, e0, e1, e2, sh.s3, k, b0 + k, set);
-      if (!b.done) fwd_step(b, lx, lyB, e0, e1, e2, sh.s3, k, b0 + k, set);
+      const float4 e0 = sh.s0[k], e1 = sh.s1[k], e2 = sh.s2[k], e3 = sh.s3[k];
+      const Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
+      const Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+      fwd_step(a, qa, e2, e3, b0 + k, set);
+      fwd_step(b, qb, e2, e3, b0 + k, set);
     }
   }
   fwd_store(a, cam, set, px, pyA, out, n_contrib, last, med);
@@ -412,14 +413,28 @@ __device__ __forceinline__ void bwd_init(BwdPix& p, bool inside, size_t pix, siz
   }
 }
 
-// Gradient of one blended pair at list position k, added into v
-// (gradient-vector layout); advances the pixel's replay state.
+// A pair that was not blended (or lies past the pixel's last blended
+// entry) is masked so that every term of bwd_pair is a finite zero and the
+// pixel's state passes through unchanged: alpha = G = 0 and the
+// screen-space branch, whose terms are finite for any offset.
+__device__ __forceinline__ void mask_pair(Pair& q, bool live) {
+  const bool h = live && q.hit;
+  q.hit = h;
+  q.alpha = h ? q.alpha : 0.f;
+  q.G = h ? q.G : 0.f;
+  q.obj = h && q.obj;
+}
+
+// Gradient of one pair at list position k, added into v (gradient-vector
+// layout), and the pixel's replay state moved past it.  Branch-free, so that
+// the two pixels of a thread interleave: both branches of the ray-splat are
+// formed and the one the forward took is selected.
 template <bool kLoss>
 __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, float4 e1, float4 e2,
                                          float4 e3, int k, int nsets, const SetDev& set, float* v) {
   using LY = Layout<kLoss>;
   const float rom = rcp_approx(1.f - q.alpha);
-  p.T = p.T * rom;  // transmittance before this pair
+  p.T = q.hit ? p.T * rom : p.T;  // transmittance before this pair
   const float w = q.alpha * p.T;
   const float pz = e2.x;
   const float z = q.obj ? pz * q.rden : pz;
@@ -451,39 +466,31 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
   const bool unclamped = e2.y * q.G < set.alpha_max;
   const float dadrho = unclamped ? -0.5f * q.alpha : 0.f;
   const float drho = dLda[0] * dadrho;
-  // d rho / d offset
-  float rx, ry, gdx, gdy, gpz;
-  if (q.obj) {
-    const float r2d = q.rden * q.rden;
-    const float tx = q.nu * e1.x + q.nv * e1.z, ty = q.nu * e1.y + q.nv * e1.w;
-    const float c2 = 2.f * q.rho * q.rden;
-    rx = 2.f * r2d * tx - c2 * e0.z;
-    ry = 2.f * r2d * ty - c2 * e0.w;
-    // rho = u^2 + v^2 with (u, v) = (nu, nv) rden, z = p_z rden
-    const float u = q.nu * q.rden, vv = q.nv * q.rden;
-    const float dnu = 2.f * u * q.rden * drho, dnv = 2.f * vv * q.rden * drho;
-    const float drden = 2.f * drho * (u * q.nu + vv * q.nv) + dzv * pz;
-    const float dden = -drden * r2d;
-    v[0] += dnu * q.dx;
-    v[1] += dnu * q.dy;
-    v[2] += dnv * q.dx;
-    v[3] += dnv * q.dy;
-    v[4] += dden * q.dx;
-    v[5] += dden * q.dy;
-    gdx = dnu * e1.x + dnv * e1.z + dden * e0.z;
-    gdy = dnu * e1.y + dnv * e1.w + dden * e0.w;
-    gpz = dzv * q.rden;
-  } else {
-    rx = 2.f * set.sinv * q.dx;
-    ry = 2.f * set.sinv * q.dy;
-    gdx = drho * rx;
-    gdy = drho * ry;
-    gpz = dzv;
-  }
+  // object-space branch: rho = u^2 + v^2 with (u, v) = (nu, nv) rden,
+  // z = p_z rden (its terms may be non-finite where it was not taken)
+  const float r2d = q.rden * q.rden;
+  const float tx = q.nu * e1.x + q.nv * e1.z, ty = q.nu * e1.y + q.nv * e1.w;
+  const float c2 = 2.f * q.rho * q.rden;
+  const float u = q.nu * q.rden, vv = q.nv * q.rden;
+  const float dnu = 2.f * u * q.rden * drho, dnv = 2.f * vv * q.rden * drho;
+  const float drden = 2.f * drho * (u * q.nu + vv * q.nv) + dzv * pz;
+  const float dden = -drden * r2d;
+  const bool ob = q.obj;
+  const float rx = ob ? 2.f * r2d * tx - c2 * e0.z : 2.f * set.sinv * q.dx;
+  const float ry = ob ? 2.f * r2d * ty - c2 * e0.w : 2.f * set.sinv * q.dy;
+  const float gdx = ob ? dnu * e1.x + dnv * e1.z + dden * e0.z : drho * rx;
+  const float gdy = ob ? dnu * e1.y + dnv * e1.w + dden * e0.w : drho * ry;
+  const float gpz = ob ? dzv * q.rden : dzv;
+  v[0] += ob ? dnu * q.dx : 0.f;
+  v[1] += ob ? dnu * q.dy : 0.f;
+  v[2] += ob ? dnv * q.dx : 0.f;
+  v[3] += ob ? dnv * q.dy : 0.f;
+  v[4] += ob ? dden * q.dx : 0.f;
+  v[5] += ob ? dden * q.dy : 0.f;
   v[6] -= gdx;
   v[7] -= gdy;
   v[8] += gpz;
-  if (unclamped) v[9] += dLda[0] * q.G;
+  v[9] += unclamped ? dLda[0] * q.G : 0.f;
   v[10] += w * p.gC[0][0];
   v[11] += w * p.gC[0][1];
   v[12] += w * p.gC[0][2];
@@ -560,17 +567,12 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
       if (!((sm[kk] >> warp) & 1u)) continue;  // footprint misses this warp's block
       const int k = b0 + kk;
       const float4 e0 = s0[kk], e1 = s1[kk], e2 = s2[kk];
-      Pair qa, qb;
-      qa.hit = false;
-      qb.hit = false;
-      if (k < a.last) {
-        ++replayed;
-        qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
-      }
-      if (k < b.last) {
-        ++replayed;
-        qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
-      }
+      const bool liveA = k < a.last, liveB = k < b.last;
+      replayed += (unsigned)liveA + (unsigned)liveB;
+      Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
+      Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+      mask_pair(qa, liveA);
+      mask_pair(qb, liveB);
       const bool contrib = qa.hit || qb.hit;
       const unsigned ballot = __ballot_sync(0xffffffffu, contrib);
       if (ballot == 0u) continue;
@@ -580,8 +582,8 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
 #pragma unroll
       for (int i = 0; i < kN; ++i) v[i] = 0.f;
       const float4 e3 = s3[kk];
-      if (qa.hit) bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
-      if (qb.hit) bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
+      bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
+      bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
       if (__popc(ballot) == 1) {
         if (contrib) {
 #pragma unroll

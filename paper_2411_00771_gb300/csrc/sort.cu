@@ -57,9 +57,53 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
   return r;
 }
 
+// Last-block election: every block calls this once, after its writes to
+// global memory.  Returns true in the block that arrives last, to which all
+// blocks' writes are then visible (it reads them through L2).  atomicInc
+// wraps the counter back to zero, so it is ready for the next launch.
+__device__ __forceinline__ bool last_block(uint32_t* done) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicInc(done, gridDim.x - 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// One block: exclusive scan of nb values in place; their sum to *total.
+__device__ void block_scan_inplace(uint32_t* __restrict__ v, int nb, uint32_t* __restrict__ total) {
+  __shared__ uint32_t tot;
+  uint32_t carry = 0;
+  for (int base = 0; base < nb; base += kThreads * kItems) {
+    // each thread owns kItems consecutive entries of this chunk
+    uint32_t x[kItems];
+    uint32_t s = 0;
+    const int t0 = base + threadIdx.x * kItems;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      x[i] = (t0 + i < nb) ? __ldcg(v + t0 + i) : 0u;
+      s += x[i];
+    }
+    uint32_t pre = block_excl_scan(s, &tot) + carry;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      if (t0 + i < nb) v[t0 + i] = pre;
+      pre += x[i];
+    }
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// Block sums of the input; the last block scans them (exclusive, in place)
+// and writes the grand total.
 __global__ void __launch_bounds__(kThreads) scan_reduce(const uint32_t* __restrict__ in, int64_t n_max,
                                                         const uint32_t* __restrict__ n_dev,
-                                                        uint32_t* __restrict__ sums) {
+                                                        uint32_t* __restrict__ sums,
+                                                        uint32_t* __restrict__ total,
+                                                        uint32_t* __restrict__ done) {
   const int64_t n = item_count(n_max, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kTileItems;
   uint32_t s = 0;
@@ -70,33 +114,8 @@ __global__ void __launch_bounds__(kThreads) scan_reduce(const uint32_t* __restri
   __shared__ uint32_t tot;
   block_excl_scan(s, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
-
-// Single block: exclusive scan of nb block sums in place; total to *total.
-__global__ void __launch_bounds__(kThreads) scan_sums(uint32_t* __restrict__ sums, int nb,
-                                                      uint32_t* __restrict__ total) {
-  __shared__ uint32_t tot;
-  uint32_t carry = 0;
-  for (int base = 0; base < nb; base += kThreads * kItems) {
-    // each thread owns kItems consecutive entries of this chunk
-    uint32_t v[kItems];
-    uint32_t s = 0;
-    const int t0 = base + threadIdx.x * kItems;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      v[i] = (t0 + i < nb) ? sums[t0 + i] : 0u;
-      s += v[i];
-    }
-    uint32_t pre = block_excl_scan(s, &tot) + carry;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      if (t0 + i < nb) sums[t0 + i] = pre;
-      pre += v[i];
-    }
-    carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && total) *total = carry;
+  if (!last_block(done)) return;
+  block_scan_inplace(sums, (int)gridDim.x, total);
 }
 
 __global__ void __launch_bounds__(kThreads) scan_down(const uint32_t* __restrict__ in,
@@ -139,7 +158,9 @@ __global__ void __launch_bounds__(kThreads) scan_down(const uint32_t* __restrict
 __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __restrict__ keys,
                                                           int64_t n_max, const uint32_t* __restrict__ n_dev,
                                                           int shift, int nbins,
-                                                          uint32_t* __restrict__ hist) {
+                                                          uint32_t* __restrict__ hist,
+                                                          uint32_t* __restrict__ dbase,
+                                                          uint32_t* __restrict__ done) {
   const int64_t n = item_count(n_max, n_dev);
   __shared__ uint32_t h[kBins];
   for (int i = threadIdx.x; i < kBins; i += kThreads) h[i] = 0u;
@@ -156,13 +177,36 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __rest
     if (valid && lane == (31 - __clz(peers))) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < nbins; d += kThreads) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
+  for (int d = threadIdx.x; d < nbins; d += kThreads) hist[(int64_t)blockIdx.x * kBins + d] = h[d];
+  if (!last_block(done)) return;
+  // last block: per digit, the exclusive prefix over blocks (in place), and
+  // the digit bases (exclusive scan of the digit totals)
+  static_assert(kThreads == kBins, "one thread per digit");
+  const int d = threadIdx.x;
+  const int nb = (int)gridDim.x;
+  uint32_t run = 0;
+  if (d < nbins) {
+    constexpr int U = 32;  // loads in flight per thread
+    for (int b0 = 0; b0 < nb; b0 += U) {
+      uint32_t v[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) v[i] = (b0 + i < nb) ? __ldcg(hist + (int64_t)(b0 + i) * kBins + d) : 0u;
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        if (b0 + i < nb) hist[(int64_t)(b0 + i) * kBins + d] = run;
+        run += v[i];
+      }
+    }
+  }
+  __shared__ uint32_t tot;
+  const uint32_t db = block_excl_scan(run, &tot);
+  if (d < nbins) dbase[d] = db;
 }
 
 __global__ void __launch_bounds__(kThreads) radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n_max, const uint32_t* __restrict__ n_dev, int shift, int nbins,
-    const uint32_t* __restrict__ offs) {
+    const uint32_t* __restrict__ offs, const uint32_t* __restrict__ dbase) {
   const int64_t n = item_count(n_max, n_dev);
   __shared__ uint32_t wh[kWarps][kBins];
   for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) (&wh[0][0])[i] = 0u;
@@ -189,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
   }
   __syncthreads();
   for (int d = threadIdx.x; d < nbins; d += kThreads) {
-    uint32_t run = offs[(int64_t)d * gridDim.x + blockIdx.x];
+    uint32_t run = dbase[d] + offs[(int64_t)blockIdx.x * kBins + d];
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
       const uint32_t t = wh[ww][d];
@@ -253,7 +297,8 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t K, int2
 
 }  // namespace
 
-size_t scan_tmp_words(int64_t n) { return (size_t)div_up(n > 0 ? n : 1, kTileItems) + 1; }
+// block sums, then the last-block counter
+size_t scan_tmp_words(int64_t n) { return (size_t)div_up(n > 0 ? n : 1, kTileItems) + 2; }
 
 cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
                         uint32_t* tmp, cudaStream_t st, const uint32_t* n_dev) {
@@ -261,18 +306,20 @@ cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
     return total_dev ? cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), st) : cudaSuccess;
   }
   const unsigned nb = div_up(n, kTileItems);
+  uint32_t* done = tmp + nb + 1;
   ProfScope ps(kProfSort, st);
-  count_launch(3);
-  scan_reduce<<<nb, kThreads, 0, st>>>(in, n, n_dev, tmp);
-  scan_sums<<<1, kThreads, 0, st>>>(tmp, (int)nb, total_dev);
+  cudaError_t e = cudaMemsetAsync(done, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  count_launch(2);
+  scan_reduce<<<nb, kThreads, 0, st>>>(in, n, n_dev, tmp, total_dev, done);
   scan_down<<<nb, kThreads, 0, st>>>(in, out, n, n_dev, tmp);
   return cudaGetLastError();
 }
 
+// block-major histogram (kBins words per block), digit bases, counter
 size_t radix_tmp_words(int64_t n) {
   const size_t nb = div_up(n > 0 ? n : 1, kTileItems);
-  const size_t h = nb * kBins;
-  return 2 * h + scan_tmp_words((int64_t)h) + 1;
+  return nb * kBins + kBins + 2;
 }
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
@@ -284,19 +331,18 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
   if (n <= 1 || bits <= 0) return cudaSuccess;
   ProfScope ps(kProfSort, st);
   const unsigned nb = div_up(n, kTileItems);
-  const size_t h = (size_t)nb * kBins;
   uint32_t* hist = tmp;
-  uint32_t* offs = tmp + h;
-  uint32_t* stmp = tmp + 2 * h;
+  uint32_t* dbase = tmp + (size_t)nb * kBins;
+  uint32_t* done = dbase + kBins;
+  cudaError_t e = cudaMemsetAsync(done, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   for (int shift = 0; shift < bits; shift += kRadixBits) {
     const int pb = bits - shift < kRadixBits ? bits - shift : kRadixBits;
     const int nbins = 1 << pb;
     count_launch(2);
-    radix_upsweep<<<nb, kThreads, 0, st>>>(ki, n, n_dev, shift, nbins, hist);
-    cudaError_t e = launch_scan(hist, offs, (int64_t)nbins * nb, nullptr, stmp, st, nullptr);
-    if (e != cudaSuccess) return e;
-    radix_downsweep<<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, nbins, offs);
+    radix_upsweep<<<nb, kThreads, 0, st>>>(ki, n, n_dev, shift, nbins, hist, dbase, done);
+    radix_downsweep<<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, nbins, hist, dbase);
     uint32_t* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
   }
