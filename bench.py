@@ -118,6 +118,13 @@ def gpu_uuid(dev):
 
 
 # ---------------------------------------------------------------------------
+def workload_config(W: int, H: int, views: int) -> dict:
+    """The config object of the JSON line (the same for both arms)."""
+    return {"workload": f"aerial city block, 1M surfels SH3, {W}x{H}, fwd+bwd+loss+densify",
+            "surfels": N_SURFELS, "width": W, "height": H, "sh_degree": 3, "views_per_step": views,
+            "l2": "inputs larger than L2 (232 MB surfel parameters, 69 MB render planes per view)"}
+
+
 def city_workload(rank: int, width: int = 1600, height: int = 900):
     from paper_2411_00771_gb300 import synthetic as syn
     scene, info = syn.city_scene(n=N_SURFELS)
@@ -267,10 +274,7 @@ def run_ours(args):
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": round(ms_step_max, 4), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"aerial city block, 1M surfels SH3, {W}x{H}, fwd+bwd+loss+densify",
-                       "surfels": n, "width": W, "height": H, "sh_degree": 3,
-                       "views_per_step": world, "l2": "inputs larger than L2 (232 MB surfel "
-                       "parameters, 69 MB render planes per view)"},
+            "config": workload_config(W, H, world),
             "e2e": {"value": round(e2e_ms / world, 4), "unit": UNIT,
                     "h2d_bytes_per_step": int(tgt_h.numel() * 4 + tinv_h.numel() * 4) * world,
                     "d2h_bytes_per_step": int(16 + n) * world},
@@ -480,8 +484,7 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": round(v, 1), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"aerial city block, 1M surfels SH3, {W}x{H}, fwd+bwd+loss+densify",
-                       "surfels": N_SURFELS, "width": cam["width"], "height": H},
+            "config": workload_config(cam["width"], H, world),
             "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
