@@ -206,6 +206,8 @@ struct gs_frame {
   int2* ranges = nullptr;
   int32_t* last = nullptr;
   int32_t* med = nullptr;
+  uint32_t* cand = nullptr;   // candidate surfels of the render (index order)
+  uint32_t* ncand = nullptr;  // their count (device; in counters[6])
   unsigned long long* counters = nullptr;  // evaluated, blended, bwd replayed, visible
   const float* out = nullptr;
 };
@@ -328,14 +330,7 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   f->out = out;
   f->buf.al = &sc->al;
   CamDev& cam = f->cam;
-  for (int i = 0; i < 9; ++i) cam.R[i] = c->R[i];
-  for (int i = 0; i < 3; ++i) cam.t[i] = c->t[i];
-  cam.fx = c->fx; cam.fy = c->fy; cam.cx = c->cx; cam.cy = c->cy;
-  for (int i = 0; i < 3; ++i)
-    cam.campos[i] = -(c->R[i] * c->t[0] + c->R[3 + i] * c->t[1] + c->R[6 + i] * c->t[2]);
-  cam.W = c->width; cam.H = c->height;
-  cam.tiles_x = (cam.W + kTile - 1) / kTile;
-  cam.tiles_y = (cam.H + kTile - 1) / kTile;
+  cam_from(*c, cam);
   const int ntiles = cam.tiles_x * cam.tiles_y;
   const int64_t n = f->n;
   const SetDev set = to_dev(sc->settings);
@@ -361,7 +356,8 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   uint32_t* cnts = tmp.get<uint32_t>(n > 0 ? n : 1, st);
   uint32_t* offs = tmp.get<uint32_t>(n > 0 ? n : 1, st);
   uint32_t* rtmp = tmp.get<uint32_t>(radix_tmp_words(n) + scan_tmp_words(n) + 4, st);
-  uint32_t* cand = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* cand = f->buf.get<uint32_t>(n > 0 ? n : 1, st);
+  f->cand = cand;
   RowGeom* geom = f->buf.get<RowGeom>(n > 0 ? n : 1, st);
   f->geom = geom;
   if (!f->rec || !f->rect || !f->tcount || !f->ranges || !f->last || !f->med || !f->counters || !dkey ||
@@ -376,7 +372,8 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   } while (0)
   GS_CKC(cudaMemsetAsync(f->counters, 0, 8 * sizeof(unsigned long long), st));
   // candidates (possibly visible surfels) in index order; only they are sorted
-  uint32_t* ncand = total + 1;
+  uint32_t* ncand = reinterpret_cast<uint32_t*>(f->counters + 6);
+  f->ncand = ncand;
   GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, cand, ncand, geom,
                            cnts, rtmp + radix_tmp_words(n), st));
   uint32_t *skey = dkey, *sidx = idx;
@@ -500,7 +497,7 @@ gs_status gs_backward(gs_scene* sc, gs_frame* f, const float* const* adj_sets,
   if (e == cudaSuccess)
     e = launch_blend_bwd(f->cam, set, f->rec, f->geom, f->vals, f->ranges, f->out, f->last, f->med, adj,
                          grec, screen_grads, n, f->counters, st);
-  if (e == cudaSuccess) e = launch_preprocess_bwd(sc->P, f->cam, f->tcount, grec, *grads, st);
+  if (e == cudaSuccess) e = launch_preprocess_bwd(sc->P, f->cam, f->cand, f->ncand, f->tcount, grec, *grads, st);
   sc->al.put(grec, sizeof(float) * kGradRec * (size_t)(n > 0 ? n : 1), st);
   if (e != cudaSuccess) return cuda_fail(e, "gs_backward");
   return GS_OK;

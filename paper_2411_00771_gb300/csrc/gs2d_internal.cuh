@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "../../include/gs2d.h"
@@ -19,7 +20,27 @@ struct CamDev {
   double fx, fy, cx, cy;
   double campos[3];  // camera centre in world coordinates, -R^T t
   int W, H, tiles_x, tiles_y;
+  // FP32 copies for the FP32 kernels (converting doubles per use is slow)
+  float Rf[9], tf[3], camposf[3];
+  float fxf, fyf, cxf, cyf;
+  float tabs;  // |t_x| + |t_y| + |t_z|
 };
+
+// Fill a CamDev from a camera (everything derived is computed here, once).
+inline void cam_from(const gs_camera& c, CamDev& cam) {
+  for (int i = 0; i < 9; ++i) cam.R[i] = c.R[i];
+  for (int i = 0; i < 3; ++i) cam.t[i] = c.t[i];
+  cam.fx = c.fx; cam.fy = c.fy; cam.cx = c.cx; cam.cy = c.cy;
+  for (int i = 0; i < 3; ++i) cam.campos[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
+  cam.W = c.width; cam.H = c.height;
+  cam.tiles_x = (c.width + 15) / 16;
+  cam.tiles_y = (c.height + 15) / 16;
+  for (int i = 0; i < 9; ++i) cam.Rf[i] = (float)c.R[i];
+  for (int i = 0; i < 3; ++i) cam.tf[i] = (float)c.t[i];
+  for (int i = 0; i < 3; ++i) cam.camposf[i] = (float)cam.campos[i];
+  cam.fxf = (float)c.fx; cam.fyf = (float)c.fy; cam.cxf = (float)c.cx; cam.cyf = (float)c.cy;
+  cam.tabs = (float)(fabs(c.t[0]) + fabs(c.t[1]) + fabs(c.t[2]));
+}
 
 struct SetDev {
   float near_plane, alpha_min, T_min, alpha_max, rho_max, sinv;
@@ -200,8 +221,9 @@ cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const float4*
                              float* grec, float* screen, int n, unsigned long long* counters,
                              cudaStream_t st);
 
-cudaError_t launch_preprocess_bwd(const ParamsDev& P, const CamDev& cam, const uint32_t* tcount,
-                                  const float* grec, const gs_param_grads& G, cudaStream_t st);
+cudaError_t launch_preprocess_bwd(const ParamsDev& P, const CamDev& cam, const uint32_t* cand,
+                                  const uint32_t* ncand, const uint32_t* tcount, const float* grec,
+                                  const gs_param_grads& G, cudaStream_t st);
 
 cudaError_t launch_loss(int W, int H, const float* out, const float* tgt, const float* tinv,
                         const gs_loss_weights& w, float* adj_total, float* adj_ssim,

@@ -96,17 +96,19 @@ __device__ __forceinline__ void quat_cols(T w, T x, T y, T z, V3<T>& r1, V3<T>& 
   r3 = {T(2) * (x * z + w * y), T(2) * (y * z - w * x), T(1) - T(2) * (x * x + y * y)};
 }
 
+// R v and R^T v; R in the precision of v (FP32 kernels take the camera's
+// FP32 copy).
 template <typename T>
-__device__ __forceinline__ V3<T> rot(const double* R, V3<T> v) {
-  return {T(R[0]) * v.x + T(R[1]) * v.y + T(R[2]) * v.z,
-          T(R[3]) * v.x + T(R[4]) * v.y + T(R[5]) * v.z,
-          T(R[6]) * v.x + T(R[7]) * v.y + T(R[8]) * v.z};
+__device__ __forceinline__ V3<T> rot(const T* R, V3<T> v) {
+  return {R[0] * v.x + R[1] * v.y + R[2] * v.z,
+          R[3] * v.x + R[4] * v.y + R[5] * v.z,
+          R[6] * v.x + R[7] * v.y + R[8] * v.z};
 }
 template <typename T>
-__device__ __forceinline__ V3<T> rotT(const double* R, V3<T> v) {
-  return {T(R[0]) * v.x + T(R[3]) * v.y + T(R[6]) * v.z,
-          T(R[1]) * v.x + T(R[4]) * v.y + T(R[7]) * v.z,
-          T(R[2]) * v.x + T(R[5]) * v.y + T(R[8]) * v.z};
+__device__ __forceinline__ V3<T> rotT(const T* R, V3<T> v) {
+  return {R[0] * v.x + R[3] * v.y + R[6] * v.z,
+          R[1] * v.x + R[4] * v.y + R[7] * v.z,
+          R[2] * v.x + R[5] * v.y + R[8] * v.z};
 }
 
 // Stage 1 (FP32, every surfel): defaults for the sort inputs and a
@@ -156,22 +158,21 @@ __global__ void __launch_bounds__(256) preprocess_cull_kernel(ParamsDev P, CamDe
     const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
     const double qn2 = (double)qw * qw + (double)qx * qx + (double)qy * qy + (double)qz * qz;
     const V3<float> mu = {P.mu[3 * n], P.mu[3 * n + 1], P.mu[3 * n + 2]};
-    V3<float> p = rot<float>(cam.R, mu);
-    p.x += (float)cam.t[0]; p.y += (float)cam.t[1]; p.z += (float)cam.t[2];
+    V3<float> p = rot<float>(cam.Rf, mu);
+    p.x += cam.tf[0]; p.y += cam.tf[1]; p.z += cam.tf[2];
     const float R = 3.0f * fmaxf(P.scale[2 * n], P.scale[2 * n + 1]) * sqrtf(set.rho_max / 9.0f);
     // FP32 error of p is far below this margin (a few ulp of |mu| + |t|)
-    const float eps = 1e-4f * (fabsf(mu.x) + fabsf(mu.y) + fabsf(mu.z) + (float)(fabs(cam.t[0]) +
-                      fabs(cam.t[1]) + fabs(cam.t[2])) + 1.0f) + 1e-3f * R;
+    const float eps = 1e-4f * (fabsf(mu.x) + fabsf(mu.y) + fabsf(mu.z) + cam.tabs + 1.0f) + 1e-3f * R;
     keep = qn2 > 0.0 && p.z + R + eps > set.near_plane;
     const float zlo = p.z - R - eps, zhi = p.z + R + eps;
     if (keep && zlo > 0.f) {
       const float rpix = sqrtf(set.rho_max / set.sinv) + 1.0f;
-      const float fx = (float)cam.fx, fy = (float)cam.fy;
+      const float fx = cam.fxf, fy = cam.fyf;
       const float xa = p.x - R - eps, xb = p.x + R + eps, ya = p.y - R - eps, yb = p.y + R + eps;
-      const float sx0 = fx * (xa < 0.f ? xa / zlo : xa / zhi) + (float)cam.cx - rpix;
-      const float sx1 = fx * (xb > 0.f ? xb / zlo : xb / zhi) + (float)cam.cx + rpix;
-      const float sy0 = fy * (ya < 0.f ? ya / zlo : ya / zhi) + (float)cam.cy - rpix;
-      const float sy1 = fy * (yb > 0.f ? yb / zlo : yb / zhi) + (float)cam.cy + rpix;
+      const float sx0 = fx * (xa < 0.f ? xa / zlo : xa / zhi) + cam.cxf - rpix;
+      const float sx1 = fx * (xb > 0.f ? xb / zlo : xb / zhi) + cam.cxf + rpix;
+      const float sy0 = fy * (ya < 0.f ? ya / zlo : ya / zhi) + cam.cyf - rpix;
+      const float sy1 = fy * (yb > 0.f ? yb / zlo : yb / zhi) + cam.cyf + rpix;
       const float m = 1e-3f * (fabsf(sx0) + fabsf(sx1) + fabsf(sy0) + fabsf(sy1)) + 1.0f;
       keep = !(sx1 < -m || sx0 > (float)cam.W + m || sy1 < -m || sy0 > (float)cam.H + m);
     }
@@ -326,18 +327,19 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
 // ---------------------------------------------------------------------------
 // Backward.
 
-template <int DEG>
-__global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev cam,
-                                                             const uint32_t* __restrict__ tcount,
-                                                             const float* __restrict__ grec,
-                                                             gs_param_grads G) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= P.n || tcount[n] == 0) return;
-  const float* g = grec + (size_t)n * kGradRec;
-  float gJi11 = g[0], gJi12 = g[1], gJi21 = g[2], gJi22 = g[3];
-  const float ge1 = g[4], ge2 = g[5], gcx = g[6], gcy = g[7], gpz0 = g[8], gop = g[9];
-  const float grgb[3] = {g[10], g[11], g[12]};
-  const V3<float> gnrm = {g[13], g[14], g[15]};
+// Gradient of one visible surfel n: chain the per-surfel record (d Ji, d e,
+// d c, d p_z, d opacity, d rgb, d normal) back to mu, q, s, o and SH,
+// accumulated into G.  kVec: SH rows and gradient rows are float4-aligned.
+template <int DEG, bool kVec>
+__device__ __forceinline__ void bwd_one(const ParamsDev& P, const CamDev& cam, int n,
+                                        const float* __restrict__ grec, const gs_param_grads& G) {
+  static_assert(kGradRec == 16, "gradient record of four float4");
+  const float4* g4 = reinterpret_cast<const float4*>(grec + (size_t)n * kGradRec);
+  const float4 ga4 = g4[0], gb4 = g4[1], gc4 = g4[2], gd4 = g4[3];
+  float gJi11 = ga4.x, gJi12 = ga4.y, gJi21 = ga4.z, gJi22 = ga4.w;
+  const float ge1 = gb4.x, ge2 = gb4.y, gcx = gb4.z, gcy = gb4.w, gpz0 = gc4.x, gop = gc4.y;
+  const float grgb[3] = {gc4.z, gc4.w, gd4.x};
+  const V3<float> gnrm = {gd4.y, gd4.z, gd4.w};
   // forward intermediates, FP32
   const float qw0 = P.quat[4 * n], qx0 = P.quat[4 * n + 1], qy0 = P.quat[4 * n + 2], qz0 = P.quat[4 * n + 3];
   const float qn = sqrtf(qw0 * qw0 + qx0 * qx0 + qy0 * qy0 + qz0 * qz0);
@@ -346,12 +348,12 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev
   V3<float> r1, r2, r3;
   quat_cols<float>(qw, qx, qy, qz, r1, r2, r3);
   const V3<float> mu = {P.mu[3 * n], P.mu[3 * n + 1], P.mu[3 * n + 2]};
-  V3<float> p = rot<float>(cam.R, mu);
-  p.x += (float)cam.t[0]; p.y += (float)cam.t[1]; p.z += (float)cam.t[2];
-  const V3<float> tu = rot<float>(cam.R, r1), tv = rot<float>(cam.R, r2), nv = rot<float>(cam.R, r3);
+  V3<float> p = rot<float>(cam.Rf, mu);
+  p.x += cam.tf[0]; p.y += cam.tf[1]; p.z += cam.tf[2];
+  const V3<float> tu = rot<float>(cam.Rf, r1), tv = rot<float>(cam.Rf, r2), nv = rot<float>(cam.Rf, r3);
   const float su = P.scale[2 * n], sv = P.scale[2 * n + 1];
   const V3<float> a = {su * tu.x, su * tu.y, su * tu.z}, b = {sv * tv.x, sv * tv.y, sv * tv.z};
-  const float fx = (float)cam.fx, fy = (float)cam.fy;
+  const float fx = cam.fxf, fy = cam.fyf;
   const float iz = 1.f / p.z;
   const float xi = p.x * iz, yi = p.y * iz;
   const float J11 = fx * (a.x - a.z * xi) * iz, J12 = fx * (b.x - b.z * xi) * iz;
@@ -381,15 +383,15 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev
   const float gyi = -fy * (a.z * gJ21 + b.z * gJ22) * iz + fy * gcy;
   float gpz = gpz0 - (J11 * gJ11 + J12 * gJ12 + J21 * gJ21 + J22 * gJ22) * iz - (w1 * gw1 + w2 * gw2) * iz;
   const V3<float> gp = {gxi * iz, gyi * iz, gpz - (xi * gxi + yi * gyi) * iz};
-  V3<float> gmu = rotT<float>(cam.R, gp);
+  V3<float> gmu = rotT<float>(cam.Rf, gp);
   const float gsu = ga.x * tu.x + ga.y * tu.y + ga.z * tu.z;
   const float gsv = gb.x * tv.x + gb.y * tv.y + gb.z * tv.z;
-  const V3<float> gr1 = rotT<float>(cam.R, V3<float>{su * ga.x, su * ga.y, su * ga.z});
-  const V3<float> gr2 = rotT<float>(cam.R, V3<float>{sv * gb.x, sv * gb.y, sv * gb.z});
+  const V3<float> gr1 = rotT<float>(cam.Rf, V3<float>{su * ga.x, su * ga.y, su * ga.z});
+  const V3<float> gr2 = rotT<float>(cam.Rf, V3<float>{sv * gb.x, sv * gb.y, sv * gb.z});
   const float sgn = (nv.x * p.x + nv.y * p.y + nv.z * p.z) > 0.f ? -1.f : 1.f;
-  const V3<float> gr3 = rotT<float>(cam.R, V3<float>{sgn * gnrm.x, sgn * gnrm.y, sgn * gnrm.z});
+  const V3<float> gr3 = rotT<float>(cam.Rf, V3<float>{sgn * gnrm.x, sgn * gnrm.y, sgn * gnrm.z});
   // colour
-  const V3<float> dd = {mu.x - (float)cam.campos[0], mu.y - (float)cam.campos[1], mu.z - (float)cam.campos[2]};
+  const V3<float> dd = {mu.x - cam.camposf[0], mu.y - cam.camposf[1], mu.z - cam.camposf[2]};
   const float dl = sqrtf(dd.x * dd.x + dd.y * dd.y + dd.z * dd.z);
   const float il = 1.f / dl;
   const float dx = dd.x * il, dy = dd.y * il, dz = dd.z * il;
@@ -400,8 +402,16 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev
   sh_basis_grad(dx, dy, dz, DEG, dY);
   const float* f = P.sh + (size_t)n * K * 3;
   float fv[K * 3];
+  if constexpr (kVec) {
 #pragma unroll
-  for (int i = 0; i < K * 3; ++i) fv[i] = f[i];
+    for (int i = 0; i < K * 3 / 4; ++i) {
+      const float4 x = reinterpret_cast<const float4*>(f)[i];
+      fv[4 * i] = x.x; fv[4 * i + 1] = x.y; fv[4 * i + 2] = x.z; fv[4 * i + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < K * 3; ++i) fv[i] = f[i];
+  }
   float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < K; ++k)
@@ -420,11 +430,25 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev
   }
   if (G.sh) {
     float* gs = G.sh + (size_t)n * K * 3;
+    if constexpr (kVec) {
+      // element j of the row is (basis j / 3, channel j % 3)
 #pragma unroll
-    for (int k = 0; k < K; ++k)
+      for (int i = 0; i < K * 3 / 4; ++i) {
+        float4* q4 = reinterpret_cast<float4*>(gs) + i;
+        float4 x = *q4;
+        x.x += gc[(4 * i) % 3] * Y[(4 * i) / 3];
+        x.y += gc[(4 * i + 1) % 3] * Y[(4 * i + 1) / 3];
+        x.z += gc[(4 * i + 2) % 3] * Y[(4 * i + 2) / 3];
+        x.w += gc[(4 * i + 3) % 3] * Y[(4 * i + 3) / 3];
+        *q4 = x;
+      }
+    } else {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (gc[c] != 0.f) gs[k * 3 + c] += gc[c] * Y[k];
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (gc[c] != 0.f) gs[k * 3 + c] += gc[c] * Y[k];
+    }
   }
   const float gdd = dx * gdir.x + dy * gdir.y + dz * gdir.z;
   gmu.x += (gdir.x - dx * gdd) * il;
@@ -460,6 +484,38 @@ __global__ void __launch_bounds__(256) preprocess_bwd_kernel(ParamsDev P, CamDev
   if (G.opacity) G.opacity[n] += gop;
 }
 
+// Over the render's candidates (a grid-stride loop over the device-side
+// count); surfels with no tile contribute nothing.
+template <int DEG, bool kVec>
+__global__ void __launch_bounds__(256, 2) preprocess_bwd_kernel(ParamsDev P, CamDev cam,
+                                                             const uint32_t* __restrict__ cand,
+                                                             const uint32_t* __restrict__ ncand,
+                                                             const uint32_t* __restrict__ tcount,
+                                                             const float* __restrict__ grec,
+                                                             gs_param_grads G) {
+  const int nc = (int)*ncand;
+  for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < nc; ci += gridDim.x * blockDim.x) {
+    const int n = (int)cand[ci];
+    if (tcount[n] == 0u) continue;
+    bwd_one<DEG, kVec>(P, cam, n, grec, G);
+  }
+}
+
+template <int DEG>
+void launch_bwd_deg(const ParamsDev& P, const CamDev& cam, const uint32_t* cand, const uint32_t* ncand,
+                    const uint32_t* tcount, const float* grec, const gs_param_grads& G, unsigned blocks,
+                    cudaStream_t st) {
+  constexpr int K3 = (DEG + 1) * (DEG + 1) * 3;
+  const bool vec = K3 % 4 == 0 && ((uintptr_t)P.sh % 16u) == 0 && ((uintptr_t)G.sh % 16u) == 0;
+  if constexpr (K3 % 4 == 0) {
+    if (vec) {
+      preprocess_bwd_kernel<DEG, true><<<blocks, 256, 0, st>>>(P, cam, cand, ncand, tcount, grec, G);
+      return;
+    }
+  }
+  preprocess_bwd_kernel<DEG, false><<<blocks, 256, 0, st>>>(P, cam, cand, ncand, tcount, grec, G);
+}
+
 }  // namespace
 
 cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
@@ -488,16 +544,19 @@ cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDe
   return cudaGetLastError();
 }
 
-cudaError_t launch_preprocess_bwd(const ParamsDev& P, const CamDev& cam, const uint32_t* tcount,
-                                  const float* grec, const gs_param_grads& G, cudaStream_t st) {
+cudaError_t launch_preprocess_bwd(const ParamsDev& P, const CamDev& cam, const uint32_t* cand,
+                                  const uint32_t* ncand, const uint32_t* tcount, const float* grec,
+                                  const gs_param_grads& G, cudaStream_t st) {
   if (P.n == 0) return cudaSuccess;
   ProfScope ps(kProfPreprocessBwd, st);
-  const unsigned blocks = div_up(P.n, 256);
+  // candidates are a subset of the surfels: a grid-stride loop over the
+  // device-side count, two CTAs per SM
+  const unsigned blocks = div_up(P.n, 256) < 304u ? div_up(P.n, 256) : 304u;
   switch (P.sh_degree) {
-    case 0: preprocess_bwd_kernel<0><<<blocks, 256, 0, st>>>(P, cam, tcount, grec, G); break;
-    case 1: preprocess_bwd_kernel<1><<<blocks, 256, 0, st>>>(P, cam, tcount, grec, G); break;
-    case 2: preprocess_bwd_kernel<2><<<blocks, 256, 0, st>>>(P, cam, tcount, grec, G); break;
-    default: preprocess_bwd_kernel<3><<<blocks, 256, 0, st>>>(P, cam, tcount, grec, G); break;
+    case 0: launch_bwd_deg<0>(P, cam, cand, ncand, tcount, grec, G, blocks, st); break;
+    case 1: launch_bwd_deg<1>(P, cam, cand, ncand, tcount, grec, G, blocks, st); break;
+    case 2: launch_bwd_deg<2>(P, cam, cand, ncand, tcount, grec, G, blocks, st); break;
+    default: launch_bwd_deg<3>(P, cam, cand, ncand, tcount, grec, G, blocks, st); break;
   }
   count_launch();
   return cudaGetLastError();

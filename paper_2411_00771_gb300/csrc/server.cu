@@ -483,14 +483,7 @@ void worker_loop(gs_server* s) {
         for (int c = 0; c < 3; ++c) sl.set.bg[c] = g.bg[c];
         sl.rf = (float)sqrt((double)g.rho_max / (double)g.screen_inv_sigma2);
         const gs_camera& c = t->req.camera;
-        for (int i = 0; i < 9; ++i) sl.cam.R[i] = c.R[i];
-        for (int i = 0; i < 3; ++i) sl.cam.t[i] = c.t[i];
-        sl.cam.fx = c.fx; sl.cam.fy = c.fy; sl.cam.cx = c.cx; sl.cam.cy = c.cy;
-        for (int i = 0; i < 3; ++i)
-          sl.cam.campos[i] = -(c.R[i] * c.t[0] + c.R[3 + i] * c.t[1] + c.R[6 + i] * c.t[2]);
-        sl.cam.W = c.width; sl.cam.H = c.height;
-        sl.cam.tiles_x = (c.width + kTile - 1) / kTile;
-        sl.cam.tiles_y = (c.height + kTile - 1) / kTile;
+        cam_from(c, sl.cam);
         std::string msg;
         const gs_status r = stage_a(s, sl, &msg);
         if (r != GS_OK) finish(s, sl, r, msg);

@@ -158,9 +158,7 @@ __global__ void __launch_bounds__(kThreads) scan_down(const uint32_t* __restrict
 __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __restrict__ keys,
                                                           int64_t n_max, const uint32_t* __restrict__ n_dev,
                                                           int shift, int nbins,
-                                                          uint32_t* __restrict__ hist,
-                                                          uint32_t* __restrict__ dbase,
-                                                          uint32_t* __restrict__ done) {
+                                                          uint32_t* __restrict__ hist) {
   const int64_t n = item_count(n_max, n_dev);
   __shared__ uint32_t h[kBins];
   for (int i = threadIdx.x; i < kBins; i += kThreads) h[i] = 0u;
@@ -168,47 +166,59 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __rest
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t base = (int64_t)blockIdx.x * kTileItems + w * (32 * kItems);
   const uint32_t mask = (uint32_t)nbins - 1u;
-#pragma unroll 4
+  uint32_t kk[kItems];
+#pragma unroll
+  for (int it = 0; it < kItems; ++it) {
+    const int64_t k = base + it * 32 + lane;
+    kk[it] = k < n ? keys[k] : 0u;
+  }
+#pragma unroll
   for (int it = 0; it < kItems; ++it) {
     const int64_t k = base + it * 32 + lane;
     const bool valid = k < n;
-    const uint32_t d = valid ? ((keys[k] >> shift) & mask) : 0x100u;
+    const uint32_t d = valid ? ((kk[it] >> shift) & mask) : 0x100u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     if (valid && lane == (31 - __clz(peers))) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
   for (int d = threadIdx.x; d < nbins; d += kThreads) hist[(int64_t)blockIdx.x * kBins + d] = h[d];
-  if (!last_block(done)) return;
-  // last block: per digit, the exclusive prefix over blocks (in place), and
-  // the digit bases (exclusive scan of the digit totals)
-  static_assert(kThreads == kBins, "one thread per digit");
-  const int d = threadIdx.x;
-  const int nb = (int)gridDim.x;
-  uint32_t run = 0;
-  if (d < nbins) {
-    constexpr int U = 32;  // loads in flight per thread
-    for (int b0 = 0; b0 < nb; b0 += U) {
-      uint32_t v[U];
-#pragma unroll
-      for (int i = 0; i < U; ++i) v[i] = (b0 + i < nb) ? __ldcg(hist + (int64_t)(b0 + i) * kBins + d) : 0u;
-#pragma unroll
-      for (int i = 0; i < U; ++i) {
-        if (b0 + i < nb) hist[(int64_t)(b0 + i) * kBins + d] = run;
-        run += v[i];
-      }
+}
+
+// Per digit d (one block each): exclusive prefix of the digit's per-block
+// counts over the blocks, in place, and the digit's total.
+__global__ void __launch_bounds__(kThreads) radix_offsets(uint32_t* __restrict__ hist, int nb,
+                                                          uint32_t* __restrict__ dtot) {
+  const int d = blockIdx.x;
+  const int per = (nb + kThreads - 1) / kThreads;
+  const int b0 = threadIdx.x * per;
+  uint32_t s = 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) s += hist[(int64_t)(b0 + i) * kBins + d];
+  __shared__ uint32_t tot;
+  uint32_t run = block_excl_scan(s, &tot);
+  for (int i = 0; i < per; ++i) {
+    if (b0 + i < nb) {
+      uint32_t* h = hist + (int64_t)(b0 + i) * kBins + d;
+      const uint32_t x = *h;
+      *h = run;
+      run += x;
     }
   }
-  __shared__ uint32_t tot;
-  const uint32_t db = block_excl_scan(run, &tot);
-  if (d < nbins) dbase[d] = db;
+  if (threadIdx.x == 0) dtot[d] = tot;
 }
 
 __global__ void __launch_bounds__(kThreads) radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n_max, const uint32_t* __restrict__ n_dev, int shift, int nbins,
-    const uint32_t* __restrict__ offs, const uint32_t* __restrict__ dbase) {
+    const uint32_t* __restrict__ offs, const uint32_t* __restrict__ dtot) {
   const int64_t n = item_count(n_max, n_dev);
   __shared__ uint32_t wh[kWarps][kBins];
+  __shared__ uint32_t dbase[kBins];
+  {
+    __shared__ uint32_t tot;
+    const uint32_t x = threadIdx.x < nbins ? dtot[threadIdx.x] : 0u;
+    dbase[threadIdx.x] = block_excl_scan(x, &tot);
+  }
   for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) (&wh[0][0])[i] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -316,10 +326,10 @@ cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
   return cudaGetLastError();
 }
 
-// block-major histogram (kBins words per block), digit bases, counter
+// block-major histogram (kBins words per block), then the digit totals
 size_t radix_tmp_words(int64_t n) {
   const size_t nb = div_up(n > 0 ? n : 1, kTileItems);
-  return nb * kBins + kBins + 2;
+  return nb * kBins + kBins;
 }
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
@@ -332,17 +342,15 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
   ProfScope ps(kProfSort, st);
   const unsigned nb = div_up(n, kTileItems);
   uint32_t* hist = tmp;
-  uint32_t* dbase = tmp + (size_t)nb * kBins;
-  uint32_t* done = dbase + kBins;
-  cudaError_t e = cudaMemsetAsync(done, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
+  uint32_t* dtot = tmp + (size_t)nb * kBins;
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   for (int shift = 0; shift < bits; shift += kRadixBits) {
     const int pb = bits - shift < kRadixBits ? bits - shift : kRadixBits;
     const int nbins = 1 << pb;
-    count_launch(2);
-    radix_upsweep<<<nb, kThreads, 0, st>>>(ki, n, n_dev, shift, nbins, hist, dbase, done);
-    radix_downsweep<<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, nbins, hist, dbase);
+    count_launch(3);
+    radix_upsweep<<<nb, kThreads, 0, st>>>(ki, n, n_dev, shift, nbins, hist);
+    radix_offsets<<<nbins, kThreads, 0, st>>>(hist, (int)nb, dtot);
+    radix_downsweep<<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, nbins, hist, dtot);
     uint32_t* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
   }
