@@ -204,6 +204,7 @@ struct gs_frame {
   uint32_t* tcount = nullptr;
   uint32_t* vals = nullptr;
   int2* ranges = nullptr;
+  uint32_t* order = nullptr;  // tiles by list length, longest first
   int32_t* last = nullptr;
   int32_t* med = nullptr;
   uint32_t* cand = nullptr;   // candidate surfels of the render (index order)
@@ -346,6 +347,7 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   f->rect = f->buf.get<uint2>(n > 0 ? n : 1, st);
   f->tcount = f->buf.get<uint32_t>(n > 0 ? n : 1, st);
   f->ranges = f->buf.get<int2>(ntiles, st);
+  f->order = f->buf.get<uint32_t>(ntiles, st);
   f->last = f->buf.get<int32_t>((size_t)cam.W * cam.H, st);
   f->med = f->buf.get<int32_t>((size_t)cam.W * cam.H, st);
   f->counters = f->buf.get<unsigned long long>(8, st);
@@ -360,7 +362,7 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   f->cand = cand;
   RowGeom* geom = f->buf.get<RowGeom>(n > 0 ? n : 1, st);
   f->geom = geom;
-  if (!f->rec || !f->rect || !f->tcount || !f->ranges || !f->last || !f->med || !f->counters || !dkey ||
+  if (!f->rec || !f->rect || !f->tcount || !f->ranges || !f->order || !f->last || !f->med || !f->counters || !dkey ||
       !idx || !dkey2 || !idx2 || !cnts || !offs || !rtmp || !cand || !geom)
     return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed"));
   uint32_t* total = rtmp + radix_tmp_words(n) + scan_tmp_words(n);
@@ -400,7 +402,9 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
   f->vals = tv;
   f->buf.release(tv == vals ? vals2 : vals, st);
   GS_CKC(launch_ranges(tk, K, f->ranges, ntiles, st));
-  GS_CKC(launch_blend_fwd(cam, set, f->rec, f->geom, f->vals, f->ranges, out, n_contrib, f->last,
+  if (tile_order_supported(ntiles)) GS_CKC(launch_tile_order(f->ranges, ntiles, f->order, st));
+  else f->order = nullptr;  // natural tile order (the buffer stays owned by f->buf)
+  GS_CKC(launch_blend_fwd(cam, set, f->order, f->rec, f->geom, f->vals, f->ranges, out, n_contrib, f->last,
                           f->med, f->counters, st));
 #undef GS_CKC
   tmp.release_all(st);
@@ -495,7 +499,7 @@ gs_status gs_backward(gs_scene* sc, gs_frame* f, const float* const* adj_sets,
   if (e == cudaSuccess) e = cudaMemsetAsync(f->counters + 2, 0, 3 * sizeof(unsigned long long), st);
   const SetDev set = to_dev(sc->settings);
   if (e == cudaSuccess)
-    e = launch_blend_bwd(f->cam, set, f->rec, f->geom, f->vals, f->ranges, f->out, f->last, f->med, adj,
+    e = launch_blend_bwd(f->cam, set, f->order, f->rec, f->geom, f->vals, f->ranges, f->out, f->last, f->med, adj,
                          grec, screen_grads, n, f->counters, st);
   if (e == cudaSuccess) e = launch_preprocess_bwd(sc->P, f->cam, f->cand, f->ncand, f->tcount, grec, *grads, st);
   sc->al.put(grec, sizeof(float) * kGradRec * (size_t)(n > 0 ? n : 1), st);

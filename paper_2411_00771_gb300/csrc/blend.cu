@@ -274,14 +274,16 @@ __device__ __forceinline__ void blend_fwd_tile(
   }
 }
 
+// One CTA per tile; block b takes tile order[b] (longest lists first).
 __global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
-    CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
-    const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, float* __restrict__ out,
-    int32_t* __restrict__ n_contrib, int32_t* __restrict__ last, int32_t* __restrict__ med,
-    unsigned long long* __restrict__ counters) {
+    CamDev cam, SetDev set, float rf, const uint32_t* __restrict__ order, const float4* __restrict__ rec,
+    const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
+    float* __restrict__ out, int32_t* __restrict__ n_contrib, int32_t* __restrict__ last,
+    int32_t* __restrict__ med, unsigned long long* __restrict__ counters) {
   __shared__ FwdSmem sh;
+  const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   blend_fwd_tile(sh, cam, set, rf, rec, geom, vals, ranges, out, n_contrib, last, med, counters,
-                 blockIdx.x, blockIdx.y);
+                 t % cam.tiles_x, t / cam.tiles_x);
 }
 
 // Persistent forward blend over the tiles of several views (serving): each
@@ -509,10 +511,10 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
 
 template <bool kLoss>
 __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
-    CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
-    const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, const float* __restrict__ out,
-    const int32_t* __restrict__ last, const int32_t* __restrict__ med, AdjDev adj,
-    float* __restrict__ grec, float* __restrict__ screen, int n,
+    CamDev cam, SetDev set, float rf, const uint32_t* __restrict__ order, const float4* __restrict__ rec,
+    const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
+    const float* __restrict__ out, const int32_t* __restrict__ last, const int32_t* __restrict__ med,
+    AdjDev adj, float* __restrict__ grec, float* __restrict__ screen, int n,
     unsigned long long* __restrict__ counters) {
   using LY = Layout<kLoss>;
   constexpr int kN = LY::kN;
@@ -521,8 +523,8 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
   __shared__ uint32_t sid[kBatch];
   __shared__ float acc[kBatch][kN + 1];
   __shared__ int smax;
-  const int tile = blockIdx.y * cam.tiles_x + blockIdx.x;
-  const int tx0 = blockIdx.x * kTile, ty0 = blockIdx.y * kTile;
+  const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+  const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
   const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
   const int warp = threadIdx.x >> 5;
@@ -630,15 +632,15 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
 
 }  // namespace
 
-cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const float4* rec,
+cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
                              const RowGeom* geom, const uint32_t* vals, const int2* ranges, float* out,
                              int32_t* n_contrib, int32_t* last, int32_t* med,
                              unsigned long long* counters, cudaStream_t st) {
-  const dim3 grid(cam.tiles_x, cam.tiles_y);
+  const unsigned grid = (unsigned)cam.tiles_x * (unsigned)cam.tiles_y;
   const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
   ProfScope ps(kProfBlendFwd, st);
-  blend_fwd_kernel<<<grid, kThreads, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, n_contrib, last,
-                                              med, counters);
+  blend_fwd_kernel<<<grid, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out, n_contrib,
+                                              last, med, counters);
   count_launch();
   return cudaGetLastError();
 }
@@ -650,12 +652,12 @@ cudaError_t launch_blend_fwd_batched(const BlendBatch& batch, int grid, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const float4* rec,
+cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
                              const RowGeom* geom, const uint32_t* vals, const int2* ranges, const float* out,
                              const int32_t* last, const int32_t* med, const AdjDev& adj,
                              float* grec, float* screen, int n, unsigned long long* counters,
                              cudaStream_t st) {
-  const dim3 grid(cam.tiles_x, cam.tiles_y);
+  const unsigned grid = (unsigned)cam.tiles_x * (unsigned)cam.tiles_y;
   const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
   // the training loss drives set 0 through colour and inverse depth only and
   // the other sets through colour: a leaner kernel for that layout
@@ -663,11 +665,11 @@ cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const float4*
   for (int s = 1; s < adj.n_sets; ++s) loss_layout = loss_layout && (adj.mask[s] & ~GS_MASK_RGB) == 0u;
   ProfScope ps(kProfBlendBwd, st);
   if (loss_layout)
-    blend_bwd_kernel<true><<<grid, kThreads, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, last, med,
-                                                      adj, grec, screen, n, counters);
+    blend_bwd_kernel<true><<<grid, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out, last,
+                                                      med, adj, grec, screen, n, counters);
   else
-    blend_bwd_kernel<false><<<grid, kThreads, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, out, last, med,
-                                                       adj, grec, screen, n, counters);
+    blend_bwd_kernel<false><<<grid, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out, last,
+                                                       med, adj, grec, screen, n, counters);
   count_launch();
   return cudaGetLastError();
 }

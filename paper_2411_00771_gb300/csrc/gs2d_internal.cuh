@@ -178,8 +178,13 @@ cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint3
                         uint32_t* keys, uint32_t* vals, cudaStream_t st, const uint32_t* n_dev = nullptr);
 cudaError_t launch_ranges(const uint32_t* keys, int64_t K, int2* ranges, int ntiles,
                           cudaStream_t st);
+// Tile ids ordered by list length, longest first (launch order of the blends);
+// for images with more tiles than the ordering kernel holds, nothing is
+// written and the blends take the natural order (pass a null order).
+bool tile_order_supported(int ntiles);
+cudaError_t launch_tile_order(const int2* ranges, int ntiles, uint32_t* order, cudaStream_t st);
 
-cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const float4* rec,
+cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
                              const RowGeom* geom, const uint32_t* vals, const int2* ranges, float* out,
                              int32_t* n_contrib, int32_t* last, int32_t* med,
                              unsigned long long* counters, cudaStream_t st);
@@ -215,7 +220,7 @@ struct AdjDev {
 // Per-surfel intermediate gradient record of the blend backward.
 constexpr int kGradRec = 16;  // Ji(4) e(2) c(2) p_z(1) opacity(1) rgb(3) n(3)
 
-cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const float4* rec,
+cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
                              const RowGeom* geom, const uint32_t* vals, const int2* ranges, const float* out,
                              const int32_t* last, const int32_t* med, const AdjDev& adj,
                              float* grec, float* screen, int n, unsigned long long* counters,

@@ -305,6 +305,41 @@ __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t K, int2
   if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (int)(i + 1);
 }
 
+// Tiles ordered by list length, longest first (by octave of the length;
+// order within an octave is arbitrary): launching the blends in this order
+// starts the longest tiles first, so the last wave is short ones.  Results
+// do not depend on the order.  One block; the octaves are staged in shared
+// memory (up to kMaxOrderTiles tiles).
+constexpr int kMaxOrderTiles = 40960;
+__global__ void __launch_bounds__(1024) tile_order_kernel(const int2* __restrict__ ranges, int ntiles,
+                                                          uint32_t* __restrict__ order) {
+  __shared__ uint8_t oct[kMaxOrderTiles];
+  __shared__ uint32_t cnt[32], cur[32];
+  if (threadIdx.x < 32) cnt[threadIdx.x] = 0u;
+  __syncthreads();
+#pragma unroll 8
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const int2 r = ranges[t];
+    const int o = __clz((uint32_t)(r.y - r.x) | 1u);  // 31 - octave: longest first
+    oct[t] = (uint8_t)o;
+    atomicAdd(&cnt[o], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // exclusive scan of the 32 bucket counts in one warp
+    const uint32_t c = cnt[threadIdx.x];
+    uint32_t v = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, v, d);
+      if ((int)threadIdx.x >= d) v += u;
+    }
+    cur[threadIdx.x] = v - c;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) order[atomicAdd(&cur[oct[t]], 1u)] = (uint32_t)t;
+}
+
 }  // namespace
 
 // block sums, then the last-block counter
@@ -386,6 +421,16 @@ cudaError_t launch_ranges(const uint32_t* keys, int64_t K, int2* ranges, int nti
   if (e != cudaSuccess || K <= 0) return e;
   count_launch();
   ranges_kernel<<<div_up(K, 256), 256, 0, st>>>(keys, K, ranges);
+  return cudaGetLastError();
+}
+
+bool tile_order_supported(int ntiles) { return ntiles > 0 && ntiles <= kMaxOrderTiles; }
+
+cudaError_t launch_tile_order(const int2* ranges, int ntiles, uint32_t* order, cudaStream_t st) {
+  if (!tile_order_supported(ntiles)) return cudaSuccess;
+  ProfScope ps(kProfSort, st);
+  count_launch();
+  tile_order_kernel<<<1, 1024, 0, st>>>(ranges, ntiles, order);
   return cudaGetLastError();
 }
 
