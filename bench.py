@@ -40,6 +40,23 @@ FLOP_BWD_PAIR = 140  # per blended pair in the backward (adjoints + chain)
 SM_COUNT, FP32_LANES, SM_MAX_HZ = 152, 128, 2.07e9
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_HZ / 1e12
 
+# DRAM bytes (read + write) of one blend_bwd launch on this workload, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the
+# full-size view); valid only for the kernel sources it was taken on.
+BLEND_BWD_TRAFFIC = {"bytes": 173731584 + 12451072,
+                     "sources_sha256": "f425e582ecc3e9b07177ae1dc450ab8a9022c2225a6c2c6abb84437e1e26821a"}
+
+
+def blend_bwd_traffic():
+    """The captured traffic if blend.cu + gs2d_internal.cuh are unchanged, else None."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    h = hashlib.sha256()
+    for f in ("blend.cu", "gs2d_internal.cuh"):
+        with open(os.path.join(here, "paper_2411_00771_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return BLEND_BWD_TRAFFIC["bytes"] if h.hexdigest() == BLEND_BWD_TRAFFIC["sources_sha256"] else None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -252,7 +269,8 @@ def run_ours(args):
     achieved = work[dom] / (per_launch[dom] * 1e-3) / 1e12
     roofline = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "traffic": (blend_bwd_traffic() if dom == "blend_bwd" and W == 1600 and H == 900 else None),
                 "ms_per_launch": round(per_launch[dom], 4),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and max clock)"}
     # per step: a group may record several scopes per step (the sort group
