@@ -10,7 +10,8 @@ OpenMP) and marshals numpy arrays through ctypes.
 Passages followed: Eq. 1 (Sec. 3.1, alpha compositing), Sec. 3.1 (2D
 Gaussian surfels, L1 + D-SSIM), Sec. 3.2 (depth loss on inverse depth,
 elongation rate eta, Eq. 2 decomposed-gradient densification, antialiasing
-low-pass filter), Sec. 4.1 (median depth), of CityGaussianV2.
+low-pass filter), Sec. 3.3 (Eq. 3 trim contribution, percentile pruning),
+Sec. 4.1 (median depth), of CityGaussianV2.
 """
 from __future__ import annotations
 
@@ -261,3 +262,33 @@ def elongation(scale, eta_thr=0.1):
     keep = np.zeros(sc.shape[0], np.uint8)
     lib.oracle_elongation(ctypes.c_int64(sc.shape[0]), _p(sc), ctypes.c_double(eta_thr), _p(keep))
     return keep
+
+
+def contribution(scene, cam, gamma=0.5, settings=None, mode=1):
+    """Single-view trim contribution (Sec. 3.3, Eq. 3).  Returns dict with
+    sum[N], count[N] (|P_k|, the support pixels), flagged[N] (support pixels
+    whose compositing took a near-threshold decision) and C[N] = sum / count
+    (0 where count = 0)."""
+    lib = _load()
+    n, deg, arrs = _scene_args(scene)
+    c, s = cam_array(cam), settings_array(settings)
+    out = dict(sum=np.zeros(n), count=np.zeros(n, np.int64), flagged=np.zeros(n, np.int64))
+    lib.oracle_contribution(ctypes.c_int64(n), ctypes.c_int(deg), *[_p(a) for a in arrs], _p(c), _p(s),
+                            ctypes.c_int(mode), ctypes.c_double(gamma), _p(out["sum"]), _p(out["count"]),
+                            _p(out["flagged"]))
+    out["C"] = np.where(out["count"] > 0, out["sum"] / np.maximum(out["count"], 1), 0.0)
+    return out
+
+
+def prune_bound(contrib, ratio):
+    """Percentile prune (Sec. 3.3): with k = ceil(ratio * N) (clamped to
+    [0, N]), the bound is the k-th smallest contribution; surfels at or below
+    it are removed.  Returns (bound or None when k = 0, keep mask)."""
+    c = np.asarray(contrib, np.float64)
+    n = c.size
+    k = int(np.ceil(ratio * n)) if n else 0
+    k = min(max(k, 0), n)
+    if k == 0:
+        return None, np.ones(n, bool)
+    bound = np.sort(c)[k - 1]
+    return bound, c > bound

@@ -19,6 +19,7 @@
  *   - Sec. 3.1: L1 + D-SSIM photometric loss; Sec. 3.2: depth loss on inverse
  *     depth; Sec. 3.2 Eq. 2: decomposed-gradient densification; Sec. 3.2:
  *     elongation rate eta = min(s)/max(s).
+ *   - Sec. 3.3 Eq. 3: single-view trim contribution of each surfel.
  * Readings where the paper is silent (pixel centres at +0.5, alpha clamp 0.99,
  * stop before the pair that would take T below T_min, the per-pair 3-sigma
  * support rho <= 9, screen filter rho_scr = 2 |x - c|^2, centre depth when the
@@ -1113,6 +1114,85 @@ int oracle_tile_lists(int64_t N, int deg, const double* mu, const double* quat, 
     qsort(k, (size_t)(b - a), sizeof(okey_t), cmp_keys);
     for (int64_t i = a; i < b; ++i) idx[i] = k[i - a].n;
     free(k);
+  }
+  ctx_free(&C);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Trim contribution (Sec. 3.3, Eq. 3).                                     */
+
+/* Single-view contribution of every surfel, as its two parts: for surfel n,
+ *   count[n] = |P_k|, the pixels of the view inside n's projected region
+ *              (its 3-sigma support rho <= rho_max, occluded or not), and
+ *   sum[n]   = sum over those pixels of alpha^gamma * T^(1 - gamma), with
+ *              alpha the opacity the compositing applied to the pair (0 for a
+ *              pair below the alpha cutoff or behind the pixel's stop) and T
+ *              the transmittance in front of n on that pixel (the product of
+ *              (1 - alpha_j) over the pairs composited before it),
+ * so that C_{n,k} = sum[n] / count[n] (0 when count[n] = 0).
+ * flagged[n] counts n's support pixels whose compositing took a decision
+ * within a hair of a threshold (the per-pixel flags of the render), where an
+ * FP32 implementation may legitimately differ.  Outputs are overwritten. */
+int oracle_contribution(int64_t N, int deg, const double* mu, const double* quat, const double* scale,
+                        const double* opac, const double* sh, const double* cam, const double* set,
+                        int mode, double gamma, double* sum, int64_t* count, int64_t* flagged) {
+  scene_t S = mk_scene(N, deg, mu, quat, scale, opac, sh);
+  ctx_t C;
+  ctx_init(&C, &S, cam, set, mode);
+  for (int64_t n = 0; n < N; ++n) { sum[n] = 0.0; count[n] = 0; flagged[n] = 0; }
+  const int64_t HW = (int64_t)C.W * C.H;
+#pragma omp parallel
+  {
+    pair_t* sup = (pair_t*)malloc(sizeof(pair_t) * (size_t)C.maxlist);
+    okey_t* keys = (okey_t*)malloc(sizeof(okey_t) * (size_t)C.maxlist);
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t f = 0; f < HW; ++f) {
+      const int i = (int)(f % C.W), j = (int)(f / C.W);
+      const double x = i + 0.5, y = j + 0.5;
+      const int* cand; int nc;
+      pixel_list(&C, i, j, &cand, &nc);
+      /* the pixel's support pairs, in compositing order */
+      int m = 0, fl = 0;
+      for (int c = 0; c < nc; ++c) {
+        const int n = cand[c];
+        if (!C.pre[n].live) continue;
+        pair_t pr;
+        eval_pair(&C.pre[n], n, x, y, set, &pr);
+        if (fabs(pr.rho - set[SET_RHO_MAX]) < 1e-4) fl = 1;
+        if (!(pr.rho <= set[SET_RHO_MAX])) continue;
+        sup[m] = pr;
+        keys[m].z = C.pre[n].zkey; keys[m].n = n; keys[m].slot = m;
+        ++m;
+      }
+      qsort(keys, (size_t)m, sizeof(okey_t), cmp_keys);
+      double T = 1.0;
+      int stopped = 0;
+      for (int k = 0; k < m; ++k) {
+        const pair_t* pr = &sup[keys[k].slot];
+        if (fabs(pr->alpha / set[SET_ALPHA_MIN] - 1.0) < 1e-5) fl = 1;
+        double a = 0.0;  /* opacity the compositing applies */
+        if (!stopped && pr->alpha >= set[SET_ALPHA_MIN]) {
+          const double Tn = T * (1.0 - pr->alpha);
+          if (fabs(Tn / set[SET_T_MIN] - 1.0) < 1e-5) fl = 1;
+          if (Tn < set[SET_T_MIN]) stopped = 1;
+          else a = pr->alpha;
+        }
+        const int n = keys[k].n;
+        double c = 0.0;
+        if (a > 0.0) c = pow(a, gamma) * pow(T, 1.0 - gamma);
+#pragma omp atomic
+        count[n] += 1;
+        if (c != 0.0) atomic_add(&sum[n], c);
+        if (a > 0.0) T *= 1.0 - a;
+      }
+      if (fl)
+        for (int k = 0; k < m; ++k) {
+#pragma omp atomic
+          flagged[keys[k].n] += 1;
+        }
+    }
+    free(sup); free(keys);
   }
   ctx_free(&C);
   return 0;

@@ -480,3 +480,138 @@ def test_densify_accumulate_counts_visible_views():
     st = oracle.densify_accumulate(scr, np.array([1, 0, 1]), st)
     assert np.allclose(st[0], [10.0, 2.0, 20.0, 2.0]) and np.all(st[1] == 0)
     assert np.allclose(st[2], [0, 0, 0, 2.0])
+
+
+# --------------------------------------------------------------------------
+# Trim contribution (Sec. 3.3, Eq. 3) and the percentile prune
+
+def test_contribution_of_single_splat_closed_form():
+    """One fronto-parallel disk: T = 1 on every pixel, so C = mean over the
+    support {rho <= 9} of alpha^gamma (0 where alpha < 1/255), with rho and
+    alpha in closed form (no ray-splat code involved)."""
+    cam = camera(64, 64, 64.0)
+    z0, su, sv, o = 3.0, 0.21, 0.13, 0.8
+    sc = make_scene([dict(mu=(0, 0, z0), scale=(su, sv), opacity=o)])
+    x, y = pixel_grid(cam)
+    dx, dy = x - 32.0, y - 32.0
+    rho = np.minimum((dx * z0 / (64.0 * su)) ** 2 + (dy * z0 / (64.0 * sv)) ** 2, 2.0 * (dx * dx + dy * dy))
+    alpha = np.minimum(0.99, o * np.exp(-0.5 * rho))
+    support = rho <= 9.0
+    used = support & (alpha >= ALPHA_MIN)
+    for gamma in (0.5, 0.25, 1.0):
+        r = oracle.contribution(sc, cam, gamma=gamma)
+        assert r["count"][0] == support.sum()
+        expect = np.where(used, alpha ** gamma, 0.0).sum()
+        assert abs(r["sum"][0] - expect) < 1e-12 * max(1.0, expect)
+        assert abs(r["C"][0] - expect / support.sum()) < 1e-14
+
+
+def test_contribution_of_occluded_splat_uses_front_transmittance():
+    """Two stacked disks: the back one sees T = 1 - alpha_front on every pixel
+    (Eq. 3's product over the pairs in front); swapping depths swaps roles."""
+    cam = camera(16, 16, 16.0)
+    z1, z2, o1, o2 = 2.0, 3.0, 0.3, 0.6
+    sc = _two_splats(z1, z2, o1, o2)
+    x, y = pixel_grid(cam)
+    d2 = (x - 8.0) ** 2 + (y - 8.0) ** 2
+    a1 = np.minimum(0.99, o1 * np.exp(-0.5 * np.minimum(d2 * (z1 / 80.0) ** 2, 2 * d2)))
+    a2 = np.minimum(0.99, o2 * np.exp(-0.5 * np.minimum(d2 * (z2 / 80.0) ** 2, 2 * d2)))
+    r = oracle.contribution(sc, cam, gamma=0.5)
+    assert np.all(r["count"] == 256)
+    assert abs(r["sum"][0] - np.sqrt(a1).sum()) < 1e-12
+    assert abs(r["sum"][1] - np.sqrt(a2 * (1 - a1)).sum()) < 1e-12
+    r0 = oracle.contribution(sc, cam, gamma=0.0)  # T in front, blended pairs only
+    assert abs(r0["sum"][1] - (1 - a1).sum()) < 1e-12
+    # surfel 0 behind surfel 1: the order follows depth, not the index
+    b1 = np.minimum(0.99, o1 * np.exp(-0.5 * np.minimum(d2 * (z2 / 80.0) ** 2, 2 * d2)))
+    b2 = np.minimum(0.99, o2 * np.exp(-0.5 * np.minimum(d2 * (z1 / 80.0) ** 2, 2 * d2)))
+    rs = oracle.contribution(_two_splats(z2, z1, o1, o2), cam, gamma=0.5)
+    assert abs(rs["sum"][1] - np.sqrt(b2).sum()) < 1e-12
+    assert abs(rs["sum"][0] - np.sqrt(b1 * (1 - b2)).sum()) < 1e-12
+
+
+@pytest.mark.parametrize("gamma", [0.5, 0.3])
+def test_contribution_brute_force_with_closed_form_geometry(gamma):
+    """Fronto-parallel disks anywhere in view have a closed-form rho at every
+    pixel (the ray meets the plane z = z_i at (p - c) z_i / f), so Eq. 3 can be
+    evaluated by brute force with no ray-splat code: support rho <= 9, order by
+    the FP32 centre depth then index, alpha cutoff, the stop, T in front."""
+    W = H = 24
+    f = 24.0
+    cam = camera(W, H, f)
+    rng = np.random.default_rng(7)
+    surf = []
+    for i in range(14):
+        z = rng.uniform(2.0, 4.0)
+        surf.append(dict(mu=(rng.uniform(-0.8, 0.8), rng.uniform(-0.8, 0.8), z),
+                         scale=(rng.uniform(0.05, 0.6), rng.uniform(0.05, 0.6)),
+                         opacity=float(rng.choice([0.02, 0.5, 0.95]))))
+    r = oracle.contribution(make_scene(surf), cam, gamma=gamma)
+    x, y = pixel_grid(cam)
+    z32 = np.array([np.float32(s_["mu"][2]) for s_ in surf], np.float64)
+    order = sorted(range(len(surf)), key=lambda i: (z32[i], i))
+    rho = []
+    for s_ in surf:
+        mx, my, mz = s_["mu"]
+        cx, cy = f * mx / mz + W / 2, f * my / mz + H / 2
+        dx, dy = x - cx, y - cy
+        ro = (dx * mz / (f * s_["scale"][0])) ** 2 + (dy * mz / (f * s_["scale"][1])) ** 2
+        rho.append(np.minimum(ro, 2.0 * (dx * dx + dy * dy)))
+    exp_sum = np.zeros(len(surf))
+    exp_cnt = np.zeros(len(surf), np.int64)
+    for j in range(H):
+        for i in range(W):
+            T, stopped = 1.0, False
+            for n in order:
+                rr = rho[n][j, i]
+                if not rr <= 9.0:
+                    continue
+                exp_cnt[n] += 1
+                a = min(0.99, surf[n]["opacity"] * math.exp(-0.5 * rr))
+                if stopped or a < ALPHA_MIN:
+                    continue
+                if T * (1 - a) < 1e-4:
+                    stopped = True
+                    continue
+                exp_sum[n] += a ** gamma * T ** (1 - gamma)
+                T *= 1 - a
+    assert np.array_equal(r["count"], exp_cnt)
+    assert np.abs(r["sum"] - exp_sum).max() < 1e-11
+    # the low-opacity disks have support pixels below the alpha cutoff
+    low = [n for n in range(len(surf)) if surf[n]["opacity"] == 0.02]
+    assert any(exp_cnt[n] > 0 for n in low)
+
+
+def test_contribution_counts_the_support_and_stops_with_the_pixel():
+    """Behind a stack that stops the pixels (T below 1e-4), later disks keep
+    their support pixels in |P| but add nothing; never-seen disks get 0."""
+    cam = camera(16, 16, 16.0)
+    big = (50.0, 50.0)
+    surf = [dict(mu=(0, 0, 2.0 + 0.1 * k), scale=big, opacity=0.8) for k in range(8)]
+    surf.append(dict(mu=(100.0, 0, 2.0), scale=(0.1, 0.1), opacity=0.8))  # off screen
+    r = oracle.contribution(make_scene(surf), cam, gamma=0.5)
+    assert np.all(r["count"][:8] == 256) and r["count"][8] == 0 and r["C"][8] == 0
+    assert np.all(r["sum"][:5] > 0) and np.all(r["sum"][5:] == 0)  # 5 pairs blended per pixel
+
+
+def test_contribution_brute_force_equals_binned():
+    scene, cam, _, _ = syn.tiny_scene(seed=4, n=200, width=32, height=32, fx=32.0,
+                                      log_scale_range=(-4.0, -1.0), sh_degree=1, z_range=(0.5, 4.0))
+    rb = oracle.contribution(scene, cam, mode=0)
+    rt = oracle.contribution(scene, cam, mode=1)
+    assert np.array_equal(rb["count"], rt["count"])
+    assert np.abs(rb["sum"] - rt["sum"]).max() < 1e-12
+
+
+def test_prune_bound_percentile():
+    """Sec. 3.3: remove the surfels at or below the ratio-percentile bound,
+    ties included (all never-observed zeros go, whatever the ratio)."""
+    c = np.array([0.5, 0.0, 0.2, 0.0, 0.9, 0.2, 0.7, 0.0, 0.3, 0.1])
+    bound, keep = oracle.prune_bound(c, 0.1)  # k = 1 -> bound = 0: all three zeros removed
+    assert bound == 0.0 and keep.sum() == 7
+    bound, keep = oracle.prune_bound(c, 0.5)  # k = 5: sorted 0,0,0,.1,.2,.2 -> bound .2
+    assert bound == 0.2 and np.array_equal(keep, c > 0.2) and keep.sum() == 4
+    bound, keep = oracle.prune_bound(c, 0.0)
+    assert bound is None and keep.all()
+    bound, keep = oracle.prune_bound(c, 1.0)
+    assert bound == 0.9 and not keep.any()
