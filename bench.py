@@ -277,6 +277,8 @@ def run_ours(args):
     # covers every scan, radix pass, emit and range pass of a render)
     breakdown = {k: round(v[0] / args.steps, 4) for k, v in prof.items()}
 
+    contribution = measure_contribution(sc, cam, n, dev, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene_np, cam, tgt_np, tinv_np, budget_s=20.0)
@@ -305,11 +307,45 @@ def run_ours(args):
                      "bwd_lanes_per_step": round(info["bwd_warp_lanes"] / max(1, info["bwd_warp_entries"]), 2)},
             "clocks": clk,
             "cpu_baseline": cpu,
+            "contribution": contribution,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_contribution(sc, cam, n, dev, args):
+    """Trim contribution (Sec. 3.3, Eq. 3) of the same view, accumulated with
+    weight 1 (Eq. 4's sum), and the percentile prune at the paper's ratio, each
+    timed with CUDA events over repeated calls after warm-up."""
+    import torch
+    from paper_2411_00771_gb300 import binding as B
+    contrib = torch.zeros(n, device=dev)
+    reps = max(3, min(args.steps, 20))
+    for _ in range(3):
+        sc.contribution(cam, gamma=0.5, weight=1.0, contrib=contrib)
+    torch.cuda.synchronize()
+    l0 = B.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        sc.contribution(cam, gamma=0.5, weight=1.0, contrib=contrib)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_view = e0.elapsed_time(e1) / reps
+    launches = (B.kernel_launches() - l0) / reps
+    for _ in range(3):
+        B.prune_by_contribution(contrib, 0.025)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        keep, bound = B.prune_by_contribution(contrib, 0.025)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"ms_per_view": round(ms_view, 4), "gamma": 0.5, "launches_per_view": launches,
+            "prune_ms": round(e0.elapsed_time(e1) / reps, 4), "prune_ratio": 0.025,
+            "pruned": int(n - int(keep.sum().item()))}
 
 
 # ---------------------------------------------------------------------------

@@ -258,6 +258,41 @@ gs_status gs_densify_select(int64_t n, const float* stats, const float* scale, f
 gs_status gs_elongation_filter(int64_t n, const float* scale, float eta_thr, uint8_t* keep,
                                void* stream);
 
+/* ---- Trim contribution and pruning (Sec. 3.3) ------------------------------
+ *
+ * gs_contribution: the single-view contribution of every surfel, Eq. 3,
+ *   C_{n,k} = (1/|P_k|) sum over p in P_k of alpha_n^gamma T_n(p)^(1-gamma),
+ * where P_k is the surfel's projected region in view k (the pixels inside its
+ * 3-sigma support rho <= rho_max, occluded or not), alpha_n the opacity the
+ * compositing applies to the pair (0 below the alpha cutoff and behind the
+ * pixel's transmittance stop) and T_n(p) the transmittance in front of it.
+ * The view is preprocessed and ordered exactly as gs_render does (the same
+ * tile lists and compositing decisions) but no image is written.
+ *   gamma:       in [0, 1]; the paper's value is 0.5.
+ *   contrib:     device FP32 [N] or NULL; weight * C_{n,k} is ADDED (C = 0
+ *                where |P_k| = 0).  With weight = 1/|V_m| over the views of a
+ *                block this accumulates Eq. 4's average.
+ *   view_sum, view_count: device [N] (FP32, uint32) or NULL; when given they
+ *                are overwritten with this view's sum and |P_k| (0 for
+ *                surfels outside the view).
+ * At least one output must be given.  Reads one 4-byte count back (like
+ * gs_render); otherwise asynchronous on `stream`.  Errors: GS_ERR_ARG
+ * (null scene/camera/outputs, gamma outside [0, 1], bad camera), GS_ERR_OOM,
+ * GS_ERR_CAPACITY, GS_ERR_CUDA.
+ *
+ * gs_prune_by_contribution: percentile pruning, Sec. 3.3.  With
+ * k = ceil(ratio * n) clamped to [0, n], the bound is the k-th smallest value
+ * of contrib (device FP32 [n]); keep[i] (device uint8 [n]) = contrib[i] >
+ * bound, so every surfel at or below the bound is removed, ties and
+ * never-observed (0) surfels included.  k = 0 keeps everything and the bound
+ * is -inf.  bound: device FP32 [1] or NULL.  ratio must be in [0, 1] (the
+ * paper uses 0.025 and, in its ablation, 0.1).  Asynchronous; allocates a
+ * 1 KB scratch through the default allocator. */
+gs_status gs_contribution(gs_scene* scene, const gs_camera* camera, float gamma, float weight,
+                          float* contrib, float* view_sum, uint32_t* view_count, void* stream);
+gs_status gs_prune_by_contribution(int64_t n, const float* contrib, double ratio, uint8_t* keep,
+                                   float* bound, void* stream);
+
 /* ---- Serving: continuous batching of forward renders ------------------
  * (the serving loop built on the rasterizer; the paper has no serving
  * component of its own.)
@@ -311,10 +346,12 @@ gs_status gs_server_destroy(gs_server* server);
  * gs_profile_read: synchronises the recorded events of one group, returns
  *   their summed duration (ms) and count, and forgets them.  Groups:
  *   0 preprocess, 1 scan/sort/emit/ranges, 2 forward blend, 3 loss,
- *   4 backward blend, 5 preprocess backward, 6 densify/filter. */
+ *   4 backward blend, 5 preprocess backward, 6 densify/filter,
+ *   7 trim contribution and pruning. */
 enum {
   GS_PROF_PREPROCESS = 0, GS_PROF_SORT = 1, GS_PROF_BLEND_FWD = 2, GS_PROF_LOSS = 3,
-  GS_PROF_BLEND_BWD = 4, GS_PROF_PREPROCESS_BWD = 5, GS_PROF_DENSIFY = 6, GS_PROF_GROUPS = 7
+  GS_PROF_BLEND_BWD = 4, GS_PROF_PREPROCESS_BWD = 5, GS_PROF_DENSIFY = 6, GS_PROF_CONTRIB = 7,
+  GS_PROF_GROUPS = 8
 };
 uint64_t gs_kernel_launches(void);
 gs_status gs_profile_enable(int32_t on);

@@ -266,16 +266,18 @@ def elongation(scale, eta_thr=0.1):
 
 def contribution(scene, cam, gamma=0.5, settings=None, mode=1):
     """Single-view trim contribution (Sec. 3.3, Eq. 3).  Returns dict with
-    sum[N], count[N] (|P_k|, the support pixels), flagged[N] (support pixels
-    whose compositing took a near-threshold decision) and C[N] = sum / count
-    (0 where count = 0)."""
+    sum[N], count[N] (|P_k|, the support pixels), flag_count[N] (pixels where
+    the surfel's own support membership is within a hair of the threshold),
+    flag_sum[N] (pixels where a decision at or in front of the surfel was near
+    its threshold) and C[N] = sum / count (0 where count = 0)."""
     lib = _load()
     n, deg, arrs = _scene_args(scene)
     c, s = cam_array(cam), settings_array(settings)
-    out = dict(sum=np.zeros(n), count=np.zeros(n, np.int64), flagged=np.zeros(n, np.int64))
+    out = dict(sum=np.zeros(n), count=np.zeros(n, np.int64), flag_count=np.zeros(n, np.int64),
+               flag_sum=np.zeros(n, np.int64))
     lib.oracle_contribution(ctypes.c_int64(n), ctypes.c_int(deg), *[_p(a) for a in arrs], _p(c), _p(s),
                             ctypes.c_int(mode), ctypes.c_double(gamma), _p(out["sum"]), _p(out["count"]),
-                            _p(out["flagged"]))
+                            _p(out["flag_count"]), _p(out["flag_sum"]))
     out["C"] = np.where(out["count"] > 0, out["sum"] / np.maximum(out["count"], 1), 0.0)
     return out
 

@@ -1131,17 +1131,25 @@ int oracle_tile_lists(int64_t N, int deg, const double* mu, const double* quat, 
  *              the transmittance in front of n on that pixel (the product of
  *              (1 - alpha_j) over the pairs composited before it),
  * so that C_{n,k} = sum[n] / count[n] (0 when count[n] = 0).
- * flagged[n] counts n's support pixels whose compositing took a decision
- * within a hair of a threshold (the per-pixel flags of the render), where an
- * FP32 implementation may legitimately differ.  Outputs are overwritten. */
+ * Decisions within a hair of a threshold, where an FP32 implementation may
+ * legitimately decide the other way, are reported per surfel:
+ *   flag_count[n]: pixels where n's own rho is within 1e-4 of rho_max (its
+ *                  membership in P_k is uncertain);
+ *   flag_sum[n]:   pixels of n's (near-)support where some decision at or in
+ *                  front of n was near its threshold (rho near rho_max, alpha
+ *                  near the cutoff, the stop near T_min), so that n's alpha or
+ *                  T there is uncertain.
+ * Outputs are overwritten. */
 int oracle_contribution(int64_t N, int deg, const double* mu, const double* quat, const double* scale,
                         const double* opac, const double* sh, const double* cam, const double* set,
-                        int mode, double gamma, double* sum, int64_t* count, int64_t* flagged) {
+                        int mode, double gamma, double* sum, int64_t* count, int64_t* flag_count,
+                        int64_t* flag_sum) {
   scene_t S = mk_scene(N, deg, mu, quat, scale, opac, sh);
   ctx_t C;
   ctx_init(&C, &S, cam, set, mode);
-  for (int64_t n = 0; n < N; ++n) { sum[n] = 0.0; count[n] = 0; flagged[n] = 0; }
+  for (int64_t n = 0; n < N; ++n) { sum[n] = 0.0; count[n] = 0; flag_count[n] = 0; flag_sum[n] = 0; }
   const int64_t HW = (int64_t)C.W * C.H;
+  const double rmax = set[SET_RHO_MAX];
 #pragma omp parallel
   {
     pair_t* sup = (pair_t*)malloc(sizeof(pair_t) * (size_t)C.maxlist);
@@ -1152,45 +1160,53 @@ int oracle_contribution(int64_t N, int deg, const double* mu, const double* quat
       const double x = i + 0.5, y = j + 0.5;
       const int* cand; int nc;
       pixel_list(&C, i, j, &cand, &nc);
-      /* the pixel's support pairs, in compositing order */
-      int m = 0, fl = 0;
+      /* the pixel's support pairs and those within the margin outside it,
+       * in compositing order */
+      int m = 0;
       for (int c = 0; c < nc; ++c) {
         const int n = cand[c];
         if (!C.pre[n].live) continue;
         pair_t pr;
         eval_pair(&C.pre[n], n, x, y, set, &pr);
-        if (fabs(pr.rho - set[SET_RHO_MAX]) < 1e-4) fl = 1;
-        if (!(pr.rho <= set[SET_RHO_MAX])) continue;
+        if (!(pr.rho <= rmax + 1e-4)) continue;
         sup[m] = pr;
         keys[m].z = C.pre[n].zkey; keys[m].n = n; keys[m].slot = m;
         ++m;
       }
       qsort(keys, (size_t)m, sizeof(okey_t), cmp_keys);
       double T = 1.0;
-      int stopped = 0;
+      int stopped = 0, taint = 0;
       for (int k = 0; k < m; ++k) {
         const pair_t* pr = &sup[keys[k].slot];
-        if (fabs(pr->alpha / set[SET_ALPHA_MIN] - 1.0) < 1e-5) fl = 1;
-        double a = 0.0;  /* opacity the compositing applies */
-        if (!stopped && pr->alpha >= set[SET_ALPHA_MIN]) {
-          const double Tn = T * (1.0 - pr->alpha);
-          if (fabs(Tn / set[SET_T_MIN] - 1.0) < 1e-5) fl = 1;
-          if (Tn < set[SET_T_MIN]) stopped = 1;
-          else a = pr->alpha;
-        }
         const int n = keys[k].n;
-        double c = 0.0;
-        if (a > 0.0) c = pow(a, gamma) * pow(T, 1.0 - gamma);
+        const int in = pr->rho <= rmax;
+        if (fabs(pr->rho - rmax) < 1e-4) {
+          taint = 1;
+#pragma omp atomic
+          flag_count[n] += 1;
+        }
+        double a = 0.0;  /* opacity the compositing applies */
+        if (in) {
+          if (fabs(pr->alpha / set[SET_ALPHA_MIN] - 1.0) < 1e-5) taint = 1;
+          if (!stopped && pr->alpha >= set[SET_ALPHA_MIN]) {
+            const double Tn = T * (1.0 - pr->alpha);
+            if (fabs(Tn / set[SET_T_MIN] - 1.0) < 1e-5) taint = 1;
+            if (Tn < set[SET_T_MIN]) stopped = 1;
+            else a = pr->alpha;
+          }
+        }
+        if (taint) {
+#pragma omp atomic
+          flag_sum[n] += 1;
+        }
+        if (!in) continue;
 #pragma omp atomic
         count[n] += 1;
-        if (c != 0.0) atomic_add(&sum[n], c);
-        if (a > 0.0) T *= 1.0 - a;
-      }
-      if (fl)
-        for (int k = 0; k < m; ++k) {
-#pragma omp atomic
-          flagged[keys[k].n] += 1;
+        if (a > 0.0) {
+          atomic_add(&sum[n], pow(a, gamma) * pow(T, 1.0 - gamma));
+          T *= 1.0 - a;
         }
+      }
     }
     free(sup); free(keys);
   }

@@ -115,6 +115,8 @@ _SIGS = {
     "gs_densify_select": [ctypes.c_int64, _V, _V, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                           _V, _V, _V, _V],
     "gs_elongation_filter": [ctypes.c_int64, _V, ctypes.c_float, _V, _V],
+    "gs_contribution": [_V, ctypes.POINTER(gs_camera), ctypes.c_float, ctypes.c_float, _V, _V, _V, _V],
+    "gs_prune_by_contribution": [ctypes.c_int64, _V, ctypes.c_double, _V, _V, _V],
     "gs_sync": [_V, ctypes.c_int32],
     "gs_profile_enable": [ctypes.c_int32],
     "gs_server_create": [ctypes.POINTER(_V), ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(gs_allocator)],
@@ -137,7 +139,8 @@ _lib.gs_kernel_launches.restype = ctypes.c_uint64
 _lib.gs_kernel_launches.argtypes = []
 
 EXPORTED = list(_SIGS) + ["gs_last_error", "gs_version", "gs_kernel_launches"]
-PROF_GROUPS = ["preprocess", "sort", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "densify"]
+PROF_GROUPS = ["preprocess", "sort", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "densify",
+               "contribution"]
 
 
 def lib():
@@ -284,6 +287,18 @@ class Scene:
         _check(_lib.gs_backward(self._handle, frame.handle, arr, m, n_sets, ctypes.byref(g),
                                 _ptr(screen, shape=(n_sets, self.n, 2), name="screen"), _stream(stream)))
 
+    def contribution(self, cam: dict, gamma: float = 0.5, weight: float = 1.0, contrib=None,
+                     view_sum=None, view_count=None, stream=None):
+        """Single-view trim contribution (Sec. 3.3, Eq. 3): adds weight * C_{n,k}
+        to `contrib` [N] and/or writes this view's sum and |P_k| into
+        `view_sum` / `view_count` [N].  Returns (contrib, view_sum, view_count)."""
+        c = make_camera(cam)
+        _check(_lib.gs_contribution(self._handle, ctypes.byref(c), float(gamma), float(weight),
+                                    _ptr(contrib, shape=(self.n,), name="contrib"),
+                                    _ptr(view_sum, shape=(self.n,), name="view_sum"),
+                                    _ptr(view_count, torch.int32, (self.n,), "view_count"), _stream(stream)))
+        return contrib, view_sum, view_count
+
     def densify_accumulate(self, frame: Frame, screen, stats, stream=None):
         n_sets = screen.shape[0]
         _check(_lib.gs_densify_accumulate(self._handle, frame.handle, _ptr(screen, name="screen"), n_sets,
@@ -401,6 +416,17 @@ def densify_select(stats, scale, omega=0.9, grad_thr=0.0002, eta_thr=0.1, stream
                                   float(eta_thr), _ptr(mask, torch.uint8), _ptr(g), _ptr(k),
                                   _stream(stream)))
     return mask, g, k
+
+
+def prune_by_contribution(contrib, ratio, stream=None):
+    """Percentile pruning (Sec. 3.3): keep[i] = contrib[i] > the k-th smallest
+    contribution, k = ceil(ratio * N).  Returns (keep uint8 [N], bound [1])."""
+    n = contrib.shape[0]
+    keep = torch.empty(n, dtype=torch.uint8, device=contrib.device)
+    bound = torch.empty(1, dtype=torch.float32, device=contrib.device)
+    _check(_lib.gs_prune_by_contribution(n, _ptr(contrib, shape=(n,), name="contrib"), float(ratio),
+                                         _ptr(keep, torch.uint8), _ptr(bound), _stream(stream)))
+    return keep, bound
 
 
 def elongation_filter(scale, eta_thr=0.1, stream=None):

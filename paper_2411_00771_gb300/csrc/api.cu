@@ -218,6 +218,118 @@ const ParamsDev& scene_params(const gs_scene* sc) { return sc->P; }
 const gs_settings& scene_settings(const gs_scene* sc) { return sc->settings; }
 }  // namespace gs2d
 
+extern "C" gs_status gs_frame_release(gs_frame* f, void* stream);
+
+namespace {
+
+// A frame of scene sc seen by camera c (host side; no device memory yet).
+gs_frame* new_frame(gs_scene* sc, const gs_camera* c, const float* out, const char* who, gs_status* err) {
+  if (!sc || !c) {
+    *err = fail(GS_ERR_ARG, std::string(who) + ": null argument");
+    return nullptr;
+  }
+  if (c->width <= 0 || c->height <= 0 || c->width > 16 * 65535 || c->height > 16 * 65535) {
+    *err = fail(GS_ERR_ARG, std::string(who) + ": bad image size");
+    return nullptr;
+  }
+  if (!(c->fx > 0) || !(c->fy > 0)) {
+    *err = fail(GS_ERR_ARG, std::string(who) + ": focal lengths must be > 0");
+    return nullptr;
+  }
+  gs_frame* f = new (std::nothrow) gs_frame();
+  if (!f) {
+    *err = fail(GS_ERR_OOM, std::string(who) + ": host allocation");
+    return nullptr;
+  }
+  f->scene = sc;
+  f->n = sc->P.n;
+  f->sh_degree = sc->P.sh_degree;
+  f->out = out;
+  f->buf.al = &sc->al;
+  cam_from(*c, f->cam);
+  return f;
+}
+
+// Every step of a render before the blend: preprocess, candidate depth order,
+// tile lists, ranges and the tiles' launch order, into frame f.  Reads the
+// 4-byte instance count back once.  On failure f keeps what it allocated
+// (the caller releases it).
+gs_status build_lists(gs_scene* sc, gs_frame* f, const char* who, cudaStream_t st) {
+  const CamDev& cam = f->cam;
+  const int ntiles = cam.tiles_x * cam.tiles_y;
+  const int64_t n = f->n;
+  const SetDev set = to_dev(sc->settings);
+  Buffers tmp;
+  tmp.al = &sc->al;
+  auto failed = [&](gs_status s) {
+    tmp.release_all(st);
+    return s;
+  };
+  // per-surfel buffers
+  f->rec = f->buf.get<float4>((size_t)(n > 0 ? n : 1) * kRecF4, st);
+  f->rect = f->buf.get<uint2>(n > 0 ? n : 1, st);
+  f->tcount = f->buf.get<uint32_t>(n > 0 ? n : 1, st);
+  f->ranges = f->buf.get<int2>(ntiles, st);
+  f->order = f->buf.get<uint32_t>(ntiles, st);
+  f->counters = f->buf.get<unsigned long long>(8, st);
+  f->cand = f->buf.get<uint32_t>(n > 0 ? n : 1, st);
+  f->geom = f->buf.get<RowGeom>(n > 0 ? n : 1, st);
+  uint32_t* dkey = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* idx = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* dkey2 = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* idx2 = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* cnts = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* offs = tmp.get<uint32_t>(n > 0 ? n : 1, st);
+  uint32_t* rtmp = tmp.get<uint32_t>(radix_tmp_words(n) + scan_tmp_words(n) + 4, st);
+  if (!f->rec || !f->rect || !f->tcount || !f->ranges || !f->order || !f->counters || !f->cand || !f->geom ||
+      !dkey || !idx || !dkey2 || !idx2 || !cnts || !offs || !rtmp)
+    return failed(fail(GS_ERR_OOM, std::string(who) + ": device allocation failed"));
+  uint32_t* total = rtmp + radix_tmp_words(n) + scan_tmp_words(n);
+  cudaError_t e;
+#define GS_CKC(expr)                                         \
+  do {                                                       \
+    e = (expr);                                              \
+    if (e != cudaSuccess) return failed(cuda_fail(e, #expr)); \
+  } while (0)
+  GS_CKC(cudaMemsetAsync(f->counters, 0, 8 * sizeof(unsigned long long), st));
+  // candidates (possibly visible surfels) in index order; only they are sorted
+  uint32_t* ncand = reinterpret_cast<uint32_t*>(f->counters + 6);
+  f->ncand = ncand;
+  GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, f->cand, ncand, f->geom,
+                           cnts, rtmp + radix_tmp_words(n), st));
+  uint32_t *skey = dkey, *sidx = idx;
+  GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st, ncand));
+  GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st, ncand));
+  GS_CKC(launch_scan(cnts, offs, n, total, rtmp + radix_tmp_words(n), st, ncand));
+  uint32_t Kh = 0;
+  GS_CKC(cudaMemcpyAsync(&Kh, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  GS_CKC(cudaStreamSynchronize(st));
+  const int64_t K = Kh;
+  if (K >= (int64_t(1) << 31)) return failed(fail(GS_ERR_CAPACITY, std::string(who) + ": more than 2^31 tile instances"));
+  f->K = K;
+  uint32_t* keys = tmp.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* vals = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* keys2 = tmp.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* vals2 = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* ktmp = tmp.get<uint32_t>(radix_tmp_words(K), st);
+  if (!keys || !vals || !keys2 || !vals2 || !ktmp)
+    return failed(fail(GS_ERR_OOM, std::string(who) + ": device allocation failed (tile lists)"));
+  const float rf = (float)sqrt((double)sc->settings.rho_max / (double)sc->settings.screen_inv_sigma2);
+  GS_CKC(launch_emit(sidx, offs, cnts, f->rect, f->geom, rf, n, cam.tiles_x, keys, vals, st, ncand));
+  uint32_t *tk = keys, *tv = vals;
+  GS_CKC(radix_sort_pairs(keys, vals, keys2, vals2, K, bits_for(ntiles), ktmp, &tk, &tv, st));
+  f->vals = tv;
+  f->buf.release(tv == vals ? vals2 : vals, st);
+  GS_CKC(launch_ranges(tk, K, f->ranges, ntiles, st));
+  if (tile_order_supported(ntiles)) GS_CKC(launch_tile_order(f->ranges, ntiles, f->order, st));
+  else f->order = nullptr;  // natural tile order (the buffer stays owned by f->buf)
+#undef GS_CKC
+  tmp.release_all(st);
+  return GS_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 uint64_t gs_kernel_launches(void) { return gs2d::g_launches.load(); }
@@ -318,101 +430,80 @@ gs_status gs_frame_release(gs_frame* f, void* stream) {
 gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_contrib,
                     gs_frame** saved, void* stream) {
   if (saved) *saved = nullptr;
-  if (!sc || !c || !out) return fail(GS_ERR_ARG, "gs_render: null argument");
-  if (c->width <= 0 || c->height <= 0 || c->width > 16 * 65535 || c->height > 16 * 65535)
-    return fail(GS_ERR_ARG, "gs_render: bad image size");
-  if (!(c->fx > 0) || !(c->fy > 0)) return fail(GS_ERR_ARG, "gs_render: focal lengths must be > 0");
+  if (!out) return fail(GS_ERR_ARG, "gs_render: null argument");
+  gs_status s = GS_OK;
+  gs_frame* f = new_frame(sc, c, out, "gs_render", &s);
+  if (!f) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  gs_frame* f = new (std::nothrow) gs_frame();
-  if (!f) return fail(GS_ERR_OOM, "gs_render: host allocation");
-  f->scene = sc;
-  f->n = sc->P.n;
-  f->sh_degree = sc->P.sh_degree;
-  f->out = out;
-  f->buf.al = &sc->al;
-  CamDev& cam = f->cam;
-  cam_from(*c, cam);
-  const int ntiles = cam.tiles_x * cam.tiles_y;
-  const int64_t n = f->n;
-  const SetDev set = to_dev(sc->settings);
-  Buffers tmp;
-  tmp.al = &sc->al;
-  auto cleanup = [&](gs_status s) {
-    tmp.release_all(st);
+  f->last = f->buf.get<int32_t>((size_t)f->cam.W * f->cam.H, st);
+  f->med = f->buf.get<int32_t>((size_t)f->cam.W * f->cam.H, st);
+  if (!f->last || !f->med) {
+    gs_frame_release(f, stream);
+    return fail(GS_ERR_OOM, "gs_render: device allocation failed");
+  }
+  s = build_lists(sc, f, "gs_render", st);
+  if (s == GS_OK) {
+    const cudaError_t e = launch_blend_fwd(f->cam, to_dev(sc->settings), f->order, f->rec, f->geom, f->vals,
+                                           f->ranges, out, n_contrib, f->last, f->med, f->counters, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "gs_render: blend");
+  }
+  if (s != GS_OK || !saved) {
     gs_frame_release(f, stream);
     return s;
-  };
-  // per-surfel buffers
-  f->rec = f->buf.get<float4>((size_t)(n > 0 ? n : 1) * kRecF4, st);
-  f->rect = f->buf.get<uint2>(n > 0 ? n : 1, st);
-  f->tcount = f->buf.get<uint32_t>(n > 0 ? n : 1, st);
-  f->ranges = f->buf.get<int2>(ntiles, st);
-  f->order = f->buf.get<uint32_t>(ntiles, st);
-  f->last = f->buf.get<int32_t>((size_t)cam.W * cam.H, st);
-  f->med = f->buf.get<int32_t>((size_t)cam.W * cam.H, st);
-  f->counters = f->buf.get<unsigned long long>(8, st);
-  uint32_t* dkey = tmp.get<uint32_t>(n > 0 ? n : 1, st);
-  uint32_t* idx = tmp.get<uint32_t>(n > 0 ? n : 1, st);
-  uint32_t* dkey2 = tmp.get<uint32_t>(n > 0 ? n : 1, st);
-  uint32_t* idx2 = tmp.get<uint32_t>(n > 0 ? n : 1, st);
-  uint32_t* cnts = tmp.get<uint32_t>(n > 0 ? n : 1, st);
-  uint32_t* offs = tmp.get<uint32_t>(n > 0 ? n : 1, st);
-  uint32_t* rtmp = tmp.get<uint32_t>(radix_tmp_words(n) + scan_tmp_words(n) + 4, st);
-  uint32_t* cand = f->buf.get<uint32_t>(n > 0 ? n : 1, st);
-  f->cand = cand;
-  RowGeom* geom = f->buf.get<RowGeom>(n > 0 ? n : 1, st);
-  f->geom = geom;
-  if (!f->rec || !f->rect || !f->tcount || !f->ranges || !f->order || !f->last || !f->med || !f->counters || !dkey ||
-      !idx || !dkey2 || !idx2 || !cnts || !offs || !rtmp || !cand || !geom)
-    return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed"));
-  uint32_t* total = rtmp + radix_tmp_words(n) + scan_tmp_words(n);
-  cudaError_t e;
-#define GS_CKC(expr)                                          \
-  do {                                                        \
-    e = (expr);                                               \
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, #expr)); \
-  } while (0)
-  GS_CKC(cudaMemsetAsync(f->counters, 0, 8 * sizeof(unsigned long long), st));
-  // candidates (possibly visible surfels) in index order; only they are sorted
-  uint32_t* ncand = reinterpret_cast<uint32_t*>(f->counters + 6);
-  f->ncand = ncand;
-  GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, cand, ncand, geom,
-                           cnts, rtmp + radix_tmp_words(n), st));
-  uint32_t *skey = dkey, *sidx = idx;
-  GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st, ncand));
-  GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st, ncand));
-  GS_CKC(launch_scan(cnts, offs, n, total, rtmp + radix_tmp_words(n), st, ncand));
-  uint32_t Kh = 0;
-  GS_CKC(cudaMemcpyAsync(&Kh, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  GS_CKC(cudaStreamSynchronize(st));
-  const int64_t K = Kh;
-  if (K >= (int64_t(1) << 31)) return cleanup(fail(GS_ERR_CAPACITY, "gs_render: more than 2^31 tile instances"));
-  f->K = K;
-  uint32_t* keys = tmp.get<uint32_t>(K > 0 ? K : 1, st);
-  uint32_t* vals = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
-  uint32_t* keys2 = tmp.get<uint32_t>(K > 0 ? K : 1, st);
-  uint32_t* vals2 = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
-  uint32_t* ktmp = tmp.get<uint32_t>(radix_tmp_words(K), st);
-  if (!keys || !vals || !keys2 || !vals2 || !ktmp)
-    return cleanup(fail(GS_ERR_OOM, "gs_render: device allocation failed (tile lists)"));
-  const float rf = (float)sqrt((double)sc->settings.rho_max / (double)sc->settings.screen_inv_sigma2);
-  GS_CKC(launch_emit(sidx, offs, cnts, f->rect, geom, rf, n, cam.tiles_x, keys, vals, st, ncand));
-  uint32_t *tk = keys, *tv = vals;
-  GS_CKC(radix_sort_pairs(keys, vals, keys2, vals2, K, bits_for(ntiles), ktmp, &tk, &tv, st));
-  f->vals = tv;
-  f->buf.release(tv == vals ? vals2 : vals, st);
-  GS_CKC(launch_ranges(tk, K, f->ranges, ntiles, st));
-  if (tile_order_supported(ntiles)) GS_CKC(launch_tile_order(f->ranges, ntiles, f->order, st));
-  else f->order = nullptr;  // natural tile order (the buffer stays owned by f->buf)
-  GS_CKC(launch_blend_fwd(cam, set, f->order, f->rec, f->geom, f->vals, f->ranges, out, n_contrib, f->last,
-                          f->med, f->counters, st));
-#undef GS_CKC
-  tmp.release_all(st);
-  if (saved) {
-    *saved = f;
-  } else {
-    gs_frame_release(f, stream);
   }
+  *saved = f;
+  return GS_OK;
+}
+
+gs_status gs_contribution(gs_scene* sc, const gs_camera* c, float gamma, float weight, float* contrib,
+                          float* view_sum, uint32_t* view_count, void* stream) {
+  if (!contrib && !view_sum && !view_count) return fail(GS_ERR_ARG, "gs_contribution: no output");
+  if (!(gamma >= 0.f && gamma <= 1.f)) return fail(GS_ERR_ARG, "gs_contribution: gamma must be in [0, 1]");
+  gs_status s = GS_OK;
+  gs_frame* f = new_frame(sc, c, nullptr, "gs_contribution", &s);
+  if (!f) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = f->n;
+  // per-view sums and support counts: the caller's arrays (overwritten, zero
+  // outside the candidates) or scratch (zeroed for the candidates only)
+  float* csum = view_sum ? view_sum : f->buf.get<float>(n > 0 ? n : 1, st);
+  uint32_t* ccnt = view_count ? view_count : f->buf.get<uint32_t>(n > 0 ? n : 1, st);
+  if (!csum || !ccnt) {
+    gs_frame_release(f, stream);
+    return fail(GS_ERR_OOM, "gs_contribution: device allocation failed");
+  }
+  cudaError_t e = cudaSuccess;
+  if (view_sum && n > 0) e = cudaMemsetAsync(view_sum, 0, sizeof(float) * (size_t)n, st);
+  if (e == cudaSuccess && view_count && n > 0) e = cudaMemsetAsync(view_count, 0, sizeof(uint32_t) * (size_t)n, st);
+  if (e != cudaSuccess) {
+    gs_frame_release(f, stream);
+    return cuda_fail(e, "gs_contribution");
+  }
+  s = build_lists(sc, f, "gs_contribution", st);
+  if (s == GS_OK) {
+    const bool zero_cand = !view_sum || !view_count;
+    e = launch_contribution(f->cam, to_dev(sc->settings), gamma, weight, f->order, f->rec, f->geom, f->vals,
+                            f->ranges, f->cand, f->ncand, n, zero_cand, csum, ccnt, contrib, st);
+    if (e != cudaSuccess) s = cuda_fail(e, "gs_contribution");
+  }
+  gs_frame_release(f, stream);
+  return s;
+}
+
+gs_status gs_prune_by_contribution(int64_t n, const float* contrib, double ratio, uint8_t* keep, float* bound,
+                                   void* stream) {
+  if (n < 0 || (n > 0 && (!contrib || !keep))) return fail(GS_ERR_ARG, "gs_prune_by_contribution: bad argument");
+  if (!(ratio >= 0.0 && ratio <= 1.0)) return fail(GS_ERR_ARG, "gs_prune_by_contribution: ratio must be in [0, 1]");
+  const double kd = ceil(ratio * (double)n);
+  const int64_t k = kd < 0.0 ? 0 : (kd > (double)n ? n : (int64_t)kd);
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  uint32_t* tmp = static_cast<uint32_t*>(al.get(select_tmp_words() * sizeof(uint32_t), st));
+  if (!tmp) return fail(GS_ERR_OOM, "gs_prune_by_contribution: scratch allocation failed");
+  const cudaError_t e = launch_prune(n, contrib, k, keep, bound, tmp, st);
+  al.put(tmp, 0, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_prune_by_contribution");
   return GS_OK;
 }
 

@@ -630,6 +630,98 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Trim contribution (Sec. 3.3, Eq. 3).
+//
+// The tiles of the render walk their lists front to back as the forward
+// does, with the forward's decisions (same evaluation, same transmittance
+// sequence), but every pixel goes through the whole list: a pair that lies
+// in the surfel's support (rho <= rho_max) counts towards |P_k| even behind
+// the pixel's stop.  A blended pair adds alpha^gamma T^(1 - gamma), T the
+// transmittance in front of it.  Per entry the warp counts its support
+// pixels with ballots and sums its contributions with shuffles; the tile sums
+// them in shared memory and adds them to the surfel's totals once.
+
+__device__ __forceinline__ float contrib_step(float& T, bool& stopped, const Pair& q, const SetDev& set,
+                                              float gamma) {
+  float c = 0.f;
+  if (!stopped && q.hit) {
+    const float Tn = T * (1.f - q.alpha);
+    if (Tn < set.T_min) {
+      stopped = true;
+    } else {
+      c = gamma == 0.5f ? sqrtf(q.alpha * T) : exp2f(gamma * log2f(q.alpha) + (1.f - gamma) * log2f(T));
+      T = Tn;
+    }
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
+    CamDev cam, SetDev set, float rf, float gamma, const uint32_t* __restrict__ order,
+    const float4* __restrict__ rec, const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals,
+    const int2* __restrict__ ranges, float* __restrict__ csum, uint32_t* __restrict__ ccnt) {
+  __shared__ float4 s0[kBatch], s1[kBatch], s2[kBatch];
+  __shared__ uint32_t sm[kBatch], sid[kBatch];
+  __shared__ float asum[kBatch];
+  __shared__ uint32_t acnt[kBatch];
+  const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+  const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
+  const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
+  const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
+  const bool inA = px < cam.W && pyA < cam.H, inB = px < cam.W && pyB < cam.H;
+  const int2 rg = ranges[tile];
+  const int len = rg.y - rg.x;
+  float TA = 1.f, TB = 1.f;
+  bool stA = !inA, stB = !inB;
+  for (int b0 = 0; b0 < len; b0 += kBatch) {
+    const int nb = min(kBatch, len - b0);
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < kBatch / kThreads; ++h) {
+      const int t = threadIdx.x + h * kThreads;
+      if (t < nb) {
+        const uint32_t sidx = vals[rg.x + b0 + t];
+        const Staged e = stage_entry(rec, geom, sidx, tx0, ty0, cam.H, rf);
+        s0[t] = e.s0;
+        s1[t] = e.s1;
+        s2[t] = e.s2;
+        sm[t] = e.wmask;
+        sid[t] = sidx;
+        asum[t] = 0.f;
+        acnt[t] = 0u;
+      }
+    }
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+      if (!((sm[k] >> warp) & 1u)) continue;  // footprint misses this warp's block
+      const float4 e0 = s0[k], e1 = s1[k], e2 = s2[k];
+      const Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
+      const Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+      const unsigned ba = __ballot_sync(0xffffffffu, inA && qa.rho <= set.rho_max);
+      const unsigned bb = __ballot_sync(0xffffffffu, inB && qb.rho <= set.rho_max);
+      const uint32_t cnt = (uint32_t)(__popc(ba) + __popc(bb));
+      float c = contrib_step(TA, stA, qa, set, gamma) + contrib_step(TB, stB, qb, set, gamma);
+      if (cnt == 0u) continue;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if (lane == 0) {
+        atomicAdd(&acnt[k], cnt);
+        if (c != 0.f) atomicAdd(&asum[k], c);
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb; t += kThreads) {
+      if (acnt[t] != 0u) {
+        atomicAdd(&ccnt[sid[t]], acnt[t]);
+        if (asum[t] != 0.f) atomicAdd(&csum[sid[t]], asum[t]);
+      }
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
@@ -670,6 +762,18 @@ cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const uint32_
   else
     blend_bwd_kernel<false><<<grid, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out, last,
                                                        med, adj, grec, screen, n, counters);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend_contrib(const CamDev& cam, const SetDev& set, float gamma, const uint32_t* order,
+                                 const float4* rec, const RowGeom* geom, const uint32_t* vals,
+                                 const int2* ranges, float* csum, uint32_t* ccnt, cudaStream_t st) {
+  const unsigned grid = (unsigned)cam.tiles_x * (unsigned)cam.tiles_y;
+  const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
+  ProfScope ps(kProfContrib, st);
+  blend_contrib_kernel<<<grid, kThreads, 0, st>>>(cam, set, rf, gamma, order, rec, geom, vals, ranges, csum,
+                                                  ccnt);
   count_launch();
   return cudaGetLastError();
 }

@@ -226,6 +226,28 @@ cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const uint32_
                              float* grec, float* screen, int n, unsigned long long* counters,
                              cudaStream_t st);
 
+// Trim contribution (Sec. 3.3, Eq. 3) of one view over the frame's tile
+// lists: per surfel the support count and the sum of alpha^gamma T^(1-gamma)
+// (csum, ccnt: [N], accumulated).
+cudaError_t launch_blend_contrib(const CamDev& cam, const SetDev& set, float gamma, const uint32_t* order,
+                                 const float4* rec, const RowGeom* geom, const uint32_t* vals,
+                                 const int2* ranges, float* csum, uint32_t* ccnt, cudaStream_t st);
+// Zero the candidates' csum/ccnt (when zero_cand), run the contribution blend
+// and add weight * csum / ccnt to contrib[n] for the candidates (contrib may
+// be null).
+cudaError_t launch_contribution(const CamDev& cam, const SetDev& set, float gamma, float weight,
+                                const uint32_t* order, const float4* rec, const RowGeom* geom,
+                                const uint32_t* vals, const int2* ranges, const uint32_t* cand,
+                                const uint32_t* ncand, int64_t n, bool zero_cand, float* csum, uint32_t* ccnt,
+                                float* contrib, cudaStream_t st);
+// Percentile pruning (Sec. 3.3): the k-th smallest value of contrib (k >= 1;
+// radix select on order-preserving keys), keep[i] = contrib[i] > it, the
+// bound to *bound (device, may be null); k = 0 keeps everything and writes
+// -inf.  tmp: select_tmp_words() words.
+size_t select_tmp_words();
+cudaError_t launch_prune(int64_t n, const float* contrib, int64_t k, uint8_t* keep, float* bound,
+                         uint32_t* tmp, cudaStream_t st);
+
 cudaError_t launch_preprocess_bwd(const ParamsDev& P, const CamDev& cam, const uint32_t* cand,
                                   const uint32_t* ncand, const uint32_t* tcount, const float* grec,
                                   const gs_param_grads& G, cudaStream_t st);
@@ -256,7 +278,8 @@ enum ProfId {
   kProfBlendBwd = 4,
   kProfPreprocessBwd = 5,
   kProfDensify = 6,
-  kProfCount = 7
+  kProfContrib = 7,
+  kProfCount = 8
 };
 void count_launch(int n = 1);
 void set_last_error(const char* msg);
