@@ -86,6 +86,22 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
   return e;
 }
 
+// Per warp, the batch's entries whose footprint may reach the warp's pixel
+// block, as kBatch / 32 bit words (ballots of the staged masks); the loops
+// below visit only their set bits, so entries that miss the block cost
+// nothing (long lists, where most entries miss a given block).
+constexpr int kWords = kBatch / 32;
+__device__ __forceinline__ void warp_entry_bits(const uint32_t* sm, int nb, int warp, int lane,
+                                                uint32_t* wb) {
+#pragma unroll
+  for (int j = 0; j < kWords; ++j) {
+    const int e = 32 * j + lane;
+    const uint32_t w = __ballot_sync(0xffffffffu, e < nb && ((sm[e] >> warp) & 1u));
+    if (lane == 0) wb[j] = w;
+  }
+  __syncwarp();
+}
+
 struct Pair {
   float dx, dy;    // pixel offset from the projected centre
   float nu, nv;    // Ji d
@@ -204,6 +220,7 @@ __device__ __forceinline__ void fwd_store(const FwdPix& p, const CamDev& cam, co
 struct FwdSmem {
   float4 s0[kBatch], s1[kBatch], s2[kBatch], s3[kBatch];
   uint32_t sm[kBatch];
+  uint32_t wbits[kThreads / 32][kWords];
   unsigned long long tot[2];
 };
 
@@ -240,13 +257,18 @@ __device__ __forceinline__ void blend_fwd_tile(
     }
     __syncthreads();
     const int nb = min(kBatch, len - b0);
-    for (int k = 0; k < nb && !(a.done && b.done); ++k) {
-      if (!((sh.sm[k] >> warp) & 1u)) continue;  // footprint misses this warp's block
-      const float4 e0 = sh.s0[k], e1 = sh.s1[k], e2 = sh.s2[k], e3 = sh.s3[k];
-      const Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
-      const Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
-      fwd_step(a, qa, e2, e3, b0 + k, set);
-      fwd_step(b, qb, e2, e3, b0 + k, set);
+    warp_entry_bits(sh.sm, nb, warp, threadIdx.x & 31, sh.wbits[warp]);
+    for (int j = 0; j < kWords && !(a.done && b.done); ++j) {
+      uint32_t bits = sh.wbits[warp][j];
+      while (bits != 0u && !(a.done && b.done)) {
+        const int k = 32 * j + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float4 e0 = sh.s0[k], e1 = sh.s1[k], e2 = sh.s2[k], e3 = sh.s3[k];
+        const Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
+        const Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+        fwd_step(a, qa, e2, e3, b0 + k, set);
+        fwd_step(b, qb, e2, e3, b0 + k, set);
+      }
     }
   }
   fwd_store(a, cam, set, px, pyA, out, n_contrib, last, med);
@@ -275,7 +297,7 @@ __device__ __forceinline__ void blend_fwd_tile(
 }
 
 // One CTA per tile; block b takes tile order[b] (longest lists first).
-__global__ void __launch_bounds__(kThreads) blend_fwd_kernel(
+__global__ void __launch_bounds__(kThreads, 5) blend_fwd_kernel(
     CamDev cam, SetDev set, float rf, const uint32_t* __restrict__ order, const float4* __restrict__ rec,
     const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
     float* __restrict__ out, int32_t* __restrict__ n_contrib, int32_t* __restrict__ last,
@@ -510,7 +532,7 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
 }
 
 template <bool kLoss>
-__global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
+__global__ void __launch_bounds__(kThreads, 5) blend_bwd_kernel(
     CamDev cam, SetDev set, float rf, const uint32_t* __restrict__ order, const float4* __restrict__ rec,
     const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
     const float* __restrict__ out, const int32_t* __restrict__ last, const int32_t* __restrict__ med,
@@ -522,6 +544,7 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
   __shared__ uint32_t sm[kBatch];
   __shared__ uint32_t sid[kBatch];
   __shared__ float acc[kBatch][kN + 1];
+  __shared__ uint32_t wbits[kThreads / 32][kWords];
   __shared__ int smax;
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
@@ -565,36 +588,42 @@ __global__ void __launch_bounds__(kThreads) blend_bwd_kernel(
     }
     for (int i = threadIdx.x; i < nb * (kN + 1); i += kThreads) (&acc[0][0])[i] = 0.f;
     __syncthreads();
-    for (int kk = nb - 1; kk >= 0; --kk) {
-      if (!((sm[kk] >> warp) & 1u)) continue;  // footprint misses this warp's block
-      const int k = b0 + kk;
-      const float4 e0 = s0[kk], e1 = s1[kk], e2 = s2[kk];
-      const bool liveA = k < a.last, liveB = k < b.last;
-      replayed += (unsigned)liveA + (unsigned)liveB;
-      Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
-      Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
-      mask_pair(qa, liveA);
-      mask_pair(qb, liveB);
-      const bool contrib = qa.hit || qb.hit;
-      const unsigned ballot = __ballot_sync(0xffffffffu, contrib);
-      if (ballot == 0u) continue;
-      ++wentries;
-      wlanes += __popc(ballot);
-      float v[kN];
-#pragma unroll
-      for (int i = 0; i < kN; ++i) v[i] = 0.f;
-      const float4 e3 = s3[kk];
-      bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
-      bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
-      if (__popc(ballot) == 1) {
-        if (contrib) {
-#pragma unroll
-          for (int i = 0; i < kN; ++i)
-            if (v[i] != 0.f) atomicAdd(&acc[kk][i], v[i]);
+    warp_entry_bits(sm, nb, warp, lane, wbits[warp]);
+    for (int j = kWords - 1; j >= 0; --j) {
+      uint32_t bits = wbits[warp][j];
+      while (bits != 0u) {  // back to front: highest set bit first
+        const int hb = 31 - __clz(bits);
+        bits &= ~(1u << hb);
+        const int kk = 32 * j + hb;
+        const int k = b0 + kk;
+        const float4 e0 = s0[kk], e1 = s1[kk], e2 = s2[kk];
+        const bool liveA = k < a.last, liveB = k < b.last;
+        replayed += (unsigned)liveA + (unsigned)liveB;
+        Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
+        Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+        mask_pair(qa, liveA);
+        mask_pair(qb, liveB);
+        const bool contrib = qa.hit || qb.hit;
+        const unsigned ballot = __ballot_sync(0xffffffffu, contrib);
+        if (ballot == 0u) continue;
+        ++wentries;
+        wlanes += __popc(ballot);
+        float v[kN];
+  #pragma unroll
+        for (int i = 0; i < kN; ++i) v[i] = 0.f;
+        const float4 e3 = s3[kk];
+        bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
+        bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
+        if (__popc(ballot) == 1) {
+          if (contrib) {
+  #pragma unroll
+            for (int i = 0; i < kN; ++i)
+              if (v[i] != 0.f) atomicAdd(&acc[kk][i], v[i]);
+          }
+        } else {
+          rs_level<16, kN>(v, lane);
+          if (myslot >= 0 && v[0] != 0.f) atomicAdd(&acc[kk][myslot], v[0]);
         }
-      } else {
-        rs_level<16, kN>(v, lane);
-        if (myslot >= 0 && v[0] != 0.f) atomicAdd(&acc[kk][myslot], v[0]);
       }
     }
     __syncthreads();
@@ -665,6 +694,7 @@ __global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
   __shared__ uint32_t sm[kBatch], sid[kBatch];
   __shared__ float asum[kBatch];
   __shared__ uint32_t acnt[kBatch];
+  __shared__ uint32_t wbits[kThreads / 32][kWords];
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
@@ -695,21 +725,26 @@ __global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
       }
     }
     __syncthreads();
-    for (int k = 0; k < nb; ++k) {
-      if (!((sm[k] >> warp) & 1u)) continue;  // footprint misses this warp's block
-      const float4 e0 = s0[k], e1 = s1[k], e2 = s2[k];
-      const Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
-      const Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
-      const unsigned ba = __ballot_sync(0xffffffffu, inA && qa.rho <= set.rho_max);
-      const unsigned bb = __ballot_sync(0xffffffffu, inB && qb.rho <= set.rho_max);
-      const uint32_t cnt = (uint32_t)(__popc(ba) + __popc(bb));
-      float c = contrib_step(TA, stA, qa, set, gamma) + contrib_step(TB, stB, qb, set, gamma);
-      if (cnt == 0u) continue;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-      if (lane == 0) {
-        atomicAdd(&acnt[k], cnt);
-        if (c != 0.f) atomicAdd(&asum[k], c);
+    warp_entry_bits(sm, nb, warp, lane, wbits[warp]);
+    for (int j = 0; j < kWords; ++j) {
+      uint32_t bits = wbits[warp][j];
+      while (bits != 0u) {
+        const int k = 32 * j + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float4 e0 = s0[k], e1 = s1[k], e2 = s2[k];
+        const Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
+        const Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+        const unsigned ba = __ballot_sync(0xffffffffu, inA && qa.rho <= set.rho_max);
+        const unsigned bb = __ballot_sync(0xffffffffu, inB && qb.rho <= set.rho_max);
+        const uint32_t cnt = (uint32_t)(__popc(ba) + __popc(bb));
+        float c = contrib_step(TA, stA, qa, set, gamma) + contrib_step(TB, stB, qb, set, gamma);
+        if (cnt == 0u) continue;
+  #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) {
+          atomicAdd(&acnt[k], cnt);
+          if (c != 0.f) atomicAdd(&asum[k], c);
+        }
       }
     }
     __syncthreads();
