@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <mutex>
@@ -328,6 +329,47 @@ gs_status build_lists(gs_scene* sc, gs_frame* f, const char* who, cudaStream_t s
   return GS_OK;
 }
 
+// The forward blend of a built frame.  An image with too few tiles to fill
+// the GPU (under two waves of five CTAs per SM) has its long tile lists
+// composited in segments of lseg entries, lseg chosen so that the segments
+// make about two waves.
+gs_status blend_forward(gs_scene* sc, gs_frame* f, float* out, int32_t* n_contrib, cudaStream_t st) {
+  const CamDev& cam = f->cam;
+  const SetDev set = to_dev(sc->settings);
+  const int ntiles = cam.tiles_x * cam.tiles_y;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e;
+  SegBufs sb;
+  sb.lseg = split_lseg(ntiles, f->K, sms);
+  if (sb.lseg == 0) {
+    e = launch_blend_fwd(cam, set, f->order, f->rec, f->geom, f->vals, f->ranges, out, n_contrib, f->last, f->med,
+                         f->counters, st);
+    return e == cudaSuccess ? GS_OK : cuda_fail(e, "gs_render: blend");
+  }
+  const int64_t nmax = split_nseg_max(f->K, sb.lseg);
+  sb.nseg_max = (unsigned)nmax;
+  Buffers tmp;
+  tmp.al = &sc->al;
+  sb.segcnt = tmp.get<uint32_t>(ntiles, st);
+  sb.segoff = tmp.get<uint32_t>(ntiles, st);
+  sb.nseg = tmp.get<uint32_t>(1, st);
+  sb.scan_tmp = tmp.get<uint32_t>(scan_tmp_words(ntiles), st);
+  sb.seg_tile = tmp.get<uint32_t>(nmax, st);
+  sb.seg_idx = tmp.get<uint32_t>(nmax, st);
+  sb.trans = tmp.get<float>((size_t)nmax * 256, st);
+  sb.part = tmp.get<unsigned char>((size_t)nmax * 256 * seg_part_bytes(), st);
+  if (!sb.segcnt || !sb.segoff || !sb.nseg || !sb.scan_tmp || !sb.seg_tile || !sb.seg_idx || !sb.trans || !sb.part) {
+    tmp.release_all(st);
+    return fail(GS_ERR_OOM, "gs_render: device allocation failed (segments)");
+  }
+  e = launch_blend_fwd_split(cam, set, f->order, f->rec, f->geom, f->vals, f->ranges, out, n_contrib, f->last,
+                             f->med, f->counters, sb, st);
+  tmp.release_all(st);
+  return e == cudaSuccess ? GS_OK : cuda_fail(e, "gs_render: blend");
+}
+
 }  // namespace
 
 extern "C" {
@@ -442,11 +484,7 @@ gs_status gs_render(gs_scene* sc, const gs_camera* c, float* out, int32_t* n_con
     return fail(GS_ERR_OOM, "gs_render: device allocation failed");
   }
   s = build_lists(sc, f, "gs_render", st);
-  if (s == GS_OK) {
-    const cudaError_t e = launch_blend_fwd(f->cam, to_dev(sc->settings), f->order, f->rec, f->geom, f->vals,
-                                           f->ranges, out, n_contrib, f->last, f->med, f->counters, st);
-    if (e != cudaSuccess) s = cuda_fail(e, "gs_render: blend");
-  }
+  if (s == GS_OK) s = blend_forward(sc, f, out, n_contrib, st);
   if (s != GS_OK || !saved) {
     gs_frame_release(f, stream);
     return s;

@@ -163,6 +163,7 @@ __device__ __forceinline__ void fwd_init(FwdPix& p, bool inside) {
 // Branch-free, so that the two pixels of a thread interleave: a pair that is
 // not blended updates the sums with weight 0 (and a finite depth of 1), which
 // leaves them unchanged.
+template <bool kFixedRef = false>
 __device__ __forceinline__ void fwd_step(FwdPix& p, const Pair& q, float4 e2, float4 e3, int pos,
                                          const SetDev& set) {
   p.evaluated += p.done ? 0u : 1u;
@@ -176,7 +177,7 @@ __device__ __forceinline__ void fwd_step(FwdPix& p, const Pair& q, float4 e2, fl
   p.C0 = fmaf(w, e2.z, p.C0);
   p.C1 = fmaf(w, e2.w, p.C1);
   p.C2 = fmaf(w, e3.x, p.C2);
-  p.zr = (bl && p.cnt == 0) ? z : p.zr;
+  if constexpr (!kFixedRef) p.zr = (bl && p.cnt == 0) ? z : p.zr;
   const float zs = z - p.zr;
   p.D = fmaf(2.f * w, fmaf(zs, p.A, -p.Zs), p.D);
   p.A += w;
@@ -229,7 +230,7 @@ __device__ __forceinline__ void blend_fwd_tile(
     FwdSmem& sh, const CamDev& cam, const SetDev& set, float rf, const float4* __restrict__ rec,
     const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
     float* __restrict__ out, int32_t* __restrict__ n_contrib, int32_t* __restrict__ last,
-    int32_t* __restrict__ med, unsigned long long* __restrict__ counters, int bx, int by) {
+    int32_t* __restrict__ med, unsigned long long* __restrict__ counters, int bx, int by, int lseg = 0) {
   const int tile = by * cam.tiles_x + bx;
   const int tx0 = bx * kTile, ty0 = by * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
@@ -238,6 +239,7 @@ __device__ __forceinline__ void blend_fwd_tile(
   const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
   const int2 rg = ranges[tile];
   const int len = rg.y - rg.x;
+  if (lseg > 0 && len > lseg) return;  // a long list: composited in segments
   FwdPix a, b;
   fwd_init(a, px < cam.W && pyA < cam.H);
   fwd_init(b, px < cam.W && pyB < cam.H);
@@ -301,11 +303,250 @@ __global__ void __launch_bounds__(kThreads, 5) blend_fwd_kernel(
     CamDev cam, SetDev set, float rf, const uint32_t* __restrict__ order, const float4* __restrict__ rec,
     const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
     float* __restrict__ out, int32_t* __restrict__ n_contrib, int32_t* __restrict__ last,
-    int32_t* __restrict__ med, unsigned long long* __restrict__ counters) {
+    int32_t* __restrict__ med, unsigned long long* __restrict__ counters, int lseg) {
   __shared__ FwdSmem sh;
   const int t = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   blend_fwd_tile(sh, cam, set, rf, rec, geom, vals, ranges, out, n_contrib, last, med, counters,
-                 t % cam.tiles_x, t / cam.tiles_x);
+                 t % cam.tiles_x, t / cam.tiles_x, lseg);
+}
+
+// ---------------------------------------------------------------------------
+// Long lists, composited in segments.
+//
+// When an image has too few tiles to fill the GPU and some tiles carry long
+// lists (a small view of a large scene), a tile's list is cut into segments
+// of lseg entries that separate CTAs process:
+//   1. seg_trans_kernel: per segment and pixel, the product of (1 - alpha)
+//      over the segment's pairs that pass the support and cutoff tests (no
+//      stop);
+//   2. seg_blend_kernel: per segment, the pixel enters with the product of
+//      the segments in front (the transmittance it would have there had
+//      nothing stopped) and composites the segment with the forward's rules,
+//      the stop included.  A pixel that stopped in an earlier segment enters
+//      below T_min and blends nothing;
+//   3. seg_merge_kernel: per tile and pixel, the segments are combined in
+//      order.  Sums add; the distortion adds the cross terms
+//      2 (A_front Zs_seg - Zs_front A_seg) (depths relative to one reference,
+//      the tile's first centre depth); the median comes from the last
+//      segment that has one; T and the stop from the segment where blending
+//      ended.
+// The result equals the one-CTA compositing up to the rounding of T's
+// products (decisions within a hair of a threshold may differ).
+
+struct SegPart {
+  float4 f0;  // C0, C1, C2, A
+  float4 f1;  // Zs (relative to the reference), I, N0, N1
+  float4 f2;  // N2, D, M, T after the segment
+  int4 f3;    // median position, count, last position, stopped
+};
+
+// Segment b of the split tiles: its tile and its index within the tile.
+__device__ __forceinline__ bool seg_of(const uint32_t* seg_tile, const uint32_t* seg_idx, const uint32_t* nseg,
+                                       int b, int* tile, int* s) {
+  if ((uint32_t)b >= *nseg) return false;
+  *tile = (int)seg_tile[b];
+  *s = (int)seg_idx[b];
+  return true;
+}
+
+// Stage entries [b0, b0 + nb) of the tile's list (shared by the segment kernels).
+__device__ __forceinline__ void stage_batch(FwdSmem& sh, const float4* __restrict__ rec,
+                                            const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals,
+                                            int base, int nb, int tx0, int ty0, int H, float rf) {
+#pragma unroll
+  for (int h = 0; h < kBatch / kThreads; ++h) {
+    const int t = threadIdx.x + h * kThreads;
+    if (t < nb) {
+      const Staged e = stage_entry(rec, geom, vals[base + t], tx0, ty0, H, rf);
+      sh.s0[t] = e.s0;
+      sh.s1[t] = e.s1;
+      sh.s2[t] = e.s2;
+      sh.s3[t] = e.s3;
+      sh.sm[t] = e.wmask;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) seg_trans_kernel(
+    CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
+    const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, int lseg,
+    const uint32_t* __restrict__ seg_tile, const uint32_t* __restrict__ seg_idx, const uint32_t* __restrict__ nseg,
+    float* __restrict__ trans) {
+  __shared__ FwdSmem sh;
+  int tile, s;
+  if (!seg_of(seg_tile, seg_idx, nseg, blockIdx.x, &tile, &s)) return;
+  const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
+  const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
+  const int warp = threadIdx.x >> 5;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
+  const int2 rg = ranges[tile];
+  const int e0 = s * lseg, e1 = min(rg.y - rg.x, e0 + lseg);
+  float TA = 1.f, TB = 1.f;
+  for (int b0 = e0; b0 < e1; b0 += kBatch) {
+    const int nb = min(kBatch, e1 - b0);
+    __syncthreads();
+    stage_batch(sh, rec, geom, vals, rg.x + b0, nb, tx0, ty0, cam.H, rf);
+    __syncthreads();
+    warp_entry_bits(sh.sm, nb, warp, threadIdx.x & 31, sh.wbits[warp]);
+    for (int j = 0; j < kWords; ++j) {
+      uint32_t bits = sh.wbits[warp][j];
+      while (bits != 0u) {
+        const int k = 32 * j + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float4 f0 = sh.s0[k], f1 = sh.s1[k], f2 = sh.s2[k];
+        const Pair qa = eval_pair(lx, lyA, f0, f1, f2.y, set);
+        const Pair qb = eval_pair(lx, lyB, f0, f1, f2.y, set);
+        TA = qa.hit ? TA * (1.f - qa.alpha) : TA;
+        TB = qb.hit ? TB * (1.f - qb.alpha) : TB;
+      }
+    }
+  }
+  trans[(size_t)blockIdx.x * kBatch + threadIdx.x] = TA;
+  trans[(size_t)blockIdx.x * kBatch + kThreads + threadIdx.x] = TB;
+}
+
+__device__ __forceinline__ void seg_store(const FwdPix& p, bool inside, SegPart* __restrict__ part, int slot) {
+  SegPart q;
+  q.f0 = make_float4(p.C0, p.C1, p.C2, p.A);
+  q.f1 = make_float4(p.Zs, p.I, p.N0, p.N1);
+  q.f2 = make_float4(p.N2, p.D, p.M, p.T);
+  q.f3 = make_int4(p.medpos, p.cnt, p.lastpos, (inside && p.done) ? 1 : 0);
+  part[slot] = q;
+}
+
+__global__ void __launch_bounds__(kThreads) seg_blend_kernel(
+    CamDev cam, SetDev set, float rf, const float4* __restrict__ rec, const RowGeom* __restrict__ geom,
+    const uint32_t* __restrict__ vals, const int2* __restrict__ ranges, int lseg,
+    const uint32_t* __restrict__ seg_tile, const uint32_t* __restrict__ seg_idx, const uint32_t* __restrict__ nseg,
+    const float* __restrict__ trans, SegPart* __restrict__ part, unsigned long long* __restrict__ counters) {
+  __shared__ FwdSmem sh;
+  int tile, s;
+  if (!seg_of(seg_tile, seg_idx, nseg, blockIdx.x, &tile, &s)) return;
+  const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
+  const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
+  const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
+  const int warp = threadIdx.x >> 5;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
+  const int2 rg = ranges[tile];
+  const int e0 = s * lseg, e1 = min(rg.y - rg.x, e0 + lseg);
+  const bool inA = px < cam.W && pyA < cam.H, inB = px < cam.W && pyB < cam.H;
+  FwdPix a, b;
+  fwd_init(a, inA);
+  fwd_init(b, inB);
+  // transmittance in front: the segments before this one (contiguous)
+  const int first = (int)blockIdx.x - s;
+  for (int q = 0; q < s; ++q) {
+    a.T *= trans[(size_t)(first + q) * kBatch + threadIdx.x];
+    b.T *= trans[(size_t)(first + q) * kBatch + kThreads + threadIdx.x];
+  }
+  const float zref = rec[(size_t)vals[rg.x] * kRecF4 + 2].z;  // the tile's first centre depth
+  a.zr = zref;
+  b.zr = zref;
+  for (int b0 = e0; b0 < e1; b0 += kBatch) {
+    if (__syncthreads_count(a.done && b.done) == kThreads) break;
+    const int nb = min(kBatch, e1 - b0);
+    stage_batch(sh, rec, geom, vals, rg.x + b0, nb, tx0, ty0, cam.H, rf);
+    __syncthreads();
+    warp_entry_bits(sh.sm, nb, warp, threadIdx.x & 31, sh.wbits[warp]);
+    for (int j = 0; j < kWords && !(a.done && b.done); ++j) {
+      uint32_t bits = sh.wbits[warp][j];
+      while (bits != 0u && !(a.done && b.done)) {
+        const int k = 32 * j + __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const float4 f0 = sh.s0[k], f1 = sh.s1[k], f2 = sh.s2[k], f3 = sh.s3[k];
+        const Pair qa = eval_pair(lx, lyA, f0, f1, f2.y, set);
+        const Pair qb = eval_pair(lx, lyB, f0, f1, f2.y, set);
+        fwd_step<true>(a, qa, f2, f3, b0 + k, set);
+        fwd_step<true>(b, qb, f2, f3, b0 + k, set);
+      }
+    }
+  }
+  SegPart* pp = part + (size_t)blockIdx.x * kBatch;
+  seg_store(a, inA, pp, threadIdx.x);
+  seg_store(b, inB, pp, kThreads + threadIdx.x);
+  if (counters) {
+    unsigned e = a.evaluated + b.evaluated, c = (unsigned)(a.cnt + b.cnt);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&counters[0], (unsigned long long)e);
+      atomicAdd(&counters[1], (unsigned long long)c);
+    }
+  }
+}
+
+// Combine the segments of one pixel in order (slot = its index within the
+// segment records).
+__device__ __forceinline__ FwdPix seg_merge_pixel(const SegPart* __restrict__ part, int first, int nseg_tile,
+                                                  int slot, float zref) {
+  FwdPix p;
+  fwd_init(p, true);
+  p.zr = zref;
+  bool stopped = false;
+  for (int q = 0; q < nseg_tile && !stopped; ++q) {
+    const SegPart g = part[(size_t)(first + q) * kBatch + slot];
+    p.C0 += g.f0.x;
+    p.C1 += g.f0.y;
+    p.C2 += g.f0.z;
+    p.D += g.f2.y + 2.f * (p.A * g.f1.x - p.Zs * g.f0.w);
+    p.A += g.f0.w;
+    p.Zs += g.f1.x;
+    p.I += g.f1.y;
+    p.N0 += g.f1.z;
+    p.N1 += g.f1.w;
+    p.N2 += g.f2.x;
+    if (g.f3.x >= 0) {
+      p.M = g.f2.z;
+      p.medpos = g.f3.x;
+    }
+    if (g.f3.y > 0) p.lastpos = g.f3.z;
+    p.cnt += g.f3.y;
+    p.T = g.f2.w;
+    stopped = g.f3.w != 0;
+  }
+  return p;
+}
+
+__global__ void __launch_bounds__(kThreads) seg_merge_kernel(
+    CamDev cam, SetDev set, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const int2* __restrict__ ranges, const uint32_t* __restrict__ segcnt, const uint32_t* __restrict__ seg_tile,
+    const uint32_t* __restrict__ seg_idx, const uint32_t* __restrict__ nseg, const SegPart* __restrict__ part,
+    float* __restrict__ out, int32_t* __restrict__ n_contrib, int32_t* __restrict__ last,
+    int32_t* __restrict__ med) {
+  int tile, s;
+  if (!seg_of(seg_tile, seg_idx, nseg, blockIdx.x, &tile, &s) || s != 0) return;
+  const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
+  const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
+  const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
+  const int2 rg = ranges[tile];
+  const float zref = rec[(size_t)vals[rg.x] * kRecF4 + 2].z;
+  const int ns = (int)segcnt[tile];
+  const FwdPix a = seg_merge_pixel(part, blockIdx.x, ns, threadIdx.x, zref);
+  const FwdPix b = seg_merge_pixel(part, blockIdx.x, ns, kThreads + threadIdx.x, zref);
+  fwd_store(a, cam, set, px, pyA, out, n_contrib, last, med);
+  fwd_store(b, cam, set, px, pyB, out, n_contrib, last, med);
+}
+
+// Segments per tile (0 for tiles composited whole).
+__global__ void seg_count_kernel(const int2* __restrict__ ranges, int ntiles, int lseg, uint32_t* __restrict__ segcnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const int len = ranges[t].y - ranges[t].x;
+  segcnt[t] = len > lseg ? (uint32_t)((len + lseg - 1) / lseg) : 0u;
+}
+
+__global__ void seg_list_kernel(const uint32_t* __restrict__ segcnt, const uint32_t* __restrict__ segoff, int ntiles,
+                                uint32_t* __restrict__ seg_tile, uint32_t* __restrict__ seg_idx) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const uint32_t c = segcnt[t], o = segoff[t];
+  for (uint32_t q = 0; q < c; ++q) {
+    seg_tile[o + q] = (uint32_t)t;
+    seg_idx[o + q] = q;
+  }
 }
 
 // Persistent forward blend over the tiles of several views (serving): each
@@ -767,8 +1008,38 @@ cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const uint32_
   const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
   ProfScope ps(kProfBlendFwd, st);
   blend_fwd_kernel<<<grid, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out, n_contrib,
-                                              last, med, counters);
+                                              last, med, counters, 0);
   count_launch();
+  return cudaGetLastError();
+}
+
+size_t seg_part_bytes() { return sizeof(SegPart); }
+
+cudaError_t launch_blend_fwd_split(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
+                                   const RowGeom* geom, const uint32_t* vals, const int2* ranges, float* out,
+                                   int32_t* n_contrib, int32_t* last, int32_t* med, unsigned long long* counters,
+                                   const SegBufs& sb, cudaStream_t st) {
+  const int ntiles = cam.tiles_x * cam.tiles_y;
+  const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
+  ProfScope ps(kProfBlendFwd, st);
+  count_launch(2);
+  seg_count_kernel<<<div_up(ntiles, 256), 256, 0, st>>>(ranges, ntiles, sb.lseg, sb.segcnt);
+  cudaError_t e = launch_scan(sb.segcnt, sb.segoff, ntiles, sb.nseg, sb.scan_tmp, st);
+  if (e != cudaSuccess) return e;
+  seg_list_kernel<<<div_up(ntiles, 256), 256, 0, st>>>(sb.segcnt, sb.segoff, ntiles, sb.seg_tile, sb.seg_idx);
+  // the whole tiles, then the segments (grids sized for the bound, the device
+  // count decides)
+  count_launch(4);
+  blend_fwd_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out,
+                                                          n_contrib, last, med, counters, sb.lseg);
+  seg_trans_kernel<<<sb.nseg_max, kThreads, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, sb.lseg, sb.seg_tile,
+                                                     sb.seg_idx, sb.nseg, sb.trans);
+  seg_blend_kernel<<<sb.nseg_max, kThreads, 0, st>>>(cam, set, rf, rec, geom, vals, ranges, sb.lseg, sb.seg_tile,
+                                                     sb.seg_idx, sb.nseg, sb.trans,
+                                                     static_cast<SegPart*>(sb.part), counters);
+  seg_merge_kernel<<<sb.nseg_max, kThreads, 0, st>>>(cam, set, rec, vals, ranges, sb.segcnt, sb.seg_tile,
+                                                     sb.seg_idx, sb.nseg, static_cast<const SegPart*>(sb.part),
+                                                     out, n_contrib, last, med);
   return cudaGetLastError();
 }
 

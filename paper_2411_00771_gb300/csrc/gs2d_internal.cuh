@@ -189,6 +189,42 @@ cudaError_t launch_blend_fwd(const CamDev& cam, const SetDev& set, const uint32_
                              int32_t* n_contrib, int32_t* last, int32_t* med,
                              unsigned long long* counters, cudaStream_t st);
 
+// Long lists composited in segments (see blend.cu).  A tile whose list is
+// longer than lseg entries is cut into segments of lseg; the buffers hold up
+// to nseg_max segments (split_nseg_max bounds their number).
+struct SegBufs {
+  int lseg = 0;
+  unsigned nseg_max = 0;
+  uint32_t* segcnt = nullptr;    // [ntiles] segments per tile (0: whole)
+  uint32_t* segoff = nullptr;    // [ntiles] exclusive scan of segcnt
+  uint32_t* nseg = nullptr;      // [1] number of segments (device)
+  uint32_t* scan_tmp = nullptr;  // scan_tmp_words(ntiles)
+  uint32_t* seg_tile = nullptr;  // [nseg_max]
+  uint32_t* seg_idx = nullptr;   // [nseg_max]
+  float* trans = nullptr;        // [nseg_max][256]
+  void* part = nullptr;          // [nseg_max][256] records of seg_part_bytes()
+};
+size_t seg_part_bytes();
+// Segment length for a view of ntiles tiles and K instances on a GPU of sms
+// SMs, or 0 to composite whole tiles: views with fewer than two waves of
+// tiles (five CTAs per SM) and more than 1024 instances are split so that the
+// segments make about two waves (at least 1024 entries each).
+inline int split_lseg(int ntiles, int64_t K, int sms) {
+  const int64_t slots2 = 2 * (int64_t)sms * 5;
+  if (ntiles >= slots2 || K <= 1024) return 0;
+  const int64_t per = (K + slots2 - 1) / slots2;
+  const int64_t l = (per + 255) / 256 * 256;
+  return (int)(l < 1024 ? 1024 : l);
+}
+// Upper bound of the number of segments, the sum over the split tiles of
+// ceil(len / lseg): a split tile has len > lseg, so ceil(len / lseg) <
+// 2 len / lseg, and the lengths sum to at most K.
+inline int64_t split_nseg_max(int64_t K, int lseg) { return (2 * K + lseg - 1) / lseg; }
+cudaError_t launch_blend_fwd_split(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
+                                   const RowGeom* geom, const uint32_t* vals, const int2* ranges, float* out,
+                                   int32_t* n_contrib, int32_t* last, int32_t* med, unsigned long long* counters,
+                                   const SegBufs& sb, cudaStream_t st);
+
 // One view of a batched (serving) forward blend.
 struct BlendJob {
   CamDev cam;

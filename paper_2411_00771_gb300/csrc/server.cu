@@ -7,7 +7,10 @@
 //            host memory),
 //   stage B  instance buffers, emission, tile sort, tile ranges,
 //   blend    the views whose stage B has finished are blended together by
-//            one persistent launch over all their tiles (blend_fwd_batched).
+//            one persistent launch over all their tiles (blend_fwd_batched);
+//            a view with too few tiles to fill the GPU and long lists gets
+//            its own launches with the lists composited in segments, as
+//            gs_render does for it.
 // Requests that arrive while others are on the GPU enter as soon as a slot
 // and memory are free, so stages of different requests overlap on the
 // device.  Each slot keeps its buffers (per-surfel records, sort buffers,
@@ -76,6 +79,9 @@ struct Slot {
   Buf rec, geom, rect, tcount, dkey, idx, dkey2, idx2, cnts, offs, cand, rtmp;  // per surfel
   Buf keys, vals, keys2, vals2, ktmp;                                             // per instance
   Buf ranges;                                                                     // per tile
+  Buf seg_tiles, seg_list, seg_trans, seg_part;  // long lists composited in segments
+  int lseg = 0;                                  // 0: whole tiles
+  unsigned nseg_max = 0;
   // request-specific
   CamDev cam{};
   SetDev set{};
@@ -88,7 +94,8 @@ struct Slot {
   size_t bytes() const {
     return rec.bytes + geom.bytes + rect.bytes + tcount.bytes + dkey.bytes + idx.bytes + dkey2.bytes +
            idx2.bytes + cnts.bytes + offs.bytes + cand.bytes + rtmp.bytes + keys.bytes + vals.bytes +
-           keys2.bytes + vals2.bytes + ktmp.bytes + ranges.bytes;
+           keys2.bytes + vals2.bytes + ktmp.bytes + ranges.bytes + seg_tiles.bytes + seg_list.bytes +
+           seg_trans.bytes + seg_part.bytes;
   }
 };
 
@@ -168,7 +175,8 @@ size_t stage_a_bytes_needed(int64_t n, int ntiles) {
 
 void release_all(gs_server* s, Slot& sl) {
   Buf* all[] = {&sl.rec, &sl.geom, &sl.rect, &sl.tcount, &sl.dkey, &sl.idx, &sl.dkey2, &sl.idx2, &sl.cnts,
-                &sl.offs, &sl.cand, &sl.rtmp, &sl.keys, &sl.vals, &sl.keys2, &sl.vals2, &sl.ktmp, &sl.ranges};
+                &sl.offs, &sl.cand, &sl.rtmp, &sl.keys, &sl.vals, &sl.keys2, &sl.vals2, &sl.ktmp, &sl.ranges,
+                &sl.seg_tiles, &sl.seg_list, &sl.seg_trans, &sl.seg_part};
   for (Buf* b : all) dev_free(s, *b, sl.st);
 }
 
@@ -253,9 +261,21 @@ int stage_b(gs_server* s, Slot& sl, std::string* msg) {
   const int64_t K = sl.K;
   const size_t KK = (size_t)(K > 0 ? K : 1);
   cudaStream_t st = sl.st;
-  Buf* bufs[] = {&sl.keys, &sl.vals, &sl.keys2, &sl.vals2, &sl.ktmp};
-  const size_t sizes[] = {KK * 4, KK * 4, KK * 4, KK * 4, radix_tmp_words(K) * 4};
-  for (int i = 0; i < 5; ++i) {
+  const int ntiles_v = sl.cam.tiles_x * sl.cam.tiles_y;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+  // the same choice as a lone render, so that served images equal it
+  sl.lseg = split_lseg(ntiles_v, K, sms);
+  const int64_t nmax = sl.lseg ? split_nseg_max(K, sl.lseg) : 0;
+  sl.nseg_max = (unsigned)nmax;
+  const size_t tiles_words = 2 * (size_t)ntiles_v + 1 + scan_tmp_words(ntiles_v);
+  Buf* bufs[] = {&sl.keys, &sl.vals, &sl.keys2, &sl.vals2, &sl.ktmp, &sl.seg_tiles, &sl.seg_list, &sl.seg_trans,
+                 &sl.seg_part};
+  const size_t sizes[] = {KK * 4, KK * 4, KK * 4, KK * 4, radix_tmp_words(K) * 4,
+                          sl.lseg ? tiles_words * 4 : 0, (size_t)nmax * 2 * 4, (size_t)nmax * 256 * 4,
+                          (size_t)nmax * 256 * seg_part_bytes()};
+  for (int i = 0; i < 9; ++i) {
+    if (sizes[i] == 0) continue;
     const int r = ensure(s, *bufs[i], sizes[i], st);
     if (r == 1) return 0;
     if (r == 2) {
@@ -297,10 +317,40 @@ cudaEvent_t get_event(gs_server* s) {
 bool launch_batch(gs_server* s, const std::vector<int>& ready, std::string* msg) {
   BlendBatch b;
   memset(&b, 0, sizeof b);
-  int tiles = 0;
+  int tiles = 0, nj = 0;
   for (size_t i = 0; i < ready.size(); ++i) {
     Slot& sl = s->slots[ready[i]];
-    BlendJob& j = b.job[i];
+    if (cudaStreamWaitEvent(s->blend_st, sl.ev_b, 0) != cudaSuccess) {
+      *msg = "cudaStreamWaitEvent failed";
+      return false;
+    }
+    if (sl.lseg > 0) {
+      // a view with few tiles and long lists: its own launches, in segments
+      const int nt = sl.cam.tiles_x * sl.cam.tiles_y;
+      uint32_t* tw = (uint32_t*)sl.seg_tiles.p;
+      uint32_t* lw = (uint32_t*)sl.seg_list.p;
+      SegBufs sb;
+      sb.lseg = sl.lseg;
+      sb.nseg_max = sl.nseg_max;
+      sb.segcnt = tw;
+      sb.segoff = tw + nt;
+      sb.nseg = tw + 2 * nt;
+      sb.scan_tmp = tw + 2 * nt + 1;
+      sb.seg_tile = lw;
+      sb.seg_idx = lw + sl.nseg_max;
+      sb.trans = (float*)sl.seg_trans.p;
+      sb.part = sl.seg_part.p;
+      const cudaError_t es = launch_blend_fwd_split(sl.cam, sl.set, nullptr, (const float4*)sl.rec.p,
+                                                    (const RowGeom*)sl.geom.p, sl.vals_final,
+                                                    (const int2*)sl.ranges.p, sl.t->req.out, sl.t->req.n_contrib,
+                                                    nullptr, nullptr, nullptr, sb, s->blend_st);
+      if (es != cudaSuccess) {
+        *msg = std::string("blend: ") + cudaGetErrorString(es);
+        return false;
+      }
+      continue;
+    }
+    BlendJob& j = b.job[nj++];
     j.cam = sl.cam;
     j.set = sl.set;
     j.rf = sl.rf;
@@ -312,17 +362,13 @@ bool launch_batch(gs_server* s, const std::vector<int>& ready, std::string* msg)
     j.out = sl.t->req.out;
     j.n_contrib = sl.t->req.n_contrib;
     tiles += sl.cam.tiles_x * sl.cam.tiles_y;
-    if (cudaStreamWaitEvent(s->blend_st, sl.ev_b, 0) != cudaSuccess) {
-      *msg = "cudaStreamWaitEvent failed";
-      return false;
-    }
   }
-  b.njobs = (int)ready.size();
+  b.njobs = nj;
   b.total_tiles = tiles;
   const int bi = (int)s->batches.size();
   b.counter = s->counters + bi;
-  cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s->blend_st);
-  if (e == cudaSuccess) {
+  cudaError_t e = nj ? cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s->blend_st) : cudaSuccess;
+  if (e == cudaSuccess && nj) {
     // persistent grid: four CTAs per SM (the blend's occupancy), no more
     // CTAs than tiles
     int sms = 152;
@@ -394,16 +440,43 @@ void worker_loop(gs_server* s) {
           finish(s, sl, r == -2 ? GS_ERR_OOM : GS_ERR_CUDA, msg);
           progress = true;
         } else {
-          // release idle slots' buffers; if nothing else is running the
-          // request can never fit
-          bool others = false;
+          // release idle slots' buffers; a running slot will free memory
+          // when it finishes.  When only waiting slots remain, the oldest
+          // request keeps its buffers and the others go back to the head of
+          // the queue (no two waiting slots can block each other); if the
+          // oldest then still does not fit, it never will.
+          bool running = false;
           for (size_t j = 0; j < s->slots.size(); ++j) {
             if (j == i) continue;
-            if (s->slots[j].state == kIdle && s->slots[j].bytes() > 0) release_all(s, s->slots[j]);
-            else if (s->slots[j].state != kIdle) others = true;
+            const SlotState o = s->slots[j].state;
+            if (o == kIdle && s->slots[j].bytes() > 0) release_all(s, s->slots[j]);
+            else if (o != kIdle && o != kWaitMem) running = true;
           }
-          if (!others && stage_b(s, sl, &msg) != 1) {
-            finish(s, sl, GS_ERR_CAPACITY, "tile lists do not fit the memory budget");
+          bool oldest = true;
+          for (size_t j = 0; j < s->slots.size(); ++j)
+            if (j != i && s->slots[j].state == kWaitMem && s->slots[j].t->id < sl.t->id) oldest = false;
+          if (!running && oldest) {
+            std::vector<Ticket*> back;
+            for (size_t j = 0; j < s->slots.size(); ++j) {
+              Slot& o = s->slots[j];
+              if (j == i || o.state != kWaitMem) continue;
+              release_all(s, o);
+              back.push_back(o.t);
+              o.t = nullptr;
+              o.state = kIdle;
+            }
+            if (!back.empty()) {
+              std::sort(back.begin(), back.end(), [](const Ticket* a, const Ticket* b) { return a->id > b->id; });
+              std::lock_guard<std::mutex> lk(s->mu);
+              for (Ticket* t : back) {
+                t->state = 0;
+                s->queue.push_front(t);
+              }
+            }
+            const int r2 = stage_b(s, sl, &msg);
+            if (r2 == 1) sl.state = kStageB;
+            else if (r2 < 0) finish(s, sl, r2 == -2 ? GS_ERR_OOM : GS_ERR_CUDA, msg);
+            else finish(s, sl, GS_ERR_CAPACITY, "tile lists do not fit the memory budget");
             progress = true;
           }
         }

@@ -286,3 +286,28 @@ def test_gradients_against_finite_differences_on_64_surfels():
             assert abs(gv - fd) <= 1e-3 * max(abs(fd), 1e-4), (key, idx, gv, fd)
             checked += 1
     assert checked == 192
+
+
+def _dense_small_view():
+    """30k surfels seen at 64x64: 16 tiles with lists of thousands of entries,
+    which the render composites in segments (fewer tiles than the GPU holds)."""
+    return syn.tiny_scene(seed=77, n=30000, width=64, height=64, fx=64.0, sh_degree=1,
+                          log_scale_range=(-4.0, -2.5))
+
+
+def test_long_lists_composited_in_segments_match_oracle():
+    scene, cam, _, _ = _dense_small_view()
+    sc, d, out, cnt, frame, ref = _compare_render(scene, cam, frac=0.03)
+    vals, ranges, _ = frame.lists()
+    r = ranges.cpu().numpy()
+    assert (r[:, 1] - r[:, 0]).max() > 2 * 1024  # several segments per tile
+    info = frame.info()
+    assert info["pairs_blended"] == int(cnt.sum())
+
+
+def test_long_lists_backward_after_segmented_forward():
+    scene, cam, _, _ = _dense_small_view()
+    rng = np.random.default_rng(9)
+    adj = rng.normal(size=(1, 11, 64, 64))
+    grads, screen, ref, _ = _backward_case(scene, cam, adj, [0x7FF])
+    _assert_grads(grads, screen, ref, tol=2e-3)

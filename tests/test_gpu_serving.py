@@ -194,3 +194,22 @@ def test_wait_timeout_keeps_the_ticket(scenes):
     with pytest.raises(B.GsError):
         srv.wait(last, 0)  # consumed
     srv.close()
+
+
+def test_served_small_view_with_long_lists_equals_single_render():
+    """A view with few tiles and long lists is composited in segments by both
+    paths; the served image equals the lone render bit for bit."""
+    from paper_2411_00771_gb300 import binding as B
+    scene, cam, _, _ = syn.tiny_scene(seed=77, n=30000, width=64, height=64, fx=64.0, sh_degree=1,
+                                      log_scale_range=(-4.0, -2.5))
+    sc, _ = gu.gpu_scene(scene)
+    cnt_ref = torch.empty((64, 64), dtype=torch.int32, device="cuda")
+    ref, _ = sc.render(cam, n_contrib=cnt_ref, save=False)
+    srv = B.Server(budget_bytes=1 << 30, max_slots=2)
+    sid = srv.add_scene(sc)
+    out = torch.full((12, 64, 64), float("nan"), device="cuda")
+    cnt = torch.full((64, 64), -1, dtype=torch.int32, device="cuda")
+    srv.wait(srv.submit(sid, cam, out, cnt), 60000)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref) and torch.equal(cnt, cnt_ref)
+    srv.close()
