@@ -20,9 +20,12 @@ struct CamDev {
   double fx, fy, cx, cy;
   double campos[3];  // camera centre in world coordinates, -R^T t
   int W, H, tiles_x, tiles_y;
-  // FP32 copies for the FP32 kernels (converting doubles per use is slow)
+  // FP32 copies for the FP32 kernels (converting doubles per use is slow);
+  // with the *lo parts (value - FP32 copy, rounded) they are the double-float
+  // form the preprocess computes in
   float Rf[9], tf[3], camposf[3];
   float fxf, fyf, cxf, cyf;
+  float Rlo[9], tlo[3], fxlo, fylo, cxlo, cylo;
   float tabs;  // |t_x| + |t_y| + |t_z|
 };
 
@@ -39,6 +42,10 @@ inline void cam_from(const gs_camera& c, CamDev& cam) {
   for (int i = 0; i < 3; ++i) cam.tf[i] = (float)c.t[i];
   for (int i = 0; i < 3; ++i) cam.camposf[i] = (float)cam.campos[i];
   cam.fxf = (float)c.fx; cam.fyf = (float)c.fy; cam.cxf = (float)c.cx; cam.cyf = (float)c.cy;
+  for (int i = 0; i < 9; ++i) cam.Rlo[i] = (float)(c.R[i] - (double)cam.Rf[i]);
+  for (int i = 0; i < 3; ++i) cam.tlo[i] = (float)(c.t[i] - (double)cam.tf[i]);
+  cam.fxlo = (float)(c.fx - (double)cam.fxf); cam.fylo = (float)(c.fy - (double)cam.fyf);
+  cam.cxlo = (float)(c.cx - (double)cam.cxf); cam.cylo = (float)(c.cy - (double)cam.cyf);
   cam.tabs = (float)(fabs(c.t[0]) + fabs(c.t[1]) + fabs(c.t[2]));
 }
 

@@ -6,15 +6,17 @@
 // of the tangent plane in inverse form (Ji, e), the conservative screen
 // bounding box of {rho <= rho_max} (ellipse of the disk union the screen
 // filter disk) and its tile rectangle, SH colour and the camera-facing
-// normal.  The geometry runs in FP64 so that pixel offsets from c and the
-// inverse Jacobian of nearly edge-on disks are accurate to FP32 rounding;
-// the record the blends read is FP32 with c split into two floats.
+// normal.  The geometry runs in double-float (pairs of FP32 values, about
+// 48 bits) so that pixel offsets from c and the inverse Jacobian of nearly
+// edge-on disks are accurate to FP32 rounding; the record the blends read is
+// FP32 with c split into two floats.
 //
 // Backward: chains the per-surfel gradient record of the blend backward
 // (d Ji, d e, d c, d p_z, d opacity, d rgb, d normal) to the parameters,
 // in FP32, recomputing the forward intermediates.
 #include <math.h>
 
+#include "gs2d_df.cuh"
 #include "gs2d_internal.cuh"
 
 namespace gs2d {
@@ -118,34 +120,6 @@ __device__ __forceinline__ V3<T> rotT(const T* R, V3<T> v) {
 // so a sphere entirely behind the near plane, or whose camera-space box
 // projects (with the screen-filter radius, one pixel and a relative error
 // margin added) entirely outside the image, has an empty tile rectangle.
-// Double-precision reciprocal, reciprocal square root and square root by
-// Newton-Raphson refinement of the single-precision hardware estimates
-// (x_{k+1} = x_k (2 - a x_k) for 1/a, y_{k+1} = y_k (3 - a y_k^2) / 2 for
-// 1/sqrt(a)); each step squares the relative error, two steps take the
-// 2^-22 estimate to double precision.  Arguments outside the float range of
-// the estimate fall back to the division / square root.
-__device__ __forceinline__ double rcp_nr(double a) {
-  const float af = (float)a;
-  if (!(fabsf(af) > 1e-30f && fabsf(af) < 1e30f)) return 1.0 / a;
-  float e;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(af));
-  double x = (double)e;
-  x = x * fma(-a, x, 2.0);
-  x = x * fma(-a, x, 2.0);
-  return x;
-}
-__device__ __forceinline__ double rsqrt_nr(double a) {
-  const float af = (float)a;
-  if (!(af > 1e-30f && af < 1e30f)) return 1.0 / sqrt(a);
-  float e;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(af));
-  double y = (double)e;
-  y = y * fma(-0.5 * a * y, y, 1.5);
-  y = y * fma(-0.5 * a * y, y, 1.5);
-  return y;
-}
-__device__ __forceinline__ double sqrt_nr(double a) { return a > 0.0 ? a * rsqrt_nr(a) : 0.0; }
-
 __global__ void __launch_bounds__(256) preprocess_cull_kernel(ParamsDev P, CamDev cam, SetDev set,
                                                               uint2* __restrict__ rect,
                                                               uint32_t* __restrict__ tcount,
@@ -156,14 +130,14 @@ __global__ void __launch_bounds__(256) preprocess_cull_kernel(ParamsDev P, CamDe
     tcount[n] = 0u;
     rect[n] = make_uint2(0u, 0u);
     const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
-    const double qn2 = (double)qw * qw + (double)qx * qx + (double)qy * qy + (double)qz * qz;
+    const df qn2 = two_prod(qw, qw) + two_prod(qx, qx) + two_prod(qy, qy) + two_prod(qz, qz);
     const V3<float> mu = {P.mu[3 * n], P.mu[3 * n + 1], P.mu[3 * n + 2]};
     V3<float> p = rot<float>(cam.Rf, mu);
     p.x += cam.tf[0]; p.y += cam.tf[1]; p.z += cam.tf[2];
     const float R = 3.0f * fmaxf(P.scale[2 * n], P.scale[2 * n + 1]) * sqrtf(set.rho_max / 9.0f);
     // FP32 error of p is far below this margin (a few ulp of |mu| + |t|)
     const float eps = 1e-4f * (fabsf(mu.x) + fabsf(mu.y) + fabsf(mu.z) + cam.tabs + 1.0f) + 1e-3f * R;
-    keep = qn2 > 0.0 && p.z + R + eps > set.near_plane;
+    keep = df_pos(qn2) && p.z + R + eps > set.near_plane;
     const float zlo = p.z - R - eps, zhi = p.z + R + eps;
     if (keep && zlo > 0.f) {
       const float rpix = sqrtf(set.rho_max / set.sinv) + 1.0f;
@@ -189,8 +163,43 @@ __global__ void __launch_bounds__(256) compact_kernel(const uint32_t* __restrict
   if (i < n && flags[i]) cand[pos[i]] = (uint32_t)i;
 }
 
-// Stage 2 (FP64 geometry, candidates only): the definition's preprocess,
-// the footprint's exact tile-row coverage and the blend record.
+// Double-float vector helpers for the preprocess geometry.
+struct D3 {
+  df x, y, z;
+};
+__device__ __forceinline__ df dot3(const D3& a, const D3& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// R v with R the camera rotation in double-float (row-major)
+__device__ __forceinline__ D3 cam_rot(const CamDev& c, const D3& v) {
+  D3 r;
+  df* o[3] = {&r.x, &r.y, &r.z};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const df r0 = df_make(c.Rf[3 * i], c.Rlo[3 * i]);
+    const df r1 = df_make(c.Rf[3 * i + 1], c.Rlo[3 * i + 1]);
+    const df r2 = df_make(c.Rf[3 * i + 2], c.Rlo[3 * i + 2]);
+    *o[i] = r0 * v.x + r1 * v.y + r2 * v.z;
+  }
+  return r;
+}
+__device__ __forceinline__ D3 cam_rot(const CamDev& c, float x, float y, float z) {
+  D3 r;
+  df* o[3] = {&r.x, &r.y, &r.z};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const df r0 = df_make(c.Rf[3 * i], c.Rlo[3 * i]);
+    const df r1 = df_make(c.Rf[3 * i + 1], c.Rlo[3 * i + 1]);
+    const df r2 = df_make(c.Rf[3 * i + 2], c.Rlo[3 * i + 2]);
+    *o[i] = r0 * x + r1 * y + r2 * z;
+  }
+  return r;
+}
+
+// Stage 2 (candidates only): the definition's preprocess, the footprint's
+// exact tile-row coverage and the blend record.  The geometry that decides
+// where a surfel lands (view transform, projection, the centred inverse
+// homography, the bound of {rho <= rho_max} and its tile rectangle) is
+// computed in double-float (about 48 bits; the FP64 pipe is too slow for a
+// million surfels per view), colour and normal in FP32.
 template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDev cam, SetDev set,
                                                               const uint32_t* __restrict__ cand,
@@ -202,63 +211,72 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
                                                               uint32_t* __restrict__ idx,
                                                               RowGeom* __restrict__ geom) {
   const uint32_t total = *ncand;
-  const double rf = sqrt((double)set.rho_max / (double)set.sinv);
+  const df rf = df_sqrt(df_make(set.rho_max) / df_make(set.sinv));
+  const float rff = df_float(rf);
+  const df fx = df_make(cam.fxf, cam.fxlo), fy = df_make(cam.fyf, cam.fylo);
+  const df cx0 = df_make(cam.cxf, cam.cxlo), cy0 = df_make(cam.cyf, cam.cylo);
   for (uint32_t ci = blockIdx.x * blockDim.x + threadIdx.x; ci < total; ci += gridDim.x * blockDim.x) {
     const int n = (int)cand[ci];
     idx[ci] = (uint32_t)n;
     dkey[ci] = 0xFFFFFFFFu;  // not visible unless set below
-    const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
-    const double qn2 = (double)qw * qw + (double)qx * qx + (double)qy * qy + (double)qz * qz;
-    if (!(qn2 > 0.0)) continue;
-    const double iq = rsqrt_nr(qn2);
-    V3<double> r1, r2, r3;
-    quat_cols<double>(qw * iq, qx * iq, qy * iq, qz * iq, r1, r2, r3);
-    const V3<double> mu = {(double)P.mu[3 * n], (double)P.mu[3 * n + 1], (double)P.mu[3 * n + 2]};
-    V3<double> p = rot<double>(cam.R, mu);
-    p.x += cam.t[0]; p.y += cam.t[1]; p.z += cam.t[2];
-    const V3<double> tu = rot<double>(cam.R, r1), tv = rot<double>(cam.R, r2), nv = rot<double>(cam.R, r3);
-    const double su = P.scale[2 * n], sv = P.scale[2 * n + 1];
-    const V3<double> a = {su * tu.x, su * tu.y, su * tu.z}, b = {sv * tv.x, sv * tv.y, sv * tv.z};
-    const double zmin = p.z - sqrt_nr((double)set.rho_max * (a.z * a.z + b.z * b.z));
-    if (!(zmin > (double)set.near_plane)) continue;
-    const double iz = rcp_nr(p.z);
-    const double xi = p.x * iz, yi = p.y * iz;
-    const double cx = cam.fx * xi + cam.cx, cy = cam.fy * yi + cam.cy;
-    const double J11 = cam.fx * (a.x - a.z * xi) * iz, J12 = cam.fx * (b.x - b.z * xi) * iz;
-    const double J21 = cam.fy * (a.y - a.z * yi) * iz, J22 = cam.fy * (b.y - b.z * yi) * iz;
-    const double w1 = a.z * iz, w2 = b.z * iz;
+    const float qw0 = P.quat[4 * n], qx0 = P.quat[4 * n + 1], qy0 = P.quat[4 * n + 2], qz0 = P.quat[4 * n + 3];
+    const df qn2 = two_prod(qw0, qw0) + two_prod(qx0, qx0) + two_prod(qy0, qy0) + two_prod(qz0, qz0);
+    if (!df_pos(qn2)) continue;
+    const df iq = df_rsqrt(qn2);
+    const df qw = iq * qw0, qx = iq * qx0, qy = iq * qy0, qz = iq * qz0;
+    // columns of the rotation of the unit quaternion
+    const df one = df_make(1.f);
+    const D3 r1 = {one - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy + qw * qz), 2.f * (qx * qz - qw * qy)};
+    const D3 r2 = {2.f * (qx * qy - qw * qz), one - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz + qw * qx)};
+    const D3 r3 = {2.f * (qx * qz + qw * qy), 2.f * (qy * qz - qw * qx), one - 2.f * (qx * qx + qy * qy)};
+    const float mux = P.mu[3 * n], muy = P.mu[3 * n + 1], muz = P.mu[3 * n + 2];
+    D3 p = cam_rot(cam, mux, muy, muz);
+    p.x = p.x + df_make(cam.tf[0], cam.tlo[0]);
+    p.y = p.y + df_make(cam.tf[1], cam.tlo[1]);
+    p.z = p.z + df_make(cam.tf[2], cam.tlo[2]);
+    const D3 tu = cam_rot(cam, r1), tv = cam_rot(cam, r2), nv = cam_rot(cam, r3);
+    const float su = P.scale[2 * n], sv = P.scale[2 * n + 1];
+    const D3 a = {tu.x * su, tu.y * su, tu.z * su}, b = {tv.x * sv, tv.y * sv, tv.z * sv};
+    const df zmin = p.z - df_sqrt((a.z * a.z + b.z * b.z) * set.rho_max);
+    if (!df_pos(zmin - set.near_plane)) continue;
+    const df iz = df_rcp(p.z);
+    const df xi = p.x * iz, yi = p.y * iz;
+    const df cx = fx * xi + cx0, cy = fy * yi + cy0;
+    const df J11 = fx * (a.x - a.z * xi) * iz, J12 = fx * (b.x - b.z * xi) * iz;
+    const df J21 = fy * (a.y - a.z * yi) * iz, J22 = fy * (b.y - b.z * yi) * iz;
+    const df w1 = a.z * iz, w2 = b.z * iz;
     // bounding box of {rho_obj <= rho_max} in offsets from c: dual conic of
     // the centred homography H = [[J, 0], [w^T, 1]]; scaled to C33 = 1 it is
     // [[e0 e0^T - G, e0], [e0^T, 1]] for the ellipse (d - e0)^T G^-1 (d - e0) <= 1
-    const double rm = set.rho_max;
-    const double C11 = rm * (J11 * J11 + J12 * J12), C22 = rm * (J21 * J21 + J22 * J22);
-    const double C12 = rm * (J11 * J21 + J12 * J22);
-    const double C13 = rm * (J11 * w1 + J12 * w2), C23 = rm * (J21 * w1 + J22 * w2);
-    const double C33 = rm * (w1 * w1 + w2 * w2) - 1.0;
-    const double ex = sqrt_nr(fmax(C13 * C13 - C11 * C33, 0.0));
-    const double ey = sqrt_nr(fmax(C23 * C23 - C22 * C33, 0.0));
-    const double i33 = rcp_nr(C33);
-    const double x0 = (C13 - ex) * i33, x1 = (C13 + ex) * i33;
-    const double y0 = (C23 - ey) * i33, y1 = (C23 + ey) * i33;
-    const double xmin = cx + fmin(fmin(x0, x1), -rf), xmax = cx + fmax(fmax(x0, x1), rf);
-    const double ymin = cy + fmin(fmin(y0, y1), -rf), ymax = cy + fmax(fmax(y0, y1), rf);
-    double ilo = ceil(xmin - 0.5), ihi = floor(xmax - 0.5);
-    double jlo = ceil(ymin - 0.5), jhi = floor(ymax - 0.5);
-    ilo = fmax(ilo, 0.0); jlo = fmax(jlo, 0.0);
-    ihi = fmin(ihi, (double)(cam.W - 1)); jhi = fmin(jhi, (double)(cam.H - 1));
+    const float rm = set.rho_max;
+    const df C11 = (J11 * J11 + J12 * J12) * rm, C22 = (J21 * J21 + J22 * J22) * rm;
+    const df C12 = (J11 * J21 + J12 * J22) * rm;
+    const df C13 = (J11 * w1 + J12 * w2) * rm, C23 = (J21 * w1 + J22 * w2) * rm;
+    const df C33 = (w1 * w1 + w2 * w2) * rm - 1.f;
+    const df ex = df_sqrt(df_max(C13 * C13 - C11 * C33, df_make(0.f)));
+    const df ey = df_sqrt(df_max(C23 * C23 - C22 * C33, df_make(0.f)));
+    const df i33 = df_rcp(C33);
+    const df x0 = (C13 - ex) * i33, x1 = (C13 + ex) * i33;
+    const df y0 = (C23 - ey) * i33, y1 = (C23 + ey) * i33;
+    const df xmin = cx + df_min(df_min(x0, x1), -rf), xmax = cx + df_max(df_max(x0, x1), rf);
+    const df ymin = cy + df_min(df_min(y0, y1), -rf), ymax = cy + df_max(df_max(y0, y1), rf);
+    float ilo = df_ceil(xmin - 0.5f), ihi = df_floor(xmax - 0.5f);
+    float jlo = df_ceil(ymin - 0.5f), jhi = df_floor(ymax - 0.5f);
+    ilo = fmaxf(ilo, 0.f); jlo = fmaxf(jlo, 0.f);
+    ihi = fminf(ihi, (float)(cam.W - 1)); jhi = fminf(jhi, (float)(cam.H - 1));
     if (!(ilo <= ihi && jlo <= jhi)) continue;
     RowGeom gm;
     {
-      const double e0x = C13 * i33, e0y = C23 * i33;
-      const double g11 = e0x * e0x - C11 * i33, g12 = e0x * e0y - C12 * i33, g22 = e0y * e0y - C22 * i33;
-      const float chx = (float)cx, chy = (float)cy;
-      gm.cx_hi = chx; gm.cx_lo = (float)(cx - (double)chx);
-      gm.cy_hi = chy; gm.cy_lo = (float)(cy - (double)chy);
-      gm.e0x = (float)e0x; gm.e0y = (float)e0y;
-      if (g11 > 0.0 && g22 > 0.0) {
+      const df e0x = C13 * i33, e0y = C23 * i33;
+      const df g11 = e0x * e0x - C11 * i33, g12 = e0x * e0y - C12 * i33, g22 = e0y * e0y - C22 * i33;
+      gm.cx_hi = cx.hi; gm.cx_lo = cx.lo;
+      gm.cy_hi = cy.hi; gm.cy_lo = cy.lo;
+      gm.e0x = df_float(e0x); gm.e0y = df_float(e0y);
+      if (df_pos(g11) && df_pos(g22)) {
         // rounded once to FP32; the row rule's margin covers their error
-        const float det = (float)fmax(g11 * g22 - g12 * g12, 0.0);
-        const float f11 = (float)g11, f12 = (float)g12, f22 = (float)g22;
+        const df dg = g11 * g22 - g12 * g12;
+        const float det = df_pos(dg) ? df_float(dg) : 0.f;
+        const float f11 = df_float(g11), f12 = df_float(g12), f22 = df_float(g22);
         gm.hy = sqrtf(f22);
         gm.t = f12 * rsqrtf(f11);
         gm.slope = f12 / f22;
@@ -274,21 +292,21 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     uint32_t cnt = 0;
     for (int ty = ty0; ty < ty1; ++ty) {
       int a0, a1;
-      if (row_tiles(gm, ty, (float)rf, &a0, &a1)) cnt += (uint32_t)(a1 - a0);
+      if (row_tiles(gm, ty, rff, &a0, &a1)) cnt += (uint32_t)(a1 - a0);
     }
     if (cnt == 0) continue;
     geom[n] = gm;
     tcount[n] = cnt;
-    const float pz = (float)p.z;
+    const float pz = df_float(p.z);
     dkey[ci] = __float_as_uint(pz);
-    const double det = J11 * J22 - J12 * J21;
+    const df det = J11 * J22 - J12 * J21;
     float4 r1f;
     float2 ef;
-    if (det != 0.0) {
-      const double id = rcp_nr(det);
-      const double i11 = J22 * id, i12 = -J12 * id, i21 = -J21 * id, i22 = J11 * id;
-      r1f = make_float4((float)i11, (float)i12, (float)i21, (float)i22);
-      ef = make_float2((float)(-(i11 * w1 + i21 * w2)), (float)(-(i12 * w1 + i22 * w2)));
+    if (df_nonzero(det)) {
+      const df id = df_rcp(det);
+      const df i11 = J22 * id, i12 = -(J12 * id), i21 = -(J21 * id), i22 = J11 * id;
+      r1f = make_float4(df_float(i11), df_float(i12), df_float(i21), df_float(i22));
+      ef = make_float2(df_float(-(i11 * w1 + i21 * w2)), df_float(-(i12 * w1 + i22 * w2)));
     } else {
       // edge-on disk: no object-space footprint (rho_obj is NaN, the
       // screen filter decides)
@@ -297,8 +315,7 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
       ef = make_float2(0.f, 0.f);
     }
     // colour: SH at the world direction from the camera centre
-    const float dx = (float)(mu.x - cam.campos[0]), dy = (float)(mu.y - cam.campos[1]),
-                dz = (float)(mu.z - cam.campos[2]);
+    const float dx = mux - cam.camposf[0], dy = muy - cam.camposf[1], dz = muz - cam.camposf[2];
     const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
     constexpr int K = (DEG + 1) * (DEG + 1);
     float Y[16];
@@ -313,14 +330,13 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c] + 0.5f, 0.f);
-    const double sg = (nv.x * p.x + nv.y * p.y + nv.z * p.z) > 0.0 ? -1.0 : 1.0;
-    const float chx = (float)cx, chy = (float)cy;
+    const float sg = df_pos(dot3(nv, p)) ? -1.f : 1.f;
     float4* Rr = rec + (size_t)n * kRecF4;
-    Rr[0] = make_float4(chx, chy, (float)(cx - (double)chx), (float)(cy - (double)chy));
+    Rr[0] = make_float4(cx.hi, cy.hi, cx.lo, cy.lo);
     Rr[1] = r1f;
     Rr[2] = make_float4(ef.x, ef.y, pz, P.opacity[n]);
-    Rr[3] = make_float4(col[0], col[1], col[2], (float)(sg * nv.x));
-    Rr[4] = make_float4((float)(sg * nv.y), (float)(sg * nv.z), 0.f, 0.f);
+    Rr[3] = make_float4(col[0], col[1], col[2], sg * df_float(nv.x));
+    Rr[4] = make_float4(sg * df_float(nv.y), sg * df_float(nv.z), 0.f, 0.f);
   }
 }
 
