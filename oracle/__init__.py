@@ -294,3 +294,29 @@ def prune_bound(contrib, ratio):
         return None, np.ones(n, bool)
     bound = np.sort(c)[k - 1]
     return bound, c > bound
+
+
+def visibility_count(points, sigma, cams, near=0.2, lowpass=0.3):
+    """Visible frequency of points over views (Sec. 4.1 crop volume
+    estimation).  Returns (count[N], flagged[N]): views where the point is
+    visible, and views where a visibility decision was within 1e-9 of its
+    threshold."""
+    lib = _load()
+    pts = np.ascontiguousarray(points, np.float64).reshape(-1, 3)
+    n = pts.shape[0]
+    C = np.ascontiguousarray(np.stack([cam_array(c) for c in cams]), np.float64)
+    count = np.zeros(n, np.int64)
+    flagged = np.zeros(n, np.int64)
+    lib.oracle_visibility_count(ctypes.c_int64(n), _p(pts), ctypes.c_double(sigma), ctypes.c_int(len(cams)),
+                                _p(C), ctypes.c_double(near), ctypes.c_double(lowpass), _p(count), _p(flagged))
+    return count, flagged
+
+
+def visible_height_range(points, count, min_count):
+    """Points seen in at least min_count views, and the lowest and highest
+    world z among them (Sec. 4.1); (None, None) when none remains."""
+    keep = np.asarray(count) >= min_count
+    z = np.asarray(points, np.float64).reshape(-1, 3)[keep, 2]
+    if z.size == 0:
+        return keep, (None, None)
+    return keep, (float(z.min()), float(z.max()))

@@ -20,6 +20,7 @@
  *     depth; Sec. 3.2 Eq. 2: decomposed-gradient densification; Sec. 3.2:
  *     elongation rate eta = min(s)/max(s).
  *   - Sec. 3.3 Eq. 3: single-view trim contribution of each surfel.
+ *   - Sec. 4.1: visible frequency of points (crop volume estimation).
  * Readings where the paper is silent (pixel centres at +0.5, alpha clamp 0.99,
  * stop before the pair that would take T below T_min, the per-pair 3-sigma
  * support rho <= 9, screen filter rho_scr = 2 |x - c|^2, centre depth when the
@@ -1211,5 +1212,61 @@ int oracle_contribution(int64_t N, int deg, const double* mu, const double* quat
     free(sup); free(keys);
   }
   ctx_free(&C);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Visible frequency of points (Sec. 4.1, crop volume estimation).         */
+
+/* Each point is an isotropic 3D Gaussian of standard deviation sigma.  In a
+ * view (camera array as above) it is visible when it lies in front of the
+ * near plane and the 3-sigma square of its projected footprint overlaps the
+ * image: the footprint's covariance is the EWA projection sigma^2 J J^T of the
+ * isotropic covariance (J the Jacobian of the perspective projection at the
+ * point) plus the rasterizer's low-pass of lowpass px^2 on both axes, its
+ * 3-sigma half-width r = 3 sqrt(largest eigenvalue), and the square
+ * [c - r, c + r]^2 around the projected centre c must meet [0, W] x [0, H]
+ * with positive overlap.  count[j] += the number of visible views;
+ * flagged[j] += the views where a decision was within 1e-9 (relative) of its
+ * threshold. */
+int oracle_visibility_count(int64_t N, const double* pts, double sigma, int V, const double* cams,
+                            double near, double lowpass, int64_t* count, int64_t* flagged) {
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < N; ++j) {
+    int64_t c = 0, f = 0;
+    for (int v = 0; v < V; ++v) {
+      const double* cm = cams + (size_t)v * CAM_LEN;
+      double p[3];
+      matvec3(cm + CAM_R, pts + 3 * j, p);
+      for (int i = 0; i < 3; ++i) p[i] += cm[CAM_T + i];
+      const double z = p[2];
+      if (fabs(z - near) <= 1e-9 * (fabs(near) + 1.0)) ++f;
+      if (!(z > near)) continue;
+      const double fx = cm[CAM_FX], fy = cm[CAM_FY];
+      /* J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]] */
+      const double J[2][3] = {{fx / z, 0.0, -fx * p[0] / (z * z)}, {0.0, fy / z, -fy * p[1] / (z * z)}};
+      double S[2][2];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          S[a][b] = sigma * sigma * (J[a][0] * J[b][0] + J[a][1] * J[b][1] + J[a][2] * J[b][2]) +
+                    (a == b ? lowpass : 0.0);
+      const double mid = 0.5 * (S[0][0] + S[1][1]);
+      const double half = 0.5 * (S[0][0] - S[1][1]);
+      const double lmax = mid + sqrt(half * half + S[0][1] * S[0][1]);
+      const double r = 3.0 * sqrt(lmax);
+      const double cx = fx * p[0] / z + cm[CAM_CX], cy = fy * p[1] / z + cm[CAM_CY];
+      const double W = cm[CAM_W], H = cm[CAM_H];
+      const double m[4] = {cx + r, W - (cx - r), cy + r, H - (cy - r)};  /* all > 0: overlap */
+      int vis = 1;
+      for (int k = 0; k < 4; ++k) {
+        const double scale = fabs(cx) + fabs(cy) + r + W + H;
+        if (fabs(m[k]) <= 1e-9 * scale) ++f;
+        if (!(m[k] > 0.0)) vis = 0;
+      }
+      c += vis;
+    }
+    count[j] += c;
+    flagged[j] += f;
+  }
   return 0;
 }

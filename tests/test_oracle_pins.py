@@ -615,3 +615,76 @@ def test_prune_bound_percentile():
     assert bound is None and keep.all()
     bound, keep = oracle.prune_bound(c, 1.0)
     assert bound == 0.9 and not keep.any()
+
+
+# --------------------------------------------------------------------------
+# Visible frequency of points (Sec. 4.1, crop volume estimation)
+
+def test_visibility_on_axis_behind_and_near_plane():
+    cam = camera(64, 48, 60.0)
+    pts = np.array([[0.0, 0.0, 5.0], [0.0, 0.0, -5.0], [0.0, 0.0, 0.19], [0.0, 0.0, 0.21]])
+    c, f = oracle.visibility_count(pts, 0.05, [cam, cam, cam])
+    assert list(c) == [3, 0, 0, 3] and not f.any()
+
+
+def test_visibility_image_edge_closed_form():
+    """Point at (x, 0, z) seen by an identity camera: the projected covariance
+    is diagonal (sigma^2 f^2 (1/z^2 + x^2/z^4) + lp, sigma^2 f^2/z^2 + lp), the
+    larger entry is the x one, and the point drops out when c - 3 sqrt(S_xx)
+    passes W.  Bisection on that closed form finds the edge; points just
+    inside and outside it flip."""
+    W, H, f, z, s, lp = 64, 48, 60.0, 4.0, 0.05, 0.3
+    cam = camera(W, H, f)
+
+    def left_edge(x):
+        sxx = s * s * f * f * (1 / z ** 2 + x * x / z ** 4) + lp
+        return f * x / z + W / 2 - 3 * math.sqrt(sxx) - W
+
+    a, b = 0.0, 10.0
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        a, b = (m, b) if left_edge(m) < 0 else (a, m)
+    xe = 0.5 * (a + b)
+    pts = np.array([[xe * (1 - 1e-6), 0, z], [xe * (1 + 1e-6), 0, z]])
+    c, fl = oracle.visibility_count(pts, s, [cam], lowpass=lp)
+    assert list(c) == [1, 0] and not fl.any()
+
+
+def test_visibility_matches_numerical_jacobian_and_eigensolver():
+    """Random points and views: the 3-sigma half-width from numpy's
+    eigensolver on sigma^2 J J^T + lp I, with J by central differences of the
+    projection, decides the same visibility away from the thresholds."""
+    rng = np.random.default_rng(12)
+    pts = rng.uniform([-30, -30, -2], [30, 30, 25], (400, 3))
+    cams = [syn.orbit_camera(rng, 96, 72, radius=60.0, altitude=40.0) for _ in range(12)]
+    s, lp = 0.8, 0.3
+    c, fl = oracle.visibility_count(pts, s, cams, lowpass=lp)
+    exp = np.zeros(len(pts), np.int64)
+    margin_ok = np.ones(len(pts), bool)
+    for cam in cams:
+        R, t = np.asarray(cam["R"]), np.asarray(cam["t"])
+
+        def proj(q):
+            p = R @ q + t
+            return np.array([cam["fx"] * p[0] / p[2] + cam["cx"], cam["fy"] * p[1] / p[2] + cam["cy"]])
+
+        for j, q in enumerate(pts):
+            p = R @ q + t
+            if p[2] <= 0.2:
+                continue
+            Jw = np.stack([(proj(q + e) - proj(q - e)) / 2e-4 for e in np.eye(3) * 1e-4], axis=1)  # d pix / d world
+            S = s * s * Jw @ Jw.T + lp * np.eye(2)
+            r = 3 * math.sqrt(np.linalg.eigvalsh(S).max())
+            cx, cy = proj(q)
+            m = np.array([cx + r, cam["width"] - (cx - r), cy + r, cam["height"] - (cy - r)])
+            if np.abs(m).min() < 1e-4 * (abs(cx) + abs(cy) + r + 200):
+                margin_ok[j] = False
+            exp[j] += int(np.all(m > 0))
+    assert margin_ok.mean() > 0.95
+    assert np.array_equal(c[margin_ok], exp[margin_ok]) and c.sum() > 100 and (c < len(cams)).any()
+
+
+def test_visible_height_range():
+    pts = np.array([[0, 0, 1.0], [0, 0, 5.0], [0, 0, 3.0], [0, 0, 9.0]])
+    keep, (lo, hi) = oracle.visible_height_range(pts, [5, 1, 3, 0], 2)
+    assert list(keep) == [True, False, True, False] and (lo, hi) == (1.0, 3.0)
