@@ -293,6 +293,31 @@ gs_status gs_contribution(gs_scene* scene, const gs_camera* camera, float gamma,
 gs_status gs_prune_by_contribution(int64_t n, const float* contrib, double ratio, uint8_t* keep,
                                    float* bound, void* stream);
 
+/* ---- Visible frequency of points (Sec. 4.1, crop volume estimation) -------
+ *
+ * gs_visibility_count: for each of n points (device FP32 [n][3], world
+ * coordinates), ADDS to counts[j] (device uint32 [n]) the number of the
+ * n_views cameras (host array) in which the point is visible as a Gaussian
+ * primitive of a rasterizer: an isotropic 3D Gaussian of standard deviation
+ * sigma (world units) that lies in front of near_plane and whose projected
+ * footprint's 3-sigma square overlaps the image.  The footprint covariance is
+ * sigma^2 J J^T + lowpass I (J the Jacobian of the perspective projection at
+ * the point; lowpass the rasterizer's screen-space dilation in px^2, 0.3 in
+ * the usual 3DGS rasterizer); the half-width is 3 sqrt(largest eigenvalue).
+ * Occlusion plays no part (the rasterizer's per-primitive visible mask).  FP32;
+ * a decision within about 1e-6 (relative) of its threshold may go either way.
+ * Asynchronous; the cameras are copied to the device before the call returns.
+ *
+ * gs_visibility_bounds: keep[j] = (counts[j] >= min_count) (device uint8 [n]);
+ * zrange (device FP32 [2]) = lowest and highest world z among the kept points,
+ * NaN when none is kept.  The paper then fits an alpha shape to the kept
+ * points' ground projection (not part of this library). */
+gs_status gs_visibility_count(int64_t n, const float* points, float sigma, const gs_camera* cams,
+                              int32_t n_views, float near_plane, float lowpass, uint32_t* counts,
+                              void* stream);
+gs_status gs_visibility_bounds(int64_t n, const float* points, const uint32_t* counts, uint32_t min_count,
+                               uint8_t* keep, float* zrange, void* stream);
+
 /* ---- Serving: continuous batching of forward renders ------------------
  * (the serving loop built on the rasterizer; the paper has no serving
  * component of its own.)

@@ -299,8 +299,8 @@ def prune_bound(contrib, ratio):
 def visibility_count(points, sigma, cams, near=0.2, lowpass=0.3):
     """Visible frequency of points over views (Sec. 4.1 crop volume
     estimation).  Returns (count[N], flagged[N]): views where the point is
-    visible, and views where a visibility decision was within 1e-9 of its
-    threshold."""
+    visible, and views where a visibility decision was within 2e-6 (relative)
+    of its threshold."""
     lib = _load()
     pts = np.ascontiguousarray(points, np.float64).reshape(-1, 3)
     n = pts.shape[0]

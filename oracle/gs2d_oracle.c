@@ -1227,8 +1227,9 @@ int oracle_contribution(int64_t N, int deg, const double* mu, const double* quat
  * 3-sigma half-width r = 3 sqrt(largest eigenvalue), and the square
  * [c - r, c + r]^2 around the projected centre c must meet [0, W] x [0, H]
  * with positive overlap.  count[j] += the number of visible views;
- * flagged[j] += the views where a decision was within 1e-9 (relative) of its
- * threshold. */
+ * flagged[j] += the views where a decision was within 2e-6 (relative to the
+ * magnitudes involved) of its threshold, beyond what an FP32 evaluation can
+ * resolve. */
 int oracle_visibility_count(int64_t N, const double* pts, double sigma, int V, const double* cams,
                             double near, double lowpass, int64_t* count, int64_t* flagged) {
 #pragma omp parallel for schedule(static)
@@ -1240,7 +1241,7 @@ int oracle_visibility_count(int64_t N, const double* pts, double sigma, int V, c
       matvec3(cm + CAM_R, pts + 3 * j, p);
       for (int i = 0; i < 3; ++i) p[i] += cm[CAM_T + i];
       const double z = p[2];
-      if (fabs(z - near) <= 1e-9 * (fabs(near) + 1.0)) ++f;
+      if (fabs(z - near) <= 2e-6 * (fabs(z) + fabs(near))) ++f;
       if (!(z > near)) continue;
       const double fx = cm[CAM_FX], fy = cm[CAM_FY];
       /* J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]] */
@@ -1260,7 +1261,7 @@ int oracle_visibility_count(int64_t N, const double* pts, double sigma, int V, c
       int vis = 1;
       for (int k = 0; k < 4; ++k) {
         const double scale = fabs(cx) + fabs(cy) + r + W + H;
-        if (fabs(m[k]) <= 1e-9 * scale) ++f;
+        if (fabs(m[k]) <= 2e-6 * scale) ++f;
         if (!(m[k] > 0.0)) vis = 0;
       }
       c += vis;

@@ -117,6 +117,9 @@ _SIGS = {
     "gs_elongation_filter": [ctypes.c_int64, _V, ctypes.c_float, _V, _V],
     "gs_contribution": [_V, ctypes.POINTER(gs_camera), ctypes.c_float, ctypes.c_float, _V, _V, _V, _V],
     "gs_prune_by_contribution": [ctypes.c_int64, _V, ctypes.c_double, _V, _V, _V],
+    "gs_visibility_count": [ctypes.c_int64, _V, ctypes.c_float, _V, ctypes.c_int32, ctypes.c_float,
+                            ctypes.c_float, _V, _V],
+    "gs_visibility_bounds": [ctypes.c_int64, _V, _V, ctypes.c_uint32, _V, _V, _V],
     "gs_sync": [_V, ctypes.c_int32],
     "gs_profile_enable": [ctypes.c_int32],
     "gs_server_create": [ctypes.POINTER(_V), ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(gs_allocator)],
@@ -427,6 +430,31 @@ def prune_by_contribution(contrib, ratio, stream=None):
     _check(_lib.gs_prune_by_contribution(n, _ptr(contrib, shape=(n,), name="contrib"), float(ratio),
                                          _ptr(keep, torch.uint8), _ptr(bound), _stream(stream)))
     return keep, bound
+
+
+def visibility_count(points, sigma, cams, counts=None, near_plane=0.2, lowpass=0.3, stream=None):
+    """Visible frequency of points over views (Sec. 4.1): adds to `counts`
+    (int32 view of uint32 [N], zeros when None) the views in which each point
+    is visible as an isotropic Gaussian primitive.  Returns counts."""
+    n = points.shape[0]
+    if counts is None:
+        counts = torch.zeros(n, dtype=torch.int32, device=points.device)
+    arr = (gs_camera * max(len(cams), 1))(*[make_camera(c) for c in cams])
+    _check(_lib.gs_visibility_count(n, _ptr(points, shape=(n, 3), name="points"), float(sigma),
+                                    ctypes.cast(arr, _V), len(cams), float(near_plane), float(lowpass),
+                                    _ptr(counts, torch.int32, (n,), "counts"), _stream(stream)))
+    return counts
+
+
+def visibility_bounds(points, counts, min_count, stream=None):
+    """keep = counts >= min_count, and (min z, max z) of the kept points."""
+    n = points.shape[0]
+    keep = torch.empty(n, dtype=torch.uint8, device=points.device)
+    zr = torch.empty(2, dtype=torch.float32, device=points.device)
+    _check(_lib.gs_visibility_bounds(n, _ptr(points, shape=(n, 3), name="points"),
+                                     _ptr(counts, torch.int32, (n,), "counts"), int(min_count),
+                                     _ptr(keep, torch.uint8), _ptr(zr), _stream(stream)))
+    return keep, zr
 
 
 def elongation_filter(scale, eta_thr=0.1, stream=None):

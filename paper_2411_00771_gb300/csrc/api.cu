@@ -668,6 +668,52 @@ gs_status gs_elongation_filter(int64_t n, const float* scale, float eta_thr, uin
   return GS_OK;
 }
 
+gs_status gs_visibility_count(int64_t n, const float* points, float sigma, const gs_camera* cams, int32_t n_views,
+                              float near_plane, float lowpass, uint32_t* counts, void* stream) {
+  if (n < 0 || n_views < 0 || (n > 0 && (!points || !counts)) || (n_views > 0 && !cams))
+    return fail(GS_ERR_ARG, "gs_visibility_count: bad argument");
+  if (!(sigma >= 0.f) || !(lowpass >= 0.f)) return fail(GS_ERR_ARG, "gs_visibility_count: sigma and lowpass must be >= 0");
+  if (n == 0 || n_views == 0) return GS_OK;
+  std::vector<VisCam> hc((size_t)n_views);
+  for (int32_t v = 0; v < n_views; ++v) {
+    const gs_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || !(c.fx > 0) || !(c.fy > 0))
+      return fail(GS_ERR_ARG, "gs_visibility_count: bad camera " + std::to_string(v));
+    VisCam& k = hc[(size_t)v];
+    for (int i = 0; i < 9; ++i) k.R[i] = (float)c.R[i];
+    for (int i = 0; i < 3; ++i) k.t[i] = (float)c.t[i];
+    k.fx = (float)c.fx; k.fy = (float)c.fy; k.cx = (float)c.cx; k.cy = (float)c.cy;
+    k.W = (float)c.width; k.H = (float)c.height;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  const size_t bytes = sizeof(VisCam) * (size_t)n_views;
+  VisCam* dc = static_cast<VisCam*>(al.get(bytes, st));
+  if (!dc) return fail(GS_ERR_OOM, "gs_visibility_count: device allocation failed");
+  // pageable source: the copy is staged before the call returns
+  cudaError_t e = cudaMemcpyAsync(dc, hc.data(), bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_visibility_count(points, n, sigma, lowpass, near_plane, dc, n_views, counts, st);
+  al.put(dc, bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_visibility_count");
+  return GS_OK;
+}
+
+gs_status gs_visibility_bounds(int64_t n, const float* points, const uint32_t* counts, uint32_t min_count,
+                               uint8_t* keep, float* zrange, void* stream) {
+  if (n < 0 || (n > 0 && (!points || !counts || !keep)) || !zrange)
+    return fail(GS_ERR_ARG, "gs_visibility_bounds: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  int* tmp = static_cast<int*>(al.get(2 * sizeof(int), st));
+  if (!tmp) return fail(GS_ERR_OOM, "gs_visibility_bounds: scratch allocation failed");
+  const cudaError_t e = launch_visibility_keep(points, n, counts, min_count, keep, zrange, tmp, st);
+  al.put(tmp, 2 * sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_visibility_bounds");
+  return GS_OK;
+}
+
 gs_status gs_sync(void* stream, int32_t timeout_ms) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {

@@ -283,6 +283,19 @@ cudaError_t launch_contribution(const CamDev& cam, const SetDev& set, float gamm
                                 const uint32_t* vals, const int2* ranges, const uint32_t* cand,
                                 const uint32_t* ncand, int64_t n, bool zero_cand, float* csum, uint32_t* ccnt,
                                 float* contrib, cudaStream_t st);
+// Visible frequency of points (Sec. 4.1 crop volume): a view as the count
+// kernel reads it (world-to-camera rotation row-major, translation,
+// intrinsics, image size).
+struct VisCam {
+  float R[9], t[3];
+  float fx, fy, cx, cy, W, H;
+};
+cudaError_t launch_visibility_count(const float* pts, int64_t n, float sigma, float lowpass, float near_plane,
+                                    const VisCam* cams, int nviews, uint32_t* counts, cudaStream_t st);
+// keep[j] = counts[j] >= min_count; zrange = (min z, max z) of the kept
+// points (NaN when none); tmp: 2 ints of device scratch.
+cudaError_t launch_visibility_keep(const float* pts, int64_t n, const uint32_t* counts, uint32_t min_count,
+                                   uint8_t* keep, float* zrange, int* tmp, cudaStream_t st);
 // Percentile pruning (Sec. 3.3): the k-th smallest value of contrib (k >= 1;
 // radix select on order-preserving keys), keep[i] = contrib[i] > it, the
 // bound to *bound (device, may be null); k = 0 keeps everything and writes

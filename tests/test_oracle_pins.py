@@ -645,7 +645,7 @@ def test_visibility_image_edge_closed_form():
         m = 0.5 * (a + b)
         a, b = (m, b) if left_edge(m) < 0 else (a, m)
     xe = 0.5 * (a + b)
-    pts = np.array([[xe * (1 - 1e-6), 0, z], [xe * (1 + 1e-6), 0, z]])
+    pts = np.array([[xe * (1 - 1e-4), 0, z], [xe * (1 + 1e-4), 0, z]])
     c, fl = oracle.visibility_count(pts, s, [cam], lowpass=lp)
     assert list(c) == [1, 0] and not fl.any()
 
