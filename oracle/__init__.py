@@ -320,3 +320,52 @@ def visible_height_range(points, count, min_count):
     if z.size == 0:
         return keep, (None, None)
     return keep, (float(z.min()), float(z.max()))
+
+
+def normal_loss(out, cam, weight=1.0):
+    """Depth-normal consistency (2DGS's surface smoothness term, weighted as in
+    Sec. 4.1): per pixel L = sum_i w_i (1 - n_i . N~) = A - N~ . N_r, with A the
+    alpha plane, N_r the rendered (weight-summed) normal and N~ the unit normal
+    of the surface seen at the pixel, from central differences of the points
+    P = median depth * (ray through the pixel centre) of its four neighbours,
+    oriented towards the camera.  Only interior pixels whose four neighbours
+    have a depth (> 0) and a non-degenerate cross product count.  Returns
+    (loss = weight * mean over all pixels, adjoint planes [11][H][W] with
+    d loss / d alpha, median, nx, ny, nz)."""
+    o = np.asarray(out, np.float64)
+    H, W = o.shape[1:]
+    A, med, Nr = o[3], o[6], o[7:10]
+    fx, fy, cx, cy = cam["fx"], cam["fy"], cam["cx"], cam["cy"]
+    xs = (np.arange(W) + 0.5 - cx) / fx
+    ys = (np.arange(H) + 0.5 - cy) / fy
+    ray = np.stack([np.broadcast_to(xs[None, :], (H, W)), np.broadcast_to(ys[:, None], (H, W)), np.ones((H, W))])
+    P = med[None] * ray
+    adj = np.zeros((ADJ_PLANES, H, W))
+    total = 0.0
+    s = weight / (H * W)
+    for j in range(1, H - 1):
+        for i in range(1, W - 1):
+            if min(med[j, i + 1], med[j, i - 1], med[j + 1, i], med[j - 1, i]) <= 0:
+                continue
+            a = P[:, j, i + 1] - P[:, j, i - 1]
+            b = P[:, j + 1, i] - P[:, j - 1, i]
+            c = np.cross(a, b)
+            cn = np.linalg.norm(c)
+            if cn == 0:
+                continue
+            sg = -1.0 if c @ ray[:, j, i] > 0 else 1.0
+            n = sg * c / cn
+            N = Nr[:, j, i]
+            total += A[j, i] - n @ N
+            adj[3, j, i] += s
+            adj[7:10, j, i] -= s * n
+            # d/dc of -n.N with n = sg c/|c|
+            chat = c / cn
+            gc = sg * (-(N - chat * (chat @ N))) / cn * s
+            ga = np.cross(b, gc)
+            gb = np.cross(gc, a)
+            adj[6, j, i + 1] += ray[:, j, i + 1] @ ga
+            adj[6, j, i - 1] -= ray[:, j, i - 1] @ ga
+            adj[6, j + 1, i] += ray[:, j + 1, i] @ gb
+            adj[6, j - 1, i] -= ray[:, j - 1, i] @ gb
+    return weight * total / (H * W), adj

@@ -688,3 +688,63 @@ def test_visible_height_range():
     pts = np.array([[0, 0, 1.0], [0, 0, 5.0], [0, 0, 3.0], [0, 0, 9.0]])
     keep, (lo, hi) = oracle.visible_height_range(pts, [5, 1, 3, 0], 2)
     assert list(keep) == [True, False, True, False] and (lo, hi) == (1.0, 3.0)
+
+
+# --------------------------------------------------------------------------
+# Depth-normal consistency (2DGS smoothness term, weight of Sec. 4.1)
+
+def _planar_out(H, W, cam, plane_n, plane_d, alpha=0.7):
+    """Render planes of an opaque plane n.X = d seen by cam: median depth from
+    the ray-plane intersection, rendered normal = alpha * (camera-facing n)."""
+    xs = (np.arange(W) + 0.5 - cam["cx"]) / cam["fx"]
+    ys = (np.arange(H) + 0.5 - cam["cy"]) / cam["fy"]
+    ray = np.stack([np.broadcast_to(xs[None], (H, W)), np.broadcast_to(ys[:, None], (H, W)), np.ones((H, W))])
+    t = plane_d / np.einsum("k,kij->ij", plane_n, ray)
+    out = np.zeros((12, H, W))
+    out[3] = alpha
+    out[6] = t
+    nf = -np.asarray(plane_n) if plane_d > 0 else np.asarray(plane_n)  # towards the camera
+    out[7:10] = alpha * nf[:, None, None]
+    return out, nf
+
+
+def test_normal_loss_vanishes_on_matching_planes():
+    cam = camera(24, 18, 20.0)
+    for n in ([0, 0, 1.0], [0.3, -0.2, 0.93]):
+        nv = np.asarray(n) / np.linalg.norm(n)
+        out, nf = _planar_out(18, 24, cam, nv, 4.0)
+        L, adj = oracle.normal_loss(out, cam, weight=1.0)
+        assert abs(L) < 1e-12
+        # the depth normal is the plane's normal wherever it is defined
+        assert np.allclose(adj[7:10, 1:-1, 1:-1], -nf[:, None, None] / (18 * 24))
+
+
+def test_normal_loss_closed_form_for_misaligned_normals():
+    """Rendered normals tilted by theta from the true plane normal: per
+    interior pixel A - A cos(theta)."""
+    cam = camera(20, 16, 18.0)
+    out, nf = _planar_out(16, 20, cam, np.array([0, 0, 1.0]), 5.0, alpha=0.8)
+    th = 0.3
+    out[7:10] = 0.8 * np.array([math.sin(th), 0.0, -math.cos(th)])[:, None, None]
+    L, _ = oracle.normal_loss(out, cam, weight=2.0)
+    interior = 14 * 18
+    assert abs(L - 2.0 * interior * 0.8 * (1 - math.cos(th)) / (16 * 20)) < 1e-12
+
+
+def test_normal_loss_gradient_by_finite_differences():
+    cam = camera(12, 10, 11.0)
+    rng = np.random.default_rng(5)
+    out, _ = _planar_out(10, 12, cam, np.array([0.2, 0.1, 0.97]), 3.0)
+    out[6] += rng.normal(0, 0.05, out[6].shape)
+    out[3] = rng.uniform(0.3, 1.0, out[3].shape)
+    out[7:10] += rng.normal(0, 0.2, out[7:10].shape)
+    L0, adj = oracle.normal_loss(out, cam, weight=0.5)
+    for plane in (3, 6, 7, 8, 9):
+        for _ in range(6):
+            j, i = rng.integers(10), rng.integers(12)
+            h = 1e-6
+            o1, o2 = out.copy(), out.copy()
+            o1[plane, j, i] += h
+            o2[plane, j, i] -= h
+            fd = (oracle.normal_loss(o1, cam, 0.5)[0] - oracle.normal_loss(o2, cam, 0.5)[0]) / (2 * h)
+            assert abs(fd - adj[plane, j, i]) < 1e-7 * max(1.0, abs(fd)), (plane, j, i, fd, adj[plane, j, i])
