@@ -369,3 +369,62 @@ def normal_loss(out, cam, weight=1.0):
             adj[6, j + 1, i] += ray[:, j + 1, i] @ gb
             adj[6, j - 1, i] -= ray[:, j - 1, i] @ gb
     return weight * total / (H * W), adj
+
+
+def adam_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15):
+    """One bias-corrected Adam update (FP64 copies): returns (param, m, v)."""
+    p, g = np.asarray(param, np.float64), np.asarray(grad, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1 - beta2) * g * g
+    mh, vh = m / (1 - beta1 ** step), v / (1 - beta2 ** step)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def densify_plan(select, scale, opacity, dense_thr, min_opacity):
+    """Clone / split / prune actions (0 drop, 1 keep, 2 clone, 3 split), the
+    first output row of each surfel and the number of output rows."""
+    sel = np.asarray(select).astype(bool)
+    smax = np.asarray(scale, np.float64).reshape(-1, 2).max(axis=1)
+    op = np.asarray(opacity, np.float64).reshape(-1)
+    action = np.where(sel, np.where(smax <= dense_thr, 2, 3), np.where(op < min_opacity, 0, 1)).astype(np.uint8)
+    rows = np.array([0, 1, 2, 2])[action]
+    offset = np.concatenate([[0], np.cumsum(rows)[:-1]]) if rows.size else rows
+    return action, offset.astype(np.int64), int(rows.sum())
+
+
+def densify_apply(scene, action, xi):
+    """Rows of the densified scene (rows in source order): keep copies the
+    surfel, clone copies it twice, split writes two children at
+    mu + t_u s_u xi_0 + t_v s_v xi_1 with scales s / 1.6.  Returns (scene dict,
+    src, fresh)."""
+    mu = np.asarray(scene["mu"], np.float64)
+    quat = np.asarray(scene["quat"], np.float64)
+    scale = np.asarray(scene["scale"], np.float64)
+    opac = np.asarray(scene["opacity"], np.float64).reshape(-1)
+    sh = np.asarray(scene["sh"], np.float64).reshape(mu.shape[0], -1)
+    xi = np.asarray(xi, np.float64).reshape(-1, 2, 2)
+    rows = {k: [] for k in ("mu", "quat", "scale", "opacity", "sh")}
+    src, fresh = [], []
+    for i, a in enumerate(action):
+        if a == 0:
+            continue
+        q = quat[i] / np.linalg.norm(quat[i])
+        w, x, y, z = q
+        tu = np.array([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)])
+        tv = np.array([2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)])
+        for c in range(1 if a == 1 else 2):
+            m, s = mu[i].copy(), scale[i].copy()
+            if a == 3:
+                m = m + tu * s[0] * xi[i, c, 0] + tv * s[1] * xi[i, c, 1]
+                s = s / 1.6
+            rows["mu"].append(m)
+            rows["quat"].append(quat[i])
+            rows["scale"].append(s)
+            rows["opacity"].append(opac[i])
+            rows["sh"].append(sh[i])
+            src.append(i)
+            fresh.append(1 if (a == 3 or (a == 2 and c == 1)) else 0)
+    out = {k: np.array(v) for k, v in rows.items()}
+    out["sh"] = out["sh"].reshape(-1, *np.asarray(scene["sh"]).shape[1:]) if out["sh"].size else out["sh"]
+    out["sh_degree"] = scene["sh_degree"]
+    return out, np.array(src, np.int64), np.array(fresh, np.uint8)

@@ -748,3 +748,39 @@ def test_normal_loss_gradient_by_finite_differences():
             o2[plane, j, i] -= h
             fd = (oracle.normal_loss(o1, cam, 0.5)[0] - oracle.normal_loss(o2, cam, 0.5)[0]) / (2 * h)
             assert abs(fd - adj[plane, j, i]) < 1e-7 * max(1.0, abs(fd)), (plane, j, i, fd, adj[plane, j, i])
+
+
+# --------------------------------------------------------------------------
+# Training loop: Adam, densification
+
+def test_adam_matches_torch_optim():
+    import torch
+    rng = np.random.default_rng(8)
+    p0 = rng.normal(size=50)
+    grads = [rng.normal(size=50) for _ in range(4)]
+    t = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=1e-2, betas=(0.9, 0.999), eps=1e-15)
+    p, m, v = p0.copy(), np.zeros(50), np.zeros(50)
+    for k, g in enumerate(grads, start=1):
+        t.grad = torch.tensor(g)
+        opt.step()
+        p, m, v = oracle.adam_step(p, g, m, v, 1e-2, k)
+    assert np.abs(p - t.detach().numpy()).max() < 1e-14
+
+
+def test_densify_plan_and_apply_hand_checked():
+    scene = dict(mu=np.array([[0, 0, 1.0], [1, 0, 1], [2, 0, 1], [3, 0, 1]]),
+                 quat=np.array([[1.0, 0, 0, 0]] * 4),
+                 scale=np.array([[0.1, 0.2], [0.5, 0.3], [0.1, 0.1], [0.1, 0.1]]),
+                 opacity=np.array([0.5, 0.5, 0.001, 0.5]), sh=np.arange(12.0).reshape(4, 1, 3), sh_degree=0)
+    sel = np.array([1, 1, 0, 0])
+    action, offset, n_out = oracle.densify_plan(sel, scene["scale"], scene["opacity"], 0.3, 0.005)
+    assert list(action) == [2, 3, 0, 1] and list(offset) == [0, 2, 4, 4] and n_out == 5
+    xi = np.zeros((4, 2, 2))
+    xi[1] = [[1.0, 0.0], [0.0, -2.0]]
+    out, src, fresh = oracle.densify_apply(scene, action, xi)
+    assert list(src) == [0, 0, 1, 1, 3] and list(fresh) == [0, 1, 1, 1, 0]
+    # identity rotation: t_u = x, t_v = y; child 0 moves by s_u along x, child 1 by -2 s_v along y
+    assert np.allclose(out["mu"][2], [1.5, 0, 1]) and np.allclose(out["mu"][3], [1, -0.6, 1])
+    assert np.allclose(out["scale"][2], [0.5 / 1.6, 0.3 / 1.6]) and np.allclose(out["scale"][0], [0.1, 0.2])
+    assert np.array_equal(out["sh"][4], scene["sh"][3])
