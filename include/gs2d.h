@@ -258,6 +258,78 @@ gs_status gs_densify_select(int64_t n, const float* stats, const float* scale, f
 gs_status gs_elongation_filter(int64_t n, const float* scale, float eta_thr, uint8_t* keep,
                                void* stream);
 
+/* ---- Training-loop terms --------------------------------------------------
+ *
+ * gs_geometry_loss: the geometric terms that 2DGS adds to the loss and the
+ * paper keeps (Sec. 3.1; weights in Sec. 4.1: 0.0125 for the normal term, 0
+ * for the distortion).  Depth-normal consistency, per pixel L = A - N~ . N_r:
+ * A the alpha plane, N_r the rendered normal planes (weight-summed, view
+ * space) and N~ the unit normal of the surface at the pixel, the cross product
+ * of the central differences of the points P = median depth * (ray through the
+ * pixel centre) of its four neighbours, turned towards the camera; interior
+ * pixels whose four neighbours have a depth and a non-degenerate cross product
+ * count.  Depth distortion: the distortion plane.  losses (device FP32 [2]) =
+ * (w_normal * mean of L, w_dist * mean of the distortion plane) over all W*H
+ * pixels; their adjoints (alpha, median, normal, distortion planes) are ADDED
+ * to adj (device FP32 [11][H][W]); out is a render ([12][H][W]) of `cam`
+ * (W x H).  Asynchronous; allocates 16 B per pixel of scratch.
+ *
+ * gs_adam_step: one bias-corrected Adam update of n FP32 values in place:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps);
+ * step >= 1 counts updates from 1.  Asynchronous. */
+gs_status gs_geometry_loss(int32_t W, int32_t H, const gs_camera* cam, const float* out, float w_normal,
+                           float w_dist, float* adj, float* losses, void* stream);
+
+/* Densification: the clone / split / prune step of the training schedule the
+ * paper keeps from CityGaussian (Sec. 4.1), driven by the selection of Eq. 2
+ * and the elongation filter (Sec. 3.2).
+ *
+ * gs_densify_plan: per surfel an action (device uint8 [n]): 0 drop, 1 keep,
+ * 2 clone, 3 split.  A surfel with select[i] != 0 and (keep NULL or keep[i] !=
+ * 0) (select: gs_densify_select's mask; keep: gs_elongation_filter's) is
+ * cloned when max(scale) <= dense_thr and split otherwise; any other is
+ * dropped when opacity < min_opacity, else kept.  raw != 0: scale holds
+ * log-scales and opacity logits (the thresholds are mapped accordingly).  offset (device uint32 [n]) = the first output row of each surfel
+ * (rows follow the source order: keep 1 row, clone 2 (itself, then the copy),
+ * split 2 children, drop 0); *n_out (host) = the number of output rows.  Reads
+ * that count back (synchronises the stream).
+ *
+ * gs_densify_apply: writes the n_out rows (device arrays of the same layouts as
+ * the scene parameters, activated scale and opacity).  A split child j of
+ * surfel i sits at mu + t_u s_u xi[i][j][0] + t_v s_v xi[i][j][1] (t_u, t_v the
+ * first two columns of the surfel's rotation; xi device FP32 [n][2][2], the
+ * caller's standard normal draws) with scales s / 1.6 (log-scales minus ln 1.6
+ * when raw != 0); everything else is copied.  src[r] (device int32 [n_out]) = the source surfel of row r;
+ * fresh[r] (device uint8 [n_out]) = 1 for rows whose optimizer state starts
+ * afresh (clone copies and split children).
+ *
+ * gs_gather_rows: out[r][k] = fresh[r] ? 0 : in[src[r]][k] for width k
+ * (fresh may be NULL: no row is fresh); remaps per-surfel state (optimizer
+ * moments, accumulators) after densification.
+ *
+ * gs_activate / gs_activate_grad: the trained parametrisation scale =
+ * exp(log_scale) ([n][2]), opacity = sigmoid(logit) ([n]), and the chain of
+ * gradients through it in place (grad_scale *= scale, grad_opacity *=
+ * opacity (1 - opacity)).  All asynchronous except gs_densify_plan. */
+gs_status gs_densify_plan(int64_t n, const uint8_t* select, const uint8_t* keep, const float* scale,
+                          const float* opacity, int32_t raw, float dense_thr, float min_opacity,
+                          uint8_t* action, uint32_t* offset, int64_t* n_out, void* stream);
+gs_status gs_densify_apply(int64_t n, int32_t sh_degree, int32_t raw, const uint8_t* action,
+                           const uint32_t* offset,
+                           const float* xi, const float* mu, const float* quat, const float* scale,
+                           const float* opacity, const float* sh, float* mu_out, float* quat_out,
+                           float* scale_out, float* opacity_out, float* sh_out, int32_t* src,
+                           uint8_t* fresh, void* stream);
+gs_status gs_gather_rows(int64_t n_out, int32_t width, const int32_t* src, const uint8_t* fresh,
+                         const float* in, float* out, void* stream);
+gs_status gs_activate(int64_t n, const float* log_scale, const float* logit_opacity, float* scale,
+                      float* opacity, void* stream);
+gs_status gs_activate_grad(int64_t n, const float* scale, const float* opacity, float* grad_scale,
+                           float* grad_opacity, void* stream);
+gs_status gs_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float beta1,
+                       float beta2, float eps, int32_t step, void* stream);
+
 /* ---- Trim contribution and pruning (Sec. 3.3) ------------------------------
  *
  * gs_contribution: the single-view contribution of every surfel, Eq. 3,

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -120,6 +121,17 @@ _SIGS = {
     "gs_visibility_count": [ctypes.c_int64, _V, ctypes.c_float, _V, ctypes.c_int32, ctypes.c_float,
                             ctypes.c_float, _V, _V],
     "gs_visibility_bounds": [ctypes.c_int64, _V, _V, ctypes.c_uint32, _V, _V, _V],
+    "gs_geometry_loss": [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(gs_camera), _V, ctypes.c_float,
+                         ctypes.c_float, _V, _V, _V],
+    "gs_adam_step": [ctypes.c_int64, _V, _V, _V, _V, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                     ctypes.c_float, ctypes.c_int32, _V],
+    "gs_densify_plan": [ctypes.c_int64, _V, _V, _V, _V, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _V, _V,
+                        ctypes.POINTER(ctypes.c_int64), _V],
+    "gs_densify_apply": [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _V, _V, _V, _V, _V, _V, _V, _V, _V, _V,
+                         _V, _V, _V, _V, _V, _V],
+    "gs_gather_rows": [ctypes.c_int64, ctypes.c_int32, _V, _V, _V, _V, _V],
+    "gs_activate": [ctypes.c_int64, _V, _V, _V, _V, _V],
+    "gs_activate_grad": [ctypes.c_int64, _V, _V, _V, _V, _V],
     "gs_sync": [_V, ctypes.c_int32],
     "gs_profile_enable": [ctypes.c_int32],
     "gs_server_create": [ctypes.POINTER(_V), ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(gs_allocator)],
@@ -430,6 +442,97 @@ def prune_by_contribution(contrib, ratio, stream=None):
     _check(_lib.gs_prune_by_contribution(n, _ptr(contrib, shape=(n,), name="contrib"), float(ratio),
                                          _ptr(keep, torch.uint8), _ptr(bound), _stream(stream)))
     return keep, bound
+
+
+def geometry_loss(out, cam, w_normal, w_dist, adj, stream=None):
+    """Depth-normal consistency and depth distortion terms: adds their adjoints
+    into adj [11,H,W] and returns the two losses as a device tensor [2]."""
+    H, W = int(cam["height"]), int(cam["width"])
+    losses = torch.empty(2, dtype=torch.float32, device=out.device)
+    c = make_camera(cam)
+    _check(_lib.gs_geometry_loss(W, H, ctypes.byref(c), _ptr(out, shape=(OUT_PLANES, H, W), name="out"),
+                                 float(w_normal), float(w_dist), _ptr(adj, shape=(ADJ_PLANES, H, W), name="adj"),
+                                 _ptr(losses), _stream(stream)))
+    return losses
+
+
+def adam_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """One Adam update of `param` in place (all FP32 CUDA tensors of one shape)."""
+    n = param.numel()
+    for name, t in (("grad", grad), ("m", m), ("v", v)):
+        if t.numel() != n:
+            raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    _check(_lib.gs_adam_step(n, _ptr(param, name="param"), _ptr(grad, name="grad"), _ptr(m, name="m"),
+                             _ptr(v, name="v"), float(lr), float(beta1), float(beta2), float(eps), int(step),
+                             _stream(stream)))
+
+
+def densify_plan(select, scale, opacity, dense_thr, min_opacity, keep=None, raw=False, stream=None):
+    """Clone / split / prune actions, first output rows and the output row
+    count (synchronises).  raw: scale holds log-scales, opacity logits."""
+    n = scale.shape[0]
+    dev = scale.device
+    action = torch.empty(n, dtype=torch.uint8, device=dev)
+    offset = torch.empty(n, dtype=torch.int32, device=dev)
+    n_out = ctypes.c_int64()
+    _check(_lib.gs_densify_plan(n, _ptr(select, torch.uint8, (n,), "select"),
+                                _ptr(keep, torch.uint8, (n,), "keep") if keep is not None else None,
+                                _ptr(scale, shape=(n, 2), name="scale"), _ptr(opacity, shape=(n,), name="opacity"),
+                                int(bool(raw)), float(dense_thr), float(min_opacity), _ptr(action, torch.uint8),
+                                _ptr(offset, torch.int32), ctypes.byref(n_out), _stream(stream)))
+    return action, offset, int(n_out.value)
+
+
+def densify_apply(params: dict, sh_degree, action, offset, n_out, xi, raw=False, stream=None):
+    """Rows of the densified scene: returns (new params dict, src, fresh).
+    raw: params["scale"] holds log-scales (opacity is copied either way)."""
+    n = params["mu"].shape[0]
+    dev = params["mu"].device
+    K = (sh_degree + 1) ** 2
+    out = {"mu": torch.empty((n_out, 3), device=dev), "quat": torch.empty((n_out, 4), device=dev),
+           "scale": torch.empty((n_out, 2), device=dev), "opacity": torch.empty(n_out, device=dev),
+           "sh": torch.empty((n_out, K, 3), device=dev)}
+    src = torch.empty(n_out, dtype=torch.int32, device=dev)
+    fresh = torch.empty(n_out, dtype=torch.uint8, device=dev)
+    if n_out == 0:
+        return out, src, fresh
+    _check(_lib.gs_densify_apply(n, int(sh_degree), int(bool(raw)), _ptr(action, torch.uint8, (n,), "action"),
+                                 _ptr(offset, torch.int32, (n,), "offset"), _ptr(xi, shape=(n, 2, 2), name="xi"),
+                                 *[_ptr(params[k], name=k) for k in ("mu", "quat", "scale", "opacity", "sh")],
+                                 *[_ptr(out[k], name=k) for k in ("mu", "quat", "scale", "opacity", "sh")],
+                                 _ptr(src, torch.int32), _ptr(fresh, torch.uint8), _stream(stream)))
+    return out, src, fresh
+
+
+def gather_rows(src, fresh, t, stream=None):
+    """Rows src of t (first dimension), zero where fresh (may be None)."""
+    n_out = src.shape[0]
+    width = t[0].numel() if t.shape[0] else int(np.prod(t.shape[1:]))
+    out = torch.empty((n_out,) + tuple(t.shape[1:]), dtype=torch.float32, device=t.device)
+    _check(_lib.gs_gather_rows(n_out, width, _ptr(src, torch.int32), _ptr(fresh, torch.uint8) if fresh is not None
+                               else None, _ptr(t, name="rows"), _ptr(out), _stream(stream)))
+    return out
+
+
+def activate(log_scale, logit_opacity, scale=None, opacity=None, stream=None):
+    """scale = exp(log_scale), opacity = sigmoid(logit_opacity), into the given
+    tensors (new ones when None)."""
+    n = log_scale.shape[0]
+    scale = torch.empty_like(log_scale) if scale is None else scale
+    opacity = torch.empty_like(logit_opacity) if opacity is None else opacity
+    _check(_lib.gs_activate(n, _ptr(log_scale, shape=(n, 2), name="log_scale"),
+                            _ptr(logit_opacity, shape=(n,), name="logit_opacity"),
+                            _ptr(scale, shape=(n, 2), name="scale"), _ptr(opacity, shape=(n,), name="opacity"),
+                            _stream(stream)))
+    return scale, opacity
+
+
+def activate_grad(scale, opacity, grad_scale, grad_opacity, stream=None):
+    """Gradients w.r.t. the activated values -> w.r.t. log-scale and logit, in place."""
+    n = scale.shape[0]
+    _check(_lib.gs_activate_grad(n, _ptr(scale, shape=(n, 2), name="scale"), _ptr(opacity, shape=(n,), name="opacity"),
+                                 _ptr(grad_scale, shape=(n, 2), name="grad_scale"),
+                                 _ptr(grad_opacity, shape=(n,), name="grad_opacity"), _stream(stream)))
 
 
 def visibility_count(points, sigma, cams, counts=None, near_plane=0.2, lowpass=0.3, stream=None):

@@ -714,6 +714,109 @@ gs_status gs_visibility_bounds(int64_t n, const float* points, const uint32_t* c
   return GS_OK;
 }
 
+gs_status gs_geometry_loss(int32_t W, int32_t H, const gs_camera* cam, const float* out, float w_normal,
+                           float w_dist, float* adj, float* losses, void* stream) {
+  if (W <= 0 || H <= 0 || !cam || !out || !adj || !losses) return fail(GS_ERR_ARG, "gs_geometry_loss: bad argument");
+  if (cam->width != W || cam->height != H || !(cam->fx > 0) || !(cam->fy > 0))
+    return fail(GS_ERR_ARG, "gs_geometry_loss: camera does not match the image");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  const size_t bytes = geometry_tmp_bytes(W, H);
+  void* tmp = al.get(bytes, st);
+  if (!tmp) return fail(GS_ERR_OOM, "gs_geometry_loss: scratch allocation failed");
+  const cudaError_t e = launch_geometry_loss(W, H, (float)cam->fx, (float)cam->fy, (float)cam->cx, (float)cam->cy,
+                                             out, w_normal, w_dist, adj, losses, tmp, st);
+  al.put(tmp, bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_geometry_loss");
+  return GS_OK;
+}
+
+gs_status gs_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float beta1,
+                       float beta2, float eps, int32_t step, void* stream) {
+  if (n < 0 || (n > 0 && (!param || !grad || !m || !v)) || step < 1 || !(beta1 >= 0.f && beta1 < 1.f) ||
+      !(beta2 >= 0.f && beta2 < 1.f))
+    return fail(GS_ERR_ARG, "gs_adam_step: bad argument");
+  const double bc1 = 1.0 - pow((double)beta1, step), bc2 = 1.0 - pow((double)beta2, step);
+  const cudaError_t e = launch_adam(n, param, grad, m, v, lr, beta1, beta2, eps, (float)bc1, (float)bc2,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_adam_step");
+  return GS_OK;
+}
+
+gs_status gs_densify_plan(int64_t n, const uint8_t* select, const uint8_t* keep, const float* scale,
+                          const float* opacity, int32_t raw, float dense_thr, float min_opacity, uint8_t* action,
+                          uint32_t* offset, int64_t* n_out, void* stream) {
+  if (n < 0 || !n_out || (n > 0 && (!select || !scale || !opacity || !action || !offset)))
+    return fail(GS_ERR_ARG, "gs_densify_plan: bad argument");
+  *n_out = 0;
+  if (n == 0) return GS_OK;
+  if (n >= (int64_t(1) << 31)) return fail(GS_ERR_CAPACITY, "gs_densify_plan: more than 2^31 surfels");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  const size_t words = (size_t)n + scan_tmp_words(n) + 2;
+  uint32_t* tmp = static_cast<uint32_t*>(al.get(words * 4, st));
+  if (!tmp) return fail(GS_ERR_OOM, "gs_densify_plan: scratch allocation failed");
+  uint32_t* rows = tmp;
+  uint32_t* total = tmp + n;
+  uint32_t* stmp = total + 1;
+  // raw parametrisation (log-scale, logit-opacity): the thresholds move with it
+  const float thr_s = raw ? (float)log((double)dense_thr) : dense_thr;
+  const float thr_o = raw ? (float)log((double)min_opacity / (1.0 - (double)min_opacity)) : min_opacity;
+  cudaError_t e = launch_densify_plan(n, select, keep, scale, opacity, thr_s, thr_o, action, rows, st);
+  if (e == cudaSuccess) e = launch_scan(rows, offset, n, total, stmp, st);
+  uint32_t h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, total, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  al.put(tmp, words * 4, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_densify_plan");
+  *n_out = h;
+  return GS_OK;
+}
+
+gs_status gs_densify_apply(int64_t n, int32_t sh_degree, int32_t raw, const uint8_t* action,
+                           const uint32_t* offset, const float* xi, const float* mu, const float* quat, const float* scale,
+                           const float* opacity, const float* sh, float* mu_out, float* quat_out, float* scale_out,
+                           float* opacity_out, float* sh_out, int32_t* src, uint8_t* fresh, void* stream) {
+  if (n < 0 || sh_degree < 0 || sh_degree > 3 ||
+      (n > 0 && (!action || !offset || !xi || !mu || !quat || !scale || !opacity || !sh || !mu_out || !quat_out ||
+                 !scale_out || !opacity_out || !sh_out || !src || !fresh)))
+    return fail(GS_ERR_ARG, "gs_densify_apply: bad argument");
+  const cudaError_t e = launch_densify_apply(n, sh_degree, raw != 0, action, offset, xi, mu, quat, scale, opacity, sh,
+                                             mu_out, quat_out, scale_out, opacity_out, sh_out, src, fresh,
+                                             (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_densify_apply");
+  return GS_OK;
+}
+
+gs_status gs_gather_rows(int64_t n_out, int32_t width, const int32_t* src, const uint8_t* fresh, const float* in,
+                         float* out, void* stream) {
+  if (n_out < 0 || width < 0 || (n_out > 0 && width > 0 && (!src || !in || !out)))
+    return fail(GS_ERR_ARG, "gs_gather_rows: bad argument");
+  const cudaError_t e = launch_gather_rows(n_out, width, src, fresh, in, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_gather_rows");
+  return GS_OK;
+}
+
+gs_status gs_activate(int64_t n, const float* log_scale, const float* logit_opacity, float* scale, float* opacity,
+                      void* stream) {
+  if (n < 0 || (n > 0 && (!log_scale || !logit_opacity || !scale || !opacity)))
+    return fail(GS_ERR_ARG, "gs_activate: bad argument");
+  const cudaError_t e = launch_activate(n, log_scale, logit_opacity, scale, opacity, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_activate");
+  return GS_OK;
+}
+
+gs_status gs_activate_grad(int64_t n, const float* scale, const float* opacity, float* grad_scale, float* grad_opacity,
+                           void* stream) {
+  if (n < 0 || (n > 0 && (!scale || !opacity || !grad_scale || !grad_opacity)))
+    return fail(GS_ERR_ARG, "gs_activate_grad: bad argument");
+  const cudaError_t e = launch_activate_grad(n, scale, opacity, grad_scale, grad_opacity, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "gs_activate_grad");
+  return GS_OK;
+}
+
 gs_status gs_sync(void* stream, int32_t timeout_ms) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {

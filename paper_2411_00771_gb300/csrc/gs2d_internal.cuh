@@ -296,6 +296,29 @@ cudaError_t launch_visibility_count(const float* pts, int64_t n, float sigma, fl
 // points (NaN when none); tmp: 2 ints of device scratch.
 cudaError_t launch_visibility_keep(const float* pts, int64_t n, const uint32_t* counts, uint32_t min_count,
                                    uint8_t* keep, float* zrange, int* tmp, cudaStream_t st);
+// Geometric loss terms (see train.cu): depth-normal consistency and depth
+// distortion; adds their adjoints to adj ([11][H][W]) and writes loss[0..1];
+// tmp: geometry_tmp_bytes(W, H).
+size_t geometry_tmp_bytes(int W, int H);
+cudaError_t launch_geometry_loss(int W, int H, float fx, float fy, float cx, float cy, const float* out,
+                                 float w_normal, float w_dist, float* adj, float* loss, void* tmp, cudaStream_t st);
+// Bias-corrected Adam step (bc1 = 1 - beta1^t, bc2 = 1 - beta2^t).
+cudaError_t launch_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2,
+                        float eps, float bc1, float bc2, cudaStream_t st);
+// Densification actions (0 drop, 1 keep, 2 clone, 3 split) and output row
+// counts; the rows themselves; row gather (fresh rows zero); activations.
+cudaError_t launch_densify_plan(int64_t n, const uint8_t* sel, const uint8_t* keep, const float* scale,
+                                const float* opac, float dense_thr, float min_opacity, uint8_t* action, uint32_t* rows,
+                                cudaStream_t st);
+cudaError_t launch_densify_apply(int64_t n, int sh_degree, bool log_scale, const uint8_t* action, const uint32_t* off,
+                                 const float* xi, const float* mu, const float* quat, const float* scale,
+                                 const float* opac, const float* sh, float* mu_o, float* quat_o, float* scale_o,
+                                 float* opac_o, float* sh_o, int32_t* src, uint8_t* fresh, cudaStream_t st);
+cudaError_t launch_gather_rows(int64_t n_out, int width, const int32_t* src, const uint8_t* fresh, const float* in,
+                               float* out, cudaStream_t st);
+cudaError_t launch_activate(int64_t n, const float* ls, const float* lo, float* scale, float* opac, cudaStream_t st);
+cudaError_t launch_activate_grad(int64_t n, const float* scale, const float* opac, float* gs, float* go,
+                                 cudaStream_t st);
 // Percentile pruning (Sec. 3.3): the k-th smallest value of contrib (k >= 1;
 // radix select on order-preserving keys), keep[i] = contrib[i] > it, the
 // bound to *bound (device, may be null); k = 0 keeps everything and writes
