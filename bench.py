@@ -43,8 +43,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_HZ / 1e12
 # DRAM bytes (read + write) of one blend_bwd launch on this workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the
 # full-size view); valid only for the kernel sources it was taken on.
-BLEND_BWD_TRAFFIC = {"bytes": 173731584 + 12451072,
-                     "sources_sha256": "f425e582ecc3e9b07177ae1dc450ab8a9022c2225a6c2c6abb84437e1e26821a"}
+BLEND_BWD_TRAFFIC = {"bytes": 173771776 + 12999168,
+                     "sources_sha256": "cbc1781d81031741df3176646b9550829533aaa9e6dccdf3077d677d0d56533d"}
 
 
 def blend_bwd_traffic():
@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--width", type=int, default=1600, help="view width (smaller views for ncu captures)")
     ap.add_argument("--height", type=int, default=900)
+    ap.add_argument("--no-training", action="store_true", help="skip the 4M-surfel training-step measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-seconds", type=float, default=8.0)
     return ap.parse_args()
@@ -279,6 +280,7 @@ def run_ours(args):
 
     contribution = measure_contribution(sc, cam, n, dev, args)
     visibility = measure_visibility(scene_np, dev, args)
+    training = None if args.no_training else measure_training(dev, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -310,6 +312,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "contribution": contribution,
             "visibility": visibility,
+            "training": training,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -348,6 +351,51 @@ def measure_contribution(sc, cam, n, dev, args):
     return {"ms_per_view": round(ms_view, 4), "gamma": 0.5, "launches_per_view": launches,
             "prune_ms": round(e0.elapsed_time(e1) / reps, 4), "prune_ratio": 0.025,
             "pruned": int(n - int(keep.sum().item()))}
+
+
+def measure_training(dev, args):
+    """The training step of the 4M-surfel configuration: 4 views at 1600x900
+    from random poses on an orbit 200 m up, the full loss (L1, SSIM, depth,
+    normal consistency, distortion), the hand backward with the preprocess
+    recomputed, densification statistics and the FP32 Adam update, timed with
+    CUDA events: through torch.autograd (activate, render and loss as
+    autograd Functions, one backward()) and by the direct calls."""
+    import numpy as np
+    import torch
+    from paper_2411_00771_gb300 import synthetic as syn
+    from paper_2411_00771_gb300 import training as T
+    scene, info = syn.city_scene(seed=20241101 + 3, n=4_000_000)
+    rng = np.random.default_rng(20241101 + 4)
+    views = []
+    for _ in range(4):
+        cam = syn.orbit_camera(rng, 1600, 900, radius=rng.uniform(150.0, 250.0), altitude=200.0)
+        tgt, tinv = syn.city_targets(info, cam)
+        views.append((cam, torch.from_numpy(tgt).to(dev), torch.from_numpy(tinv).to(dev)))
+    P = {k: torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(dev) for k in ("mu", "quat", "scale",
+                                                                                          "opacity", "sh")}
+    tr = T.Trainer(P["mu"], P["quat"], torch.log(P["scale"]), torch.logit(P["opacity"].clamp(1e-6, 1 - 1e-6)),
+                   P["sh"], scene["sh_degree"], w_normal=0.0125, w_dist=0.01)
+    del P
+    reps = max(3, min(args.steps, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = {}
+    for mode in ("autograd", "direct"):
+        for _ in range(3):
+            tr.step(views, autograd=mode == "autograd")
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            L = tr.step(views, autograd=mode == "autograd")
+        e1.record()
+        torch.cuda.synchronize()
+        ms[mode] = e0.elapsed_time(e1) / reps
+    out = {"surfels": tr.n, "views_per_step": 4, "resolution": [1600, 900], "step": "autograd.Function",
+           "ms_per_step": round(ms["autograd"], 3), "steps_per_s": round(1e3 / ms["autograd"], 2),
+           "ms_per_step_direct": round(ms["direct"], 3), "steps": reps,
+           "loss_total": round(float(L[3]) / 4, 5)}
+    del tr, views
+    torch.cuda.empty_cache()
+    return out
 
 
 VIS_POINTS, VIS_VIEWS = 31_400_000, 958

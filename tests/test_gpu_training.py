@@ -125,9 +125,11 @@ def test_autograd_render_matches_oracle_backward():
         assert gu.rel_err(g, ref[k].reshape(g.shape)) <= 1e-3, k
 
 
-def test_training_loss_gradient_against_finite_differences():
-    """Config-2 loss (L1, SSIM, depth, normal consistency, distortion) through
-    the trained parametrisation (log-scale, logit-opacity): the GPU gradient
+@pytest.mark.parametrize("autograd", [False, True])
+def test_training_loss_gradient_against_finite_differences(autograd):
+    """The 4M-surfel configuration's loss (L1, SSIM, depth, normal
+    consistency, distortion) through the trained parametrisation (log-scale,
+    logit-opacity): the GPU gradient, by the direct step or by autograd,
     against central FD of the FP64 oracle on a 64-surfel subset."""
     from paper_2411_00771_gb300 import binding as B
     from paper_2411_00771_gb300 import training as T
@@ -139,9 +141,10 @@ def test_training_loss_gradient_against_finite_differences():
     logit = torch.logit(d["opacity"]).contiguous()
     tr = T.Trainer(d["mu"], d["quat"], log_s, logit, d["sh"], scene["sh_degree"], lr=dict(mu=0, quat=0, scale=0,
                    opacity=0, sh=0), w_normal=wn, w_dist=wdist, depth_weights=(0.5, 0.5))
-    tr.step([(cam, torch.from_numpy(tgt).cuda(), torch.from_numpy(tinv).cuda())])
+    tr.step([(cam, torch.from_numpy(tgt).cuda(), torch.from_numpy(tinv).cuda())], autograd=autograd)
     torch.cuda.synchronize()
-    grads = {k: v.cpu().numpy().astype(np.float64) for k, v in tr.grads.items()}
+    src = {k: tr.raw[k].grad for k in T.PARAMS} if autograd else tr.grads
+    grads = {k: v.detach().cpu().numpy().astype(np.float64) for k, v in src.items()}
     s64 = {k: (np.asarray(v, np.float64) if isinstance(v, np.ndarray) else v) for k, v in scene.items()}
     raw = {"scale": np.log(s64["scale"]), "opacity": np.log(s64["opacity"] / (1 - s64["opacity"]))}
 
@@ -202,3 +205,64 @@ def test_trainer_reduces_the_loss_and_densifies():
     assert n1 == tr.n and n1 > 0
     L = tr.step([(cam, tgt, tinv)])
     assert math.isfinite(float(L[3]))
+
+
+def _two_views(n=3000, W=96, H=72):
+    scene, cam, tgt, tinv = syn.tiny_scene(seed=101, n=n, width=W, height=H, fx=float(W), sh_degree=2,
+                                           log_scale_range=(-3.5, -1.5))
+    cam2 = dict(cam)
+    yaw = 0.12
+    cy, sy = math.cos(yaw), math.sin(yaw)
+    cam2["R"] = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]]) @ np.asarray(cam["R"])
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    rng = np.random.default_rng(7)
+    tgt2 = rng.random(tgt.shape).astype(np.float32)
+    return scene, [(cam, t(tgt), t(tinv)), (cam2, t(tgt2), t(tinv))]
+
+
+def _trainer(scene, **kw):
+    from paper_2411_00771_gb300 import training as T
+    d = gu.to_dev(scene)
+    return T.Trainer(d["mu"], d["quat"], torch.log(d["scale"]).contiguous(), torch.logit(d["opacity"]).contiguous(),
+                     d["sh"], scene["sh_degree"], w_normal=0.05, w_dist=0.01, **kw)
+
+
+def test_autograd_step_equals_direct_step():
+    """The step built from the differentiable activate / render / loss and one
+    backward() over two views gives the direct step's losses, gradients,
+    densification statistics and Adam update (up to the order of FP32 sums)."""
+    from paper_2411_00771_gb300 import training as T
+    scene, views = _two_views()
+    a, b = _trainer(scene), _trainer(scene)
+    La = a.step(views)
+    Lb = b.step(views, autograd=True)
+    torch.cuda.synchronize()
+    assert torch.allclose(La, Lb, rtol=1e-6, atol=1e-9)
+    for k in T.PARAMS:
+        ga, gb = a.grads[k], b.raw[k].grad
+        assert float((ga - gb).norm() / ga.norm().clamp_min(1e-30)) <= 1e-5, k
+        assert torch.allclose(a.raw[k], b.raw[k].detach(), rtol=1e-5, atol=1e-7), k
+    assert torch.allclose(a.stats, b.stats, rtol=1e-5, atol=1e-9)
+    # a second step reuses the buffers and the moments
+    a.step(views)
+    b.step(views, autograd=True)
+    torch.cuda.synchronize()
+    for k in T.PARAMS:
+        assert torch.allclose(a.raw[k], b.raw[k].detach(), rtol=1e-5, atol=1e-7), k
+
+
+@pytest.mark.parametrize("autograd", [False, True])
+def test_statistics_take_each_views_own_screen_gradient(autograd):
+    """Eq. 2 sums, per view, the norm of that view's screen gradient: a
+    two-view step must add what two one-view steps add (with the updates
+    switched off so that both see the same parameters)."""
+    scene, views = _two_views()
+    zero = dict(mu=0.0, quat=0.0, scale=0.0, opacity=0.0, sh=0.0)
+    const = (0.5, 0.5)  # the same depth weight at every step count
+    a, b = _trainer(scene, lr=zero, depth_weights=const), _trainer(scene, lr=zero, depth_weights=const)
+    a.step(views, autograd=autograd)
+    b.step(views[:1], autograd=autograd)
+    b.step(views[1:], autograd=autograd)
+    torch.cuda.synchronize()
+    assert float(a.stats[:, 3].sum()) > 0
+    assert torch.allclose(a.stats, b.stats, rtol=1e-5, atol=1e-9)
