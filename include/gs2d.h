@@ -52,7 +52,7 @@ enum {
 
 /* Planes of a render, [GS_OUT_PLANES][H][W] FP32 (Eq. 1 of Sec. 3.1 for the
  * colour; Sec. 3.1 "2D Gaussian Splatting" for distortion and normal;
- * Sec. 3.2 for inverse depth; Sec. 4.1 for median depth):
+ * Sec. 3.2 for inverse depth; Sec. 5.1 for median depth):
  *   R, G, B       sum_i w_i c_i + T_final * bg, w_i = alpha_i prod_{j<i}(1 - alpha_j)
  *   ALPHA         sum_i w_i
  *   DEPTH         sum_i w_i z_i   (expected depth times alpha; divide by ALPHA)
@@ -261,7 +261,7 @@ gs_status gs_elongation_filter(int64_t n, const float* scale, float eta_thr, uin
 /* ---- Training-loop terms --------------------------------------------------
  *
  * gs_geometry_loss: the geometric terms that 2DGS adds to the loss and the
- * paper keeps (Sec. 3.1; weights in Sec. 4.1: 0.0125 for the normal term, 0
+ * paper keeps (Sec. 3.1; weights in Sec. 5.1: 0.0125 for the normal term, 0
  * for the distortion).  Depth-normal consistency, per pixel L = A - N~ . N_r:
  * A the alpha plane, N_r the rendered normal planes (weight-summed, view
  * space) and N~ the unit normal of the surface at the pixel, the cross product
@@ -282,7 +282,7 @@ gs_status gs_geometry_loss(int32_t W, int32_t H, const gs_camera* cam, const flo
                            float w_dist, float* adj, float* losses, void* stream);
 
 /* Densification: the clone / split / prune step of the training schedule the
- * paper keeps from CityGaussian (Sec. 4.1), driven by the selection of Eq. 2
+ * paper keeps from CityGaussian (Sec. 5.1), driven by the selection of Eq. 2
  * and the elongation filter (Sec. 3.2).
  *
  * gs_densify_plan: per surfel an action (device uint8 [n]): 0 drop, 1 keep,
@@ -365,7 +365,7 @@ gs_status gs_contribution(gs_scene* scene, const gs_camera* camera, float gamma,
 gs_status gs_prune_by_contribution(int64_t n, const float* contrib, double ratio, uint8_t* keep,
                                    float* bound, void* stream);
 
-/* ---- Visible frequency of points (Sec. 4.1, crop volume estimation) -------
+/* ---- Visible frequency of points (Sec. 4, crop volume estimation) -------
  *
  * gs_visibility_count: for each of n points (device FP32 [n][3], world
  * coordinates), ADDS to counts[j] (device uint32 [n]) the number of the

@@ -11,7 +11,7 @@ Passages followed: Eq. 1 (Sec. 3.1, alpha compositing), Sec. 3.1 (2D
 Gaussian surfels, L1 + D-SSIM), Sec. 3.2 (depth loss on inverse depth,
 elongation rate eta, Eq. 2 decomposed-gradient densification, antialiasing
 low-pass filter), Sec. 3.3 (Eq. 3 trim contribution, percentile pruning),
-Sec. 4.1 (median depth), of CityGaussianV2.
+Sec. 5.1 (median depth), of CityGaussianV2.
 """
 from __future__ import annotations
 
@@ -297,7 +297,7 @@ def prune_bound(contrib, ratio):
 
 
 def visibility_count(points, sigma, cams, near=0.2, lowpass=0.3):
-    """Visible frequency of points over views (Sec. 4.1 crop volume
+    """Visible frequency of points over views (Sec. 4 crop volume
     estimation).  Returns (count[N], flagged[N]): views where the point is
     visible, and views where a visibility decision was within 2e-6 (relative)
     of its threshold."""
@@ -314,7 +314,7 @@ def visibility_count(points, sigma, cams, near=0.2, lowpass=0.3):
 
 def visible_height_range(points, count, min_count):
     """Points seen in at least min_count views, and the lowest and highest
-    world z among them (Sec. 4.1); (None, None) when none remains."""
+    world z among them (Sec. 4); (None, None) when none remains."""
     keep = np.asarray(count) >= min_count
     z = np.asarray(points, np.float64).reshape(-1, 3)[keep, 2]
     if z.size == 0:
@@ -324,7 +324,7 @@ def visible_height_range(points, count, min_count):
 
 def normal_loss(out, cam, weight=1.0):
     """Depth-normal consistency (2DGS's surface smoothness term, weighted as in
-    Sec. 4.1): per pixel L = sum_i w_i (1 - n_i . N~) = A - N~ . N_r, with A the
+    Sec. 5.1): per pixel L = sum_i w_i (1 - n_i . N~) = A - N~ . N_r, with A the
     alpha plane, N_r the rendered (weight-summed) normal and N~ the unit normal
     of the surface seen at the pixel, from central differences of the points
     P = median depth * (ray through the pixel centre) of its four neighbours,

@@ -15,12 +15,12 @@
  *     normal terms are rendered alongside colour.
  *   - Sec. 3.2 (elongation filter paragraph): sub-pixel splats are handled by
  *     the antialiasing low-pass filter (object/screen-space max).
- *   - Sec. 4.1: median depth is rendered for geometry.
+ *   - Sec. 5.1: median depth is rendered for geometry.
  *   - Sec. 3.1: L1 + D-SSIM photometric loss; Sec. 3.2: depth loss on inverse
  *     depth; Sec. 3.2 Eq. 2: decomposed-gradient densification; Sec. 3.2:
  *     elongation rate eta = min(s)/max(s).
  *   - Sec. 3.3 Eq. 3: single-view trim contribution of each surfel.
- *   - Sec. 4.1: visible frequency of points (crop volume estimation).
+ *   - Sec. 4: visible frequency of points (crop volume estimation).
  * Readings where the paper is silent (pixel centres at +0.5, alpha clamp 0.99,
  * stop before the pair that would take T below T_min, the per-pair 3-sigma
  * support rho <= 9, screen filter rho_scr = 2 |x - c|^2, centre depth when the
@@ -1216,7 +1216,7 @@ int oracle_contribution(int64_t N, int deg, const double* mu, const double* quat
 }
 
 /* ---------------------------------------------------------------------- */
-/* Visible frequency of points (Sec. 4.1, crop volume estimation).         */
+/* Visible frequency of points (Sec. 4, crop volume estimation).         */
 
 /* Each point is an isotropic 3D Gaussian of standard deviation sigma.  In a
  * view (camera array as above) it is visible when it lies in front of the

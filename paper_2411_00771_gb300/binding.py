@@ -536,7 +536,7 @@ def activate_grad(scale, opacity, grad_scale, grad_opacity, stream=None):
 
 
 def visibility_count(points, sigma, cams, counts=None, near_plane=0.2, lowpass=0.3, stream=None):
-    """Visible frequency of points over views (Sec. 4.1): adds to `counts`
+    """Visible frequency of points over views (Sec. 4): adds to `counts`
     (int32 view of uint32 [N], zeros when None) the views in which each point
     is visible as an isotropic Gaussian primitive.  Returns counts."""
     n = points.shape[0]

@@ -283,7 +283,7 @@ cudaError_t launch_contribution(const CamDev& cam, const SetDev& set, float gamm
                                 const uint32_t* vals, const int2* ranges, const uint32_t* cand,
                                 const uint32_t* ncand, int64_t n, bool zero_cand, float* csum, uint32_t* ccnt,
                                 float* contrib, cudaStream_t st);
-// Visible frequency of points (Sec. 4.1 crop volume): a view as the count
+// Visible frequency of points (Sec. 4 crop volume): a view as the count
 // kernel reads it (world-to-camera rotation row-major, translation,
 // intrinsics, image size).
 struct VisCam {

@@ -2,13 +2,13 @@
 // loss (depth-normal consistency, depth distortion) and the Adam update.
 //
 // Normal consistency (2DGS's surface smoothness term, weight 0.0125 in
-// Sec. 4.1): per pixel L = A - N~ . N_r, where A is the rendered alpha, N_r the
+// Sec. 5.1): per pixel L = A - N~ . N_r, where A is the rendered alpha, N_r the
 // rendered (weight-summed) normal and N~ the unit normal of the surface seen
 // at the pixel: the cross product of the central differences of the points
 // P = median depth * ray of its four neighbours, turned towards the camera.
 // Interior pixels whose four neighbours have a depth and a non-degenerate
 // cross product count; the loss is weight * mean over all pixels.  The depth
-// distortion term (2DGS's, weight 0 in Sec. 4.1) is its weight times the mean
+// distortion term (2DGS's, weight 0 in Sec. 5.1) is its weight times the mean
 // of the rendered distortion plane.  Pass 1
 // (per pixel) adds the adjoints of A and N_r at the pixel and writes the
 // adjoint of each neighbour's depth; pass 2 (per pixel) gathers the depth
@@ -199,7 +199,7 @@ cudaError_t launch_adam(int64_t n, float* p, const float* g, float* m, float* v,
 
 // ---------------------------------------------------------------------------
 // Densification (the clone / split / prune of the training schedule the paper
-// keeps from CityGaussian, Sec. 4.1, with the selection of Eq. 2 and the
+// keeps from CityGaussian, Sec. 5.1, with the selection of Eq. 2 and the
 // elongation filter of Sec. 3.2):
 //   action 0  drop   (opacity below min_opacity, or a split parent),
 //          1  keep,

@@ -1,4 +1,4 @@
-// Visible frequency of points over many views (Sec. 4.1, crop volume
+// Visible frequency of points over many views (Sec. 4, crop volume
 // estimation): each ground-truth point is an isotropic 3D Gaussian of
 // standard deviation sigma, and its count is the number of views in which
 // the rasterizer would keep it: in front of the near plane, with the

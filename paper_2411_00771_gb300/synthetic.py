@@ -2,7 +2,7 @@
 
 This module holds no rasterizer arithmetic; it only draws inputs.  Both the
 CUDA path and the FP64 oracle consume what it produces.  The paper's data
-(GauU-Scene and MatrixCity aerial captures, Sec. 4.1) are not available, so
+(GauU-Scene and MatrixCity aerial captures, Sec. 5.1) are not available, so
 these generators stand in for them with the same shapes: aerial views whose
 longer side is 1600 px, city blocks of a few hundred metres, millions of
 surfels, SH degree 2-3.

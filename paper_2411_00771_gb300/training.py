@@ -3,7 +3,7 @@
 `render` is a torch.autograd.Function over gs_render / gs_backward (the
 backward recomputes the preprocess); `Trainer` runs the training step of the
 paper: the loss 0.8 L1 + 0.2 (1 - SSIM) + w_depth L_depth (Sec. 3.1, 3.2;
-w_depth decayed exponentially from 0.5 to 0.0025, Sec. 4.1) plus the
+w_depth decayed exponentially from 0.5 to 0.0025, Sec. 5.1) plus the
 depth-normal consistency (0.0125) and depth distortion (0) terms, the
 decomposed-gradient densification statistics (Eq. 2), the elongation filter
 (Sec. 3.2), clone / split / prune, and an FP32 Adam update of the

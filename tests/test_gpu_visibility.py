@@ -1,4 +1,4 @@
-"""Visible frequency of points (Sec. 4.1, crop volume estimation) on the GPU
+"""Visible frequency of points (Sec. 4, crop volume estimation) on the GPU
 against the FP64 oracle: counts exact wherever no decision was within the
 oracle's near-threshold margin, the keep mask and the height range exact."""
 import math

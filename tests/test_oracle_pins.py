@@ -618,7 +618,7 @@ def test_prune_bound_percentile():
 
 
 # --------------------------------------------------------------------------
-# Visible frequency of points (Sec. 4.1, crop volume estimation)
+# Visible frequency of points (Sec. 4, crop volume estimation)
 
 def test_visibility_on_axis_behind_and_near_plane():
     cam = camera(64, 48, 60.0)
@@ -691,7 +691,7 @@ def test_visible_height_range():
 
 
 # --------------------------------------------------------------------------
-# Depth-normal consistency (2DGS smoothness term, weight of Sec. 4.1)
+# Depth-normal consistency (2DGS smoothness term, weight of Sec. 5.1)
 
 def _planar_out(H, W, cam, plane_n, plane_d, alpha=0.7):
     """Render planes of an opaque plane n.X = d seen by cam: median depth from
