@@ -11,6 +11,8 @@ Passages followed: Eq. 1 (Sec. 3.1, alpha compositing), Sec. 3.1 (2D
 Gaussian surfels, L1 + D-SSIM), Sec. 3.2 (depth loss on inverse depth,
 elongation rate eta, Eq. 2 decomposed-gradient densification, antialiasing
 low-pass filter), Sec. 3.3 (Eq. 3 trim contribution, percentile pruning),
+Sec. 3.3 (contribution-based vector quantisation of SH; Appendix C for
+the codebook size and ratio), Sec. 4 (visible frequency for the crop volume),
 Sec. 5.1 (median depth), of CityGaussianV2.
 """
 from __future__ import annotations
@@ -428,3 +430,140 @@ def densify_apply(scene, action, xi):
     out["sh"] = out["sh"].reshape(-1, *np.asarray(scene["sh"]).shape[1:]) if out["sh"].size else out["sh"]
     out["sh_degree"] = scene["sh_degree"]
     return out, np.array(src, np.int64), np.array(fresh, np.uint8)
+
+
+# ---- Contribution-based vector quantisation of SH (Sec. 3.3; Appendix C) ----
+#
+# After the blocks are merged, each surfel's contribution over the training
+# views decides which SH vectors are quantised: the least important fraction
+# (ratio 0.4) gets its SH vector replaced by the nearest entry of a codebook
+# (8192 entries) fitted by K-means; the other SH vectors, and rotation, scale
+# and opacity of every surfel, are stored as IEEE binary16.  Readings: the
+# quantised set is the percentile rule of the prune (contribution at or below
+# the k-th smallest, k = ceil(ratio N)); a vector is the whole SH row (all
+# 3 (deg+1)^2 coefficients) rounded to binary16; K-means is Lloyd's algorithm
+# started from the vectors at rows floor(u_j m) of the quantised list (u_j the
+# caller's uniform draws), centroids rounded to binary16 after every update,
+# an empty cluster keeps its centroid; the last step assigns to the final
+# codebook.  Positions stay FP32 (binary16 cannot hold city coordinates to a
+# centimetre).
+
+def vq_quantized(contrib, ratio):
+    """Surfels whose SH is vector-quantised: the complement of the prune's keep."""
+    _, keep = prune_bound(contrib, ratio)
+    return ~keep
+
+
+def half(x):
+    """Round to IEEE binary16 (round to nearest, ties to even)."""
+    return np.asarray(x, np.float64).astype(np.float16)
+
+
+def vq_vectors(sh, quant):
+    """Rows of the quantised surfels' SH, flattened and rounded to binary16,
+    in surfel-index order."""
+    sh = np.asarray(sh)
+    rows = sh.reshape(sh.shape[0], -1)[np.asarray(quant, bool)]
+    return half(rows)
+
+
+def vq_init_rows(u, m):
+    """Rows of the quantised list that seed the codebook: floor(u_j m), u_j in
+    [0, 1) (FP32 draws, product taken in FP64), clamped to m - 1."""
+    u = np.asarray(u, np.float32).astype(np.float64)
+    return np.minimum(np.floor(u * m), m - 1).astype(np.int64)
+
+
+def vq_assign(x16, c16, flag_rel=2.0 ** -17, block=2048):
+    """Nearest codebook entry of every vector: argmin_j ||x - c_j||^2 (the
+    lowest j among equal distances), in FP64 on the binary16 values; scores
+    are ||c_j||^2 - 2 x . c_j, which orders j the same way.  flag[i] marks a
+    decision whose best and second-best scores lie within
+    2 flag_rel (max_j ||c_j||^2 + 2 sum_k |x_k| max_j |c_jk|): a single-precision
+    evaluation of the scores may pick either there.  Returns (assign, flag,
+    distance of each vector to its entry)."""
+    x = np.asarray(x16, np.float64)
+    c = np.asarray(c16, np.float64)
+    norms = (c * c).sum(1)
+    cmax = np.abs(c).max(0) if c.size else np.zeros(x.shape[1])
+    m = x.shape[0]
+    assign = np.zeros(m, np.int64)
+    flag = np.zeros(m, bool)
+    dist = np.zeros(m)
+    for s in range(0, m, block):
+        xs = x[s:s + block]
+        score = norms[None, :] - 2.0 * (xs @ c.T)
+        a = score.argmin(1)
+        assign[s:s + block] = a
+        best = score[np.arange(len(a)), a]
+        if c.shape[0] > 1:
+            two = np.partition(score, 1, axis=1)[:, :2]
+            gap = two[:, 1] - two[:, 0]
+            eps = 2.0 * flag_rel * (norms.max() + 2.0 * np.abs(xs) @ cmax)
+            flag[s:s + block] = gap <= eps
+        dist[s:s + block] = np.maximum(best + (xs * xs).sum(1), 0.0)
+    return assign, flag, dist
+
+
+def vq_update(x16, assign, c16):
+    """Centroid step: each entry becomes the mean of its vectors, rounded to
+    binary16; an entry with no vector keeps its value.  The sums are exact
+    (binary16 values are integer multiples of 2^-24, summed as int64), then
+    mean = (double(sum) * 2^-24) / count."""
+    x = np.asarray(x16, np.float64)
+    K, C = np.asarray(c16).shape
+    xi = np.rint(x * 2.0 ** 24).astype(np.int64)
+    sums = np.zeros((K, C), np.int64)
+    np.add.at(sums, np.asarray(assign, np.int64), xi)
+    cnt = np.bincount(np.asarray(assign, np.int64), minlength=K)
+    mean = sums.astype(np.float64) * 2.0 ** -24 / np.maximum(cnt, 1)[:, None]
+    return np.where(cnt[:, None] > 0, mean.astype(np.float16), np.asarray(c16, np.float16)), cnt
+
+
+def vq_kmeans(x16, u, iters):
+    """Lloyd's K-means (K = len(u)) from the seeded rows.  Returns (codebook
+    binary16 [K][C], final assignment, objective per assignment step (sum of
+    squared distances, iters + 1 values), flag of any near-tie per step)."""
+    x16 = np.asarray(x16, np.float16)
+    m = x16.shape[0]
+    c = x16[vq_init_rows(u, m)].copy()
+    objective, flags = [], []
+    for _ in range(iters):
+        a, fl, d = vq_assign(x16, c)
+        objective.append(d.sum())
+        flags.append(fl)
+        c, _ = vq_update(x16, a, c)
+    a, fl, d = vq_assign(x16, c)
+    objective.append(d.sum())
+    flags.append(fl)
+    return c, a, np.array(objective), flags
+
+
+def vq_compress(scene, quant, codebook, assign):
+    """Render layout of a compressed scene: mu FP32; quat, scale, opacity in
+    binary16; sh_row[i] = the codebook entry of a quantised surfel, else
+    K + its rank among the kept surfels; sh_table = codebook rows, then the
+    kept surfels' SH rows in binary16."""
+    quant = np.asarray(quant, bool)
+    n = quant.shape[0]
+    K = codebook.shape[0]
+    sh = np.asarray(scene["sh"]).reshape(n, -1)
+    kept = np.nonzero(~quant)[0]
+    sh_row = np.zeros(n, np.int64)
+    sh_row[quant] = np.asarray(assign, np.int64)
+    sh_row[kept] = K + np.arange(kept.size)
+    return {"mu": np.asarray(scene["mu"], np.float32), "quat": half(scene["quat"]), "scale": half(scene["scale"]),
+            "opacity": half(np.asarray(scene["opacity"]).reshape(-1)), "sh_row": sh_row,
+            "sh_table": np.concatenate([np.asarray(codebook, np.float16), half(sh[kept])]),
+            "sh_degree": scene["sh_degree"]}
+
+
+def vq_decompress(comp):
+    """The FP32 scene a compressed scene stands for (every binary16 value is
+    exact in FP32)."""
+    n = comp["sh_row"].shape[0]
+    deg = comp["sh_degree"]
+    return {"mu": comp["mu"].astype(np.float32), "quat": comp["quat"].astype(np.float32),
+            "scale": comp["scale"].astype(np.float32), "opacity": comp["opacity"].astype(np.float32),
+            "sh": comp["sh_table"][comp["sh_row"]].astype(np.float32).reshape(n, (deg + 1) ** 2, 3),
+            "sh_degree": deg}

@@ -784,3 +784,101 @@ def test_densify_plan_and_apply_hand_checked():
     assert np.allclose(out["mu"][2], [1.5, 0, 1]) and np.allclose(out["mu"][3], [1, -0.6, 1])
     assert np.allclose(out["scale"][2], [0.5 / 1.6, 0.3 / 1.6]) and np.allclose(out["scale"][0], [0.1, 0.2])
     assert np.array_equal(out["sh"][4], scene["sh"][3])
+
+
+# ---------------------------------------------------------------------------
+# Contribution-based vector quantisation of SH (Sec. 3.3; Appendix C)
+
+def _vq_data(m, C, seed, K=None):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0, 0.3, (m, C))
+    x[:, :3] += rng.uniform(-1, 1.5, (m, 1))      # DC-like offset shared by the colour channels
+    x[rng.random((m, C)) < 0.01] = 3e-6            # binary16 subnormals
+    x16 = oracle.half(x)
+    if K is None:
+        return x16
+    return x16, oracle.half(rng.normal(0, 0.3, (K, C)))
+
+
+def test_vq_assign_is_scipy_nearest_code():
+    from scipy.cluster.vq import vq
+    x16, c16 = _vq_data(3000, 48, 1, K=256)
+    a, flag, d = oracle.vq_assign(x16, c16)
+    ref, rdist = vq(x16.astype(np.float64), c16.astype(np.float64))
+    assert flag.mean() < 0.01
+    assert np.array_equal(a[~flag], ref[~flag])
+    assert np.allclose(np.sqrt(d), rdist, rtol=1e-9, atol=1e-9)
+
+
+def test_vq_update_is_the_rounded_cluster_mean():
+    x16, c16 = _vq_data(5000, 27, 2, K=64)
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 60, 5000)                  # entries 60..63 stay empty
+    new, cnt = oracle.vq_update(x16, a, c16)
+    for j in range(64):
+        rows = x16[a == j].astype(np.float64)
+        expect = c16[j] if rows.shape[0] == 0 else np.float16(rows.mean(0))
+        assert np.array_equal(new[j], expect), j
+        assert cnt[j] == rows.shape[0]
+
+
+def test_vq_kmeans_recovers_separated_blobs():
+    rng = np.random.default_rng(4)
+    centres = rng.uniform(-4, 4, (8, 12)) + 20 * np.eye(8, 12)
+    x16 = oracle.half(np.repeat(centres, 100, axis=0) + rng.normal(0, 0.01, (800, 12)))
+    u = (np.arange(8) * 100 + 50) / 800.0          # one seed inside each blob
+    c, a, obj, flags = oracle.vq_kmeans(x16, u, iters=2)
+    assert np.array_equal(a, np.repeat(np.arange(8), 100))
+    for b in range(8):
+        assert np.array_equal(c[b], np.float16(x16[b * 100:(b + 1) * 100].astype(np.float64).mean(0)))
+    assert not any(f.any() for f in flags)
+
+
+def test_vq_kmeans_objective_does_not_increase():
+    """Lloyd's steps never raise the sum of squared distances; rounding the
+    centroids to binary16 may add at most count * C * (half an ulp)^2 per entry."""
+    x16 = _vq_data(2000, 48, 5)
+    u = np.random.default_rng(6).random(64, dtype=np.float32)
+    c, a, obj, _ = oracle.vq_kmeans(x16, u, iters=8)
+    slack = 2000 * 48 * (2.0 ** -11 * 4) ** 2
+    assert np.all(np.diff(obj) <= slack), np.diff(obj)
+    assert obj[-1] < 0.8 * obj[0]
+
+
+def test_vq_init_rows():
+    m = 1000
+    u = np.array([0.0, 0.5, np.nextafter(np.float32(1), np.float32(0))], np.float32)
+    assert list(oracle.vq_init_rows(u, m)) == [0, 500, 999]
+
+
+def test_vq_compress_round_trip():
+    scene, _, _, _ = syn.tiny_scene(seed=8, n=500, sh_degree=3)
+    rng = np.random.default_rng(9)
+    contrib = rng.exponential(0.1, 500).astype(np.float32)
+    quant = oracle.vq_quantized(contrib, 0.4)
+    assert quant.sum() == math.ceil(0.4 * 500)
+    assert np.all(contrib[quant].max() < contrib[~quant].min())
+    x16 = oracle.vq_vectors(scene["sh"], quant)
+    c, a, _, _ = oracle.vq_kmeans(x16, rng.random(32, dtype=np.float32), iters=3)
+    comp = oracle.vq_compress(scene, quant, c, a)
+    back = oracle.vq_decompress(comp)
+    sh = np.asarray(scene["sh"]).reshape(500, -1)
+    got = back["sh"].reshape(500, -1)
+    assert np.array_equal(got[~quant], np.float16(sh[~quant]).astype(np.float32))
+    assert np.array_equal(got[quant], c[a].astype(np.float32))
+    for k in ("quat", "scale", "opacity"):
+        v = np.asarray(scene[k], np.float32).reshape(back[k].shape)
+        assert np.all(np.abs(back[k] - v) <= np.abs(v) * 2.0 ** -11 + 2.0 ** -25), k
+    assert np.array_equal(back["mu"], np.asarray(scene["mu"], np.float32))
+    assert comp["sh_table"].shape[0] == 32 + (~quant).sum()
+
+
+def test_vq_paper_constants_fit_the_layout():
+    """Appendix C's codebook size fits the 32-bit row index with room for the
+    kept rows, and its ratio selects ceil(0.4 N) surfels when contributions
+    are distinct."""
+    paper = json.load(open(os.path.join(GOLDEN, "paper_constants.json")))
+    K, ratio = paper["vq_codebook_size"]["value"], paper["vq_ratio"]["value"]
+    assert K == 8192 and ratio == 0.4
+    c = np.random.default_rng(10).permutation(10_000).astype(np.float32)
+    assert oracle.vq_quantized(c, ratio).sum() == math.ceil(ratio * 10_000)
