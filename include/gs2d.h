@@ -390,6 +390,89 @@ gs_status gs_visibility_count(int64_t n, const float* points, float sigma, const
 gs_status gs_visibility_bounds(int64_t n, const float* points, const uint32_t* counts, uint32_t min_count,
                                uint8_t* keep, float* zrange, void* stream);
 
+/* ---- Vector quantisation of SH and compressed scenes (Sec. 3.3) ------------
+ *
+ * After the blocks are merged, the surfels of least contribution (Eq. 4,
+ * gs_contribution over the training views) have their SH vector replaced by
+ * the nearest entry of a K-means codebook; every other attribute is stored in
+ * IEEE binary16 (Appendix C: codebook size 8192, quantisation ratio 0.4).
+ * keep (device uint8 [n]) names the surfels that keep their own SH (non-zero);
+ * the others are quantised: gs_prune_by_contribution's keep at the
+ * quantisation ratio selects exactly the paper's set.
+ * A vector is the surfel's whole SH row, C = 3 (deg+1)^2 values, rounded to
+ * binary16; codebook entries are binary16 too.
+ *
+ * gs_vq_kmeans: Lloyd's K-means over the m surfels with keep[i] == 0
+ * (surfel-index order).
+ *   sh:        device FP32 [n][(deg+1)^2][3].
+ *   K >= 1 entries; iters >= 0 update steps; entry j starts as the vector at
+ *              position floor(u_j m) (u_j = init_u[j], device FP32 [K], the
+ *              caller's uniform draws in [0, 1); FP64 product; clamped to
+ *              [0, m - 1]).
+ *   Each step assigns every vector to argmin_j ||x - c_j||^2 (the lowest j
+ *   among equal scores; scores are evaluated in FP32 from the binary16 values,
+ *   so two entries within about 1e-5 relative of each other may go either
+ *   way) and then sets each entry with vectors to
+ *   rn16((double(exact sum) * 2^-24) / count) (exact sums: order-independent
+ *   and reproducible); an entry without vectors keeps its value.  A final
+ *   assignment to the last codebook follows the iters steps.
+ *   codebook:  device binary16 [K][C] (output).
+ *   assign:    device int32 [n] (output): the entry of each quantised surfel,
+ *              -1 for the others.
+ *   objective: device FP64 [iters + 1] or NULL: sum over vectors of the
+ *              squared distance to their entry, after each assignment.
+ *   method:    0 chooses, 1 tensor cores (tcgen05; K a multiple of 256),
+ *              2 CUDA cores (FP32).
+ *   m_out:     host, optional: m.
+ * Synchronises the stream twice (to size the work, and to read the error
+ * flag at the end).  Errors: GS_ERR_ARG (bad sizes, method 1 with K not a
+ * multiple of 256, SH or centroid values outside binary16), GS_ERR_OOM,
+ * GS_ERR_CUDA (includes a kernel pipeline that timed out).
+ *
+ * gs_vq_assign: one assignment of the quantised vectors to a given codebook
+ * (device binary16 [K][C]); assign as above.  Synchronises once.
+ *
+ * gs_vq_pack: the compressed render layout.  quat16 [n][4], scale16 [n][2],
+ * opacity16 [n] = rn16 of quat, scale, opacity (device FP32, activated
+ * values); sh_row [n]: assign[i] for quantised surfels, K + (rank of i among
+ * the kept surfels) otherwise; sh_table: the K codebook rows, then the kept
+ * surfels' rn16 SH rows ([K + n][C] capacity, device).  *rows_out (host) =
+ * K + number kept.  Synchronises once.  GS_ERR_ARG if a value leaves the
+ * binary16 range or an assign entry is outside [0, K).
+ *
+ * gs_create_compressed_scene: a render-only scene over a compressed layout
+ * (borrowed arrays as in gs_create_scene): mu FP32 [n][3]; quat binary16
+ * [n][4] (8-byte aligned); scale binary16 [n][2] (4-byte aligned, activated);
+ * opacity binary16 [n]; sh_row uint32 [n]; sh_table binary16 [sh_rows][C].
+ * gs_render, gs_contribution and the server accept it and compute exactly as
+ * on the FP32 scene whose values are the binary16 ones; gs_backward and
+ * gs_densify_accumulate return GS_ERR_ARG.  Checks every sh_row against
+ * sh_rows (synchronises `stream` once); GS_ERR_ARG when one is out of range. */
+gs_status gs_vq_kmeans(int64_t n, int32_t sh_degree, const float* sh, const uint8_t* keep, int32_t K,
+                       int32_t iters, const float* init_u, uint16_t* codebook, int32_t* assign, double* objective,
+                       int32_t method, int64_t* m_out, void* stream);
+gs_status gs_vq_assign(int64_t n, int32_t sh_degree, const float* sh, const uint8_t* keep, int32_t K,
+                       const uint16_t* codebook, int32_t* assign, int32_t method, void* stream);
+gs_status gs_vq_pack(int64_t n, int32_t sh_degree, const float* quat, const float* scale, const float* opacity,
+                     const float* sh, const uint8_t* keep, const int32_t* assign, int32_t K,
+                     const uint16_t* codebook, uint16_t* quat16, uint16_t* scale16, uint16_t* opacity16,
+                     uint32_t* sh_row, uint16_t* sh_table, int64_t* rows_out, void* stream);
+
+typedef struct {
+  int64_t n;
+  int32_t sh_degree;
+  const float* mu;
+  const uint16_t* quat;
+  const uint16_t* scale;
+  const uint16_t* opacity;
+  const uint32_t* sh_row;
+  const uint16_t* sh_table;
+  int64_t sh_rows;
+  gs_settings settings;
+  gs_allocator allocator;
+} gs_compressed_scene_desc;
+gs_status gs_create_compressed_scene(gs_scene** out, const gs_compressed_scene_desc* desc, void* stream);
+
 /* ---- Serving: continuous batching of forward renders ------------------
  * (the serving loop built on the rasterizer; the paper has no serving
  * component of its own.)

@@ -474,18 +474,32 @@ def vq_init_rows(u, m):
     return np.minimum(np.floor(u * m), m - 1).astype(np.int64)
 
 
-def vq_assign(x16, c16, flag_rel=2.0 ** -17, block=2048):
+def vq_score_error(x, c):
+    """Bound on the error of a single-precision evaluation of the score
+    ||c||^2 - 2 x . c from binary16 operands (rows of x against rows of c):
+    the C + 2 exact products summed with one rounding each (relative 2^-24,
+    doubled here for margin) plus the two-part binary16 norm (2^-21 of it)."""
+    C = x.shape[-1]
+    n2 = (c * c).sum(-1)
+    mag = n2 + 2.0 * (np.abs(x) * np.abs(c)).sum(-1)
+    return (C + 2) * 2.0 ** -23 * mag + 2.0 ** -21 * n2
+
+
+def vq_assign(x16, c16, block=2048):
     """Nearest codebook entry of every vector: argmin_j ||x - c_j||^2 (the
     lowest j among equal distances), in FP64 on the binary16 values; scores
     are ||c_j||^2 - 2 x . c_j, which orders j the same way.  flag[i] marks a
-    decision whose best and second-best scores lie within
-    2 flag_rel (max_j ||c_j||^2 + 2 sum_k |x_k| max_j |c_jk|): a single-precision
-    evaluation of the scores may pick either there.  Returns (assign, flag,
-    distance of each vector to its entry)."""
+    decision whose best and second-best scores differ by no more than the sum
+    of their single-precision error bounds (vq_score_error): an FP32
+    evaluation of the scores may pick either there.  The second best is taken
+    among the entries whose values differ from the best's: identical entries
+    get identical scores in any precision, and the lowest index wins.
+    Returns (assign, flag, distance of each vector to its entry)."""
     x = np.asarray(x16, np.float64)
     c = np.asarray(c16, np.float64)
     norms = (c * c).sum(1)
-    cmax = np.abs(c).max(0) if c.size else np.zeros(x.shape[1])
+    _, uid = np.unique(np.asarray(c16, np.float16).view(np.uint16), axis=0, return_inverse=True)
+    uid = uid.reshape(-1)
     m = x.shape[0]
     assign = np.zeros(m, np.int64)
     flag = np.zeros(m, bool)
@@ -494,13 +508,15 @@ def vq_assign(x16, c16, flag_rel=2.0 ** -17, block=2048):
         xs = x[s:s + block]
         score = norms[None, :] - 2.0 * (xs @ c.T)
         a = score.argmin(1)
+        rows = np.arange(len(a))
         assign[s:s + block] = a
-        best = score[np.arange(len(a)), a]
+        best = score[rows, a]
         if c.shape[0] > 1:
-            two = np.partition(score, 1, axis=1)[:, :2]
-            gap = two[:, 1] - two[:, 0]
-            eps = 2.0 * flag_rel * (norms.max() + 2.0 * np.abs(xs) @ cmax)
-            flag[s:s + block] = gap <= eps
+            sc2 = np.where(uid[None, :] == uid[a][:, None], np.inf, score)
+            b = sc2.argmin(1)
+            gap = sc2[rows, b] - best
+            eps = vq_score_error(xs, c[a]) + vq_score_error(xs, c[b])
+            flag[s:s + block] = np.isfinite(gap) & (gap <= eps)
         dist[s:s + block] = np.maximum(best + (xs * xs).sum(1), 0.0)
     return assign, flag, dist
 

@@ -66,6 +66,13 @@ class gs_scene_desc(ctypes.Structure):
                 ("settings", gs_settings), ("allocator", gs_allocator)]
 
 
+class gs_compressed_scene_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("mu", ctypes.c_void_p),
+                ("quat", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("opacity", ctypes.c_void_p),
+                ("sh_row", ctypes.c_void_p), ("sh_table", ctypes.c_void_p), ("sh_rows", ctypes.c_int64),
+                ("settings", gs_settings), ("allocator", gs_allocator)]
+
+
 class gs_frame_info(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_int64), ("n_visible", ctypes.c_int64),
                 ("pairs_evaluated", ctypes.c_int64), ("pairs_blended", ctypes.c_int64),
@@ -121,6 +128,12 @@ _SIGS = {
     "gs_visibility_count": [ctypes.c_int64, _V, ctypes.c_float, _V, ctypes.c_int32, ctypes.c_float,
                             ctypes.c_float, _V, _V],
     "gs_visibility_bounds": [ctypes.c_int64, _V, _V, ctypes.c_uint32, _V, _V, _V],
+    "gs_vq_kmeans": [ctypes.c_int64, ctypes.c_int32, _V, _V, ctypes.c_int32, ctypes.c_int32, _V, _V, _V, _V,
+                     ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _V],
+    "gs_vq_assign": [ctypes.c_int64, ctypes.c_int32, _V, _V, ctypes.c_int32, _V, _V, ctypes.c_int32, _V],
+    "gs_vq_pack": [ctypes.c_int64, ctypes.c_int32, _V, _V, _V, _V, _V, _V, ctypes.c_int32, _V, _V, _V, _V, _V, _V,
+                   ctypes.POINTER(ctypes.c_int64), _V],
+    "gs_create_compressed_scene": [ctypes.POINTER(_V), ctypes.POINTER(gs_compressed_scene_desc), _V],
     "gs_geometry_loss": [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(gs_camera), _V, ctypes.c_float,
                          ctypes.c_float, _V, _V, _V],
     "gs_adam_step": [ctypes.c_int64, _V, _V, _V, _V, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -329,6 +342,106 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+class CompressedScene(Scene):
+    """A render-only scene over the compressed layout of `vq_pack` (see
+    gs_create_compressed_scene): render, contribution and serving work as on
+    the FP32 scene of the same (binary16) values; backward raises GsError."""
+
+    def __init__(self, comp: dict, settings: gs_settings = None, stream=None):
+        self.settings = settings if settings is not None else default_settings()
+        self.sh_degree = int(comp["sh_degree"])
+        self._handle = ctypes.c_void_p()
+        n = comp["mu"].shape[0]
+        C = 3 * (self.sh_degree + 1) ** 2
+        d = gs_compressed_scene_desc()
+        d.n, d.sh_degree, d.settings = n, self.sh_degree, self.settings
+        d.mu = _ptr(comp["mu"], shape=(n, 3), name="mu")
+        d.quat = _ptr(comp["quat"], torch.float16, (n, 4), "quat")
+        d.scale = _ptr(comp["scale"], torch.float16, (n, 2), "scale")
+        d.opacity = _ptr(comp["opacity"], torch.float16, (n,), "opacity")
+        d.sh_row = _ptr(comp["sh_row"], torch.int32, (n,), "sh_row")
+        rows = comp["sh_table"].shape[0]
+        d.sh_table = _ptr(comp["sh_table"], torch.float16, (rows, C), "sh_table")
+        d.sh_rows = rows
+        _check(_lib.gs_create_compressed_scene(ctypes.byref(self._handle), ctypes.byref(d), _stream(stream)))
+        self.n = n
+        self.comp = comp
+        self.params = (comp["mu"],)
+
+    def set_params(self, *a, **k):
+        raise GsError(-1, "a compressed scene is fixed")
+
+
+def vq_kmeans(sh, sh_degree, keep, K=8192, iters=10, init_u=None, method=0, objective=True, stream=None):
+    """Lloyd's K-means of the SH vectors of the surfels with keep == 0
+    (gs_vq_kmeans).  init_u: uniform draws [K] (drawn here when None).
+    Returns (codebook binary16 [K, C], assign int32 [n] (-1 where kept),
+    objective FP64 [iters + 1] or None, number of quantised vectors)."""
+    n = sh.shape[0]
+    C = 3 * (int(sh_degree) + 1) ** 2
+    dev = sh.device
+    if init_u is None:
+        init_u = torch.rand(K, device=dev)
+    cb = torch.empty((K, C), dtype=torch.float16, device=dev)
+    assign = torch.empty(n, dtype=torch.int32, device=dev)
+    obj = torch.empty(iters + 1, dtype=torch.float64, device=dev) if objective else None
+    m = ctypes.c_int64()
+    _check(_lib.gs_vq_kmeans(n, int(sh_degree), _ptr(sh, shape=(n, C // 3, 3), name="sh"),
+                             _ptr(keep, torch.uint8, (n,), "keep"), int(K), int(iters),
+                             _ptr(init_u, shape=(K,), name="init_u"), _ptr(cb, torch.float16), _ptr(assign, torch.int32),
+                             _ptr(obj, torch.float64), int(method), ctypes.byref(m), _stream(stream)))
+    return cb, assign, obj, m.value
+
+
+def vq_assign(sh, sh_degree, keep, codebook, method=0, stream=None):
+    """Nearest codebook entry of every quantised surfel's SH (gs_vq_assign);
+    -1 for kept surfels."""
+    n = sh.shape[0]
+    C = 3 * (int(sh_degree) + 1) ** 2
+    K = codebook.shape[0]
+    assign = torch.empty(n, dtype=torch.int32, device=sh.device)
+    _check(_lib.gs_vq_assign(n, int(sh_degree), _ptr(sh, shape=(n, C // 3, 3), name="sh"),
+                             _ptr(keep, torch.uint8, (n,), "keep"), K, _ptr(codebook, torch.float16, (K, C), "codebook"),
+                             _ptr(assign, torch.int32), int(method), _stream(stream)))
+    return assign
+
+
+def vq_pack(params, sh_degree, keep, assign, codebook, stream=None):
+    """The compressed render layout (gs_vq_pack) of params = (mu, quat,
+    scale, opacity, sh): a dict for CompressedScene."""
+    mu, quat, scale, opacity, sh = params
+    n = mu.shape[0]
+    C = 3 * (int(sh_degree) + 1) ** 2
+    K = codebook.shape[0]
+    dev = mu.device
+    q16 = torch.empty((n, 4), dtype=torch.float16, device=dev)
+    s16 = torch.empty((n, 2), dtype=torch.float16, device=dev)
+    o16 = torch.empty(n, dtype=torch.float16, device=dev)
+    sh_row = torch.empty(n, dtype=torch.int32, device=dev)
+    table = torch.empty((K + n, C), dtype=torch.float16, device=dev)
+    rows = ctypes.c_int64()
+    _check(_lib.gs_vq_pack(n, int(sh_degree), _ptr(quat, shape=(n, 4), name="quat"),
+                           _ptr(scale, shape=(n, 2), name="scale"), _ptr(opacity, shape=(n,), name="opacity"),
+                           _ptr(sh, shape=(n, C // 3, 3), name="sh"), _ptr(keep, torch.uint8, (n,), "keep"),
+                           _ptr(assign, torch.int32, (n,), "assign"), K,
+                           _ptr(codebook, torch.float16, (K, C), "codebook"), _ptr(q16, torch.float16),
+                           _ptr(s16, torch.float16), _ptr(o16, torch.float16), _ptr(sh_row, torch.int32),
+                           _ptr(table, torch.float16), ctypes.byref(rows), _stream(stream)))
+    return {"mu": mu, "quat": q16, "scale": s16, "opacity": o16, "sh_row": sh_row,
+            "sh_table": table[:rows.value], "sh_degree": int(sh_degree)}
+
+
+def compress(params, sh_degree, contrib, ratio=0.4, K=8192, iters=10, init_u=None, method=0, stream=None):
+    """Contribution-based vector quantisation of a scene (Sec. 3.3, Appendix
+    C): the surfels at or below the ratio's contribution percentile get a
+    codebook entry for their SH; everything else is stored in binary16.
+    Returns (compressed dict, info: keep, bound, assign, codebook, objective)."""
+    keep, bound = prune_by_contribution(contrib, ratio, stream=stream)
+    cb, assign, obj, m = vq_kmeans(params[4], sh_degree, keep, K, iters, init_u, method, True, stream)
+    comp = vq_pack(params, sh_degree, keep, assign, cb, stream)
+    return comp, {"keep": keep, "bound": bound, "assign": assign, "codebook": cb, "objective": obj, "m": m}
 
 
 class Server:

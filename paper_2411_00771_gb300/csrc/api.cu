@@ -422,6 +422,7 @@ gs_status gs_default_settings(gs_settings* s) {
 gs_status gs_set_params(gs_scene* sc, int64_t n, const float* mu, const float* quat,
                         const float* scale, const float* opacity, const float* sh) {
   if (!sc) return fail(GS_ERR_ARG, "gs_set_params: null scene");
+  if (sc->P.sh_table) return fail(GS_ERR_ARG, "gs_set_params: the scene is compressed");
   if (n < 0 || n >= (int64_t(1) << 31)) return fail(GS_ERR_ARG, "gs_set_params: n out of range");
   if (n > 0 && (!mu || !quat || !scale || !opacity || !sh))
     return fail(GS_ERR_ARG, "gs_set_params: null parameter array");
@@ -609,6 +610,7 @@ gs_status gs_backward(gs_scene* sc, gs_frame* f, const float* const* adj_sets,
                       const uint32_t* plane_masks, int32_t n_sets, const gs_param_grads* grads,
                       float* screen_grads, void* stream) {
   if (!sc || !f || !adj_sets || !plane_masks || !grads) return fail(GS_ERR_ARG, "gs_backward: null argument");
+  if (sc->P.sh_table) return fail(GS_ERR_ARG, "gs_backward: compressed scenes are render-only");
   if (f->scene != sc) return fail(GS_ERR_STATE, "gs_backward: frame belongs to another scene");
   if (sc->P.n != f->n) return fail(GS_ERR_STATE, "gs_backward: surfel count changed since the render");
   if (n_sets < 1 || n_sets > 3) return fail(GS_ERR_ARG, "gs_backward: n_sets must be 1..3");
@@ -639,6 +641,7 @@ gs_status gs_backward(gs_scene* sc, gs_frame* f, const float* const* adj_sets,
 gs_status gs_densify_accumulate(gs_scene* sc, gs_frame* f, const float* screen, int32_t n_sets,
                                 float* stats, void* stream) {
   if (!sc || !f || !screen || !stats) return fail(GS_ERR_ARG, "gs_densify_accumulate: null argument");
+  if (sc->P.sh_table) return fail(GS_ERR_ARG, "gs_densify_accumulate: compressed scenes are render-only");
   if (f->n != sc->P.n) return fail(GS_ERR_STATE, "gs_densify_accumulate: surfel count changed");
   if (n_sets < 1) return fail(GS_ERR_ARG, "gs_densify_accumulate: n_sets must be >= 1");
   cudaError_t e = launch_densify_accumulate(f->rect, screen, f->n, n_sets, stats, (cudaStream_t)stream);
@@ -830,3 +833,225 @@ gs_status gs_sync(void* stream, int32_t timeout_ms) {
 }
 
 }  // extern "C"
+
+// ---- Vector quantisation of SH and compressed scenes ------------------------------
+
+namespace {
+
+int device_sms() {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+// Lists the quantised vectors and packs their operands: fills b (owned by
+// buf), m, C, D.  Synchronises once (m).
+gs_status vq_prepare(const char* who, int64_t n, int32_t deg, const float* sh, const uint8_t* keep, int32_t K,
+                     int32_t method, bool kmeans, cudaStream_t st, Buffers& buf, VqBufs& b, int& m, int& C, int& D,
+                     bool& tensor) {
+  const std::string w(who);
+  if (n < 0 || n >= (int64_t(1) << 31) || (n > 0 && (!sh || !keep)))
+    return fail(GS_ERR_ARG, w + ": bad n or null array");
+  if (deg < 0 || deg > 3) return fail(GS_ERR_ARG, w + ": sh_degree must be 0..3");
+  if (K < 1 || K > (1 << 24)) return fail(GS_ERR_ARG, w + ": K must be in [1, 2^24]");
+  if (method < 0 || method > 2) return fail(GS_ERR_ARG, w + ": method must be 0, 1 or 2");
+  if (method == 1 && K % 256 != 0) return fail(GS_ERR_ARG, w + ": the tensor-core path needs K % 256 == 0");
+  tensor = method == 1 || (method == 0 && K % 256 == 0);
+  D = vq_width(deg, &C);
+  b.err = buf.get<int>(1, st);
+  uint32_t* total = buf.get<uint32_t>(1, st);
+  if (!b.err || !total) return fail(GS_ERR_OOM, w + ": scratch allocation failed");
+  GS_CK(cudaMemsetAsync(b.err, 0, sizeof(int), st));
+  uint32_t hm = 0;
+  if (n > 0) {
+    uint32_t* flags = buf.get<uint32_t>((size_t)n, st);
+    uint32_t* offs = buf.get<uint32_t>((size_t)n, st);
+    uint32_t* stmp = buf.get<uint32_t>(scan_tmp_words(n), st);
+    b.rows = buf.get<uint32_t>((size_t)n, st);
+    if (!flags || !offs || !stmp || !b.rows) return fail(GS_ERR_OOM, w + ": scratch allocation failed");
+    GS_CK(launch_vq_list(keep, (int)n, 0, flags, offs, total, stmp, b.rows, st));
+    GS_CK(cudaMemcpyAsync(&hm, total, sizeof hm, cudaMemcpyDeviceToHost, st));
+    GS_CK(cudaStreamSynchronize(st));
+    buf.release(flags, st);
+    buf.release(offs, st);
+    buf.release(stmp, st);
+  }
+  m = (int)hm;
+  const size_t m_pad = ((size_t)m + 127) / 128 * 128;
+  b.xr = buf.get<uint16_t>((size_t)m * C + 1, st);
+  b.xt = buf.get<uint16_t>(m_pad * D + 1, st);
+  b.ct = tensor ? buf.get<uint16_t>((size_t)K * D, st) : nullptr;
+  b.hl = buf.get<float2>((size_t)K, st);
+  b.best64 = buf.get<unsigned long long>(m_pad + 1, st);
+  b.best_idx = buf.get<int32_t>((size_t)m + 1, st);
+  if (kmeans) {
+    b.sums = buf.get<unsigned long long>((size_t)K * C, st);
+    b.cnt = buf.get<unsigned int>((size_t)K, st);
+  }
+  if (!b.xr || !b.xt || (tensor && !b.ct) || !b.hl || !b.best64 || !b.best_idx || (kmeans && (!b.sums || !b.cnt)))
+    return fail(GS_ERR_OOM, w + ": scratch allocation failed");
+  GS_CK(launch_vq_pack_x(sh, b, m, C, D, st));
+  return GS_OK;
+}
+
+gs_status vq_check(const char* who, const int* err_dev, cudaStream_t st) {
+  int err = 0;
+  GS_CK(cudaMemcpyAsync(&err, err_dev, sizeof err, cudaMemcpyDeviceToHost, st));
+  GS_CK(cudaStreamSynchronize(st));
+  if (err == 1) return fail(GS_ERR_CUDA, std::string(who) + ": the assignment pipeline timed out");
+  if (err == 2) return fail(GS_ERR_ARG, std::string(who) + ": a value is outside the binary16 range");
+  if (err == 3) return fail(GS_ERR_ARG, std::string(who) + ": an entry index is outside [0, K)");
+  return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_vq_kmeans(int64_t n, int32_t sh_degree, const float* sh, const uint8_t* keep, int32_t K, int32_t iters,
+                       const float* init_u, uint16_t* codebook, int32_t* assign, double* objective, int32_t method,
+                       int64_t* m_out, void* stream) {
+  if (iters < 0 || !init_u || !codebook || (n > 0 && !assign)) return fail(GS_ERR_ARG, "gs_vq_kmeans: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  Buffers buf;
+  buf.al = &al;
+  VqBufs b;
+  int m = 0, C = 0, D = 0;
+  bool tensor = false;
+  gs_status s = vq_prepare("gs_vq_kmeans", n, sh_degree, sh, keep, K, method, true, st, buf, b, m, C, D, tensor);
+  if (s != GS_OK) {
+    buf.release_all(st);
+    return s;
+  }
+  const int sms = device_sms();
+  cudaError_t e = launch_vq_init(b, m, C, init_u, K, codebook, st);
+  if (e == cudaSuccess && objective) e = cudaMemsetAsync(objective, 0, sizeof(double) * (size_t)(iters + 1), st);
+  for (int t = 0; t < iters && e == cudaSuccess; ++t) {
+    e = launch_vq_assign(b, m, C, D, codebook, K, tensor, sms, st);
+    if (e == cudaSuccess) e = launch_vq_accum(b, m, C, codebook, K, true, objective ? objective + t : nullptr, st);
+    if (e == cudaSuccess) e = launch_vq_update(b, C, codebook, K, st);
+  }
+  if (e == cudaSuccess) e = launch_vq_assign(b, m, C, D, codebook, K, tensor, sms, st);
+  if (e == cudaSuccess) e = launch_vq_accum(b, m, C, codebook, K, false, objective ? objective + iters : nullptr, st);
+  if (e == cudaSuccess && n > 0) e = cudaMemsetAsync(assign, 0xFF, sizeof(int32_t) * (size_t)n, st);
+  if (e == cudaSuccess) e = launch_vq_scatter(b, m, assign, st);
+  s = e == cudaSuccess ? vq_check("gs_vq_kmeans", b.err, st) : cuda_fail(e, "gs_vq_kmeans");
+  buf.release_all(st);
+  if (s == GS_OK && m_out) *m_out = m;
+  return s;
+}
+
+gs_status gs_vq_assign(int64_t n, int32_t sh_degree, const float* sh, const uint8_t* keep, int32_t K,
+                       const uint16_t* codebook, int32_t* assign, int32_t method, void* stream) {
+  if (!codebook || (n > 0 && !assign)) return fail(GS_ERR_ARG, "gs_vq_assign: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  Buffers buf;
+  buf.al = &al;
+  VqBufs b;
+  int m = 0, C = 0, D = 0;
+  bool tensor = false;
+  gs_status s = vq_prepare("gs_vq_assign", n, sh_degree, sh, keep, K, method, false, st, buf, b, m, C, D, tensor);
+  if (s != GS_OK) {
+    buf.release_all(st);
+    return s;
+  }
+  cudaError_t e = launch_vq_assign(b, m, C, D, codebook, K, tensor, device_sms(), st);
+  if (e == cudaSuccess) e = launch_vq_accum(b, m, C, codebook, K, false, nullptr, st);
+  if (e == cudaSuccess && n > 0) e = cudaMemsetAsync(assign, 0xFF, sizeof(int32_t) * (size_t)n, st);
+  if (e == cudaSuccess) e = launch_vq_scatter(b, m, assign, st);
+  s = e == cudaSuccess ? vq_check("gs_vq_assign", b.err, st) : cuda_fail(e, "gs_vq_assign");
+  buf.release_all(st);
+  return s;
+}
+
+gs_status gs_vq_pack(int64_t n, int32_t sh_degree, const float* quat, const float* scale, const float* opacity,
+                     const float* sh, const uint8_t* keep, const int32_t* assign, int32_t K, const uint16_t* codebook,
+                     uint16_t* quat16, uint16_t* scale16, uint16_t* opacity16, uint32_t* sh_row, uint16_t* sh_table,
+                     int64_t* rows_out, void* stream) {
+  if (n < 0 || n >= (int64_t(1) << 31) || sh_degree < 0 || sh_degree > 3 || K < 0 || !rows_out ||
+      (K > 0 && (!codebook || !sh_table)) ||
+      (n > 0 && (!quat || !scale || !opacity || !sh || !keep || !assign || !quat16 || !scale16 || !opacity16 ||
+                 !sh_row || !sh_table)))
+    return fail(GS_ERR_ARG, "gs_vq_pack: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  Buffers buf;
+  buf.al = &al;
+  int C = 0;
+  vq_width(sh_degree, &C);
+  int* err = buf.get<int>(1, st);
+  uint32_t* total = buf.get<uint32_t>(1, st);
+  uint32_t* flags = buf.get<uint32_t>((size_t)n + 1, st);
+  uint32_t* offs = buf.get<uint32_t>((size_t)n + 1, st);
+  uint32_t* stmp = buf.get<uint32_t>(scan_tmp_words(n), st);
+  gs_status s = GS_OK;
+  if (!err || !total || !flags || !offs || !stmp) {
+    s = fail(GS_ERR_OOM, "gs_vq_pack: scratch allocation failed");
+  } else {
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_vq_list(keep, (int)n, 1, flags, offs, total, stmp, nullptr, st);
+    if (e == cudaSuccess)
+      e = launch_vq_pack_scene((int)n, C, K, quat, scale, opacity, sh, keep, assign, offs, codebook, quat16, scale16,
+                               opacity16, sh_row, sh_table, err, st);
+    uint32_t kept = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&kept, total, sizeof kept, cudaMemcpyDeviceToHost, st);
+    s = e == cudaSuccess ? vq_check("gs_vq_pack", err, st) : cuda_fail(e, "gs_vq_pack");
+    if (s == GS_OK) *rows_out = (int64_t)K + kept;
+  }
+  buf.release_all(st);
+  return s;
+}
+
+gs_status gs_create_compressed_scene(gs_scene** out, const gs_compressed_scene_desc* d, void* stream) {
+  if (!out || !d) return fail(GS_ERR_ARG, "gs_create_compressed_scene: null argument");
+  *out = nullptr;
+  if (d->sh_degree < 0 || d->sh_degree > 3)
+    return fail(GS_ERR_ARG, "gs_create_compressed_scene: sh_degree must be 0..3");
+  const gs_settings& se = d->settings;
+  if (!(se.rho_max > 0.f) || !(se.screen_inv_sigma2 > 0.f) || !(se.alpha_max > 0.f) || !(se.alpha_max < 1.f) ||
+      !(se.T_min > 0.f) || !(se.near_plane > 0.f))
+    return fail(GS_ERR_ARG, "gs_create_compressed_scene: invalid settings");
+  if (d->n < 0 || d->n >= (int64_t(1) << 31)) return fail(GS_ERR_ARG, "gs_create_compressed_scene: n out of range");
+  if (d->n > 0 && (!d->mu || !d->quat || !d->scale || !d->opacity || !d->sh_row || !d->sh_table))
+    return fail(GS_ERR_ARG, "gs_create_compressed_scene: null parameter array");
+  if (d->n > 0 && (d->sh_rows < 1 || d->sh_rows > (int64_t)0xFFFFFFFFu))
+    return fail(GS_ERR_ARG, "gs_create_compressed_scene: sh_rows out of range");
+  if (((uintptr_t)d->quat % 8) || ((uintptr_t)d->scale % 4) || ((uintptr_t)d->opacity % 2) ||
+      ((uintptr_t)d->sh_table % 2) || ((uintptr_t)d->sh_row % 4) || ((uintptr_t)d->mu % 4))
+    return fail(GS_ERR_ARG, "gs_create_compressed_scene: misaligned array");
+  cudaStream_t st = (cudaStream_t)stream;
+  set_pool_threshold();
+  Alloc al;
+  al.a = d->allocator;
+  if (d->n > 0) {
+    int* err = static_cast<int*>(al.get(sizeof(int), st));
+    if (!err) return fail(GS_ERR_OOM, "gs_create_compressed_scene: scratch allocation failed");
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_vq_check_rows(d->sh_row, (int)d->n, (uint32_t)d->sh_rows, err, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    al.put(err, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "gs_create_compressed_scene");
+    if (h) return fail(GS_ERR_ARG, "gs_create_compressed_scene: an sh_row is outside [0, sh_rows)");
+  }
+  gs_scene* sc = new (std::nothrow) gs_scene();
+  if (!sc) return fail(GS_ERR_OOM, "gs_create_compressed_scene: host allocation");
+  sc->settings = se;
+  sc->al = al;
+  sc->P.n = (int)d->n;
+  sc->P.sh_degree = d->sh_degree;
+  sc->P.mu = d->mu;
+  sc->P.quat = sc->P.scale = sc->P.opacity = sc->P.sh = nullptr;
+  sc->P.quat16 = d->quat;
+  sc->P.scale16 = d->scale;
+  sc->P.opacity16 = d->opacity;
+  sc->P.sh_row = d->sh_row;
+  sc->P.sh_table = d->sh_table;
+  *out = sc;
+  return GS_OK;
+}

@@ -1,6 +1,7 @@
 // Internal declarations of the CUDA library (sm_103a).  Not part of the C ABI.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -150,7 +151,37 @@ struct ParamsDev {
   const float* sh;
   int n;
   int sh_degree;
+  // Compressed store (render only; null for FP32 scenes): quat, scale and
+  // opacity as IEEE binary16, and the SH of surfel n in row sh_row[n] of
+  // sh_table (binary16, rows of 3 (deg+1)^2 values: the codebook of the
+  // vector quantisation, then the kept surfels' own SH).
+  const uint16_t* quat16 = nullptr;
+  const uint16_t* scale16 = nullptr;
+  const uint16_t* opacity16 = nullptr;
+  const uint32_t* sh_row = nullptr;
+  const uint16_t* sh_table = nullptr;
 };
+
+// Parameter loads for either store (a kernel-uniform branch).
+__device__ __forceinline__ float h2f(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+__device__ __forceinline__ float4 load_quat(const ParamsDev& P, int n) {
+  if (P.quat16) {
+    const uint2 v = *reinterpret_cast<const uint2*>(P.quat16 + 4 * (size_t)n);
+    return make_float4(h2f((uint16_t)(v.x & 0xFFFFu)), h2f((uint16_t)(v.x >> 16)), h2f((uint16_t)(v.y & 0xFFFFu)),
+                       h2f((uint16_t)(v.y >> 16)));
+  }
+  return make_float4(P.quat[4 * n], P.quat[4 * n + 1], P.quat[4 * n + 2], P.quat[4 * n + 3]);
+}
+__device__ __forceinline__ float2 load_scale(const ParamsDev& P, int n) {
+  if (P.scale16) {
+    const uint32_t v = *reinterpret_cast<const uint32_t*>(P.scale16 + 2 * (size_t)n);
+    return make_float2(h2f((uint16_t)(v & 0xFFFFu)), h2f((uint16_t)(v >> 16)));
+  }
+  return make_float2(P.scale[2 * n], P.scale[2 * n + 1]);
+}
+__device__ __forceinline__ float load_opacity(const ParamsDev& P, int n) {
+  return P.opacity16 ? h2f(P.opacity16[n]) : P.opacity[n];
+}
 
 // ---- launch wrappers (each returns cudaError_t from the launch) ----------
 // Writes, for the ncand candidates (device count) in surfel-index order,
@@ -371,5 +402,41 @@ struct ProfScope {
   ProfScope(int i, cudaStream_t s) : id(i), st(s) { prof_begin(id, st); }
   ~ProfScope() { prof_end(id, st); }
 };
+
+
+// ---- Vector quantisation of SH (vq.cu) --------------------------------------
+// Scratch of one K-means / assignment call (m quantised vectors of C
+// coefficients, width D = C + 2 rounded up to 16, K entries).
+struct VqBufs {
+  uint32_t* rows = nullptr;              // [m] quantised surfels in index order
+  uint16_t* xr = nullptr;                // [m][C] binary16 vectors, row-major
+  uint16_t* xt = nullptr;                // [m_pad][D] augmented vectors, core-matrix layout
+  uint16_t* ct = nullptr;                // [K][D] augmented codebook, core-matrix layout
+  float2* hl = nullptr;                  // [K] ||c||^2 as two binary16 values
+  unsigned long long* best64 = nullptr;  // [m_pad] (score key, entry)
+  int32_t* best_idx = nullptr;           // [m]
+  unsigned long long* sums = nullptr;    // [K][C] exact sums (units of 2^-24)
+  unsigned int* cnt = nullptr;           // [K]
+  int* err = nullptr;                    // [1] 0 ok, 1 pipeline timeout, 2 value outside binary16
+};
+// D for an SH degree; *C = 3 (deg + 1)^2.
+int vq_width(int sh_degree, int* C);
+// Lists the surfels with (keep[i] != 0) == want (rows may be null: offsets and total only).
+cudaError_t launch_vq_list(const uint8_t* keep, int n, int want, uint32_t* flags, uint32_t* offs, uint32_t* total,
+                           uint32_t* scan_tmp, uint32_t* rows, cudaStream_t st);
+cudaError_t launch_vq_pack_x(const float* sh, const VqBufs& b, int m, int C, int D, cudaStream_t st);
+cudaError_t launch_vq_init(const VqBufs& b, int m, int C, const float* u, int K, uint16_t* cb, cudaStream_t st);
+// tensor: tcgen05 kernel (K a multiple of 256), else the CUDA-core kernel.
+cudaError_t launch_vq_assign(const VqBufs& b, int m, int C, int D, const uint16_t* cb, int K, bool tensor, int num_sms,
+                             cudaStream_t st);
+cudaError_t launch_vq_accum(const VqBufs& b, int m, int C, const uint16_t* cb, int K, bool with_sums,
+                            double* objective, cudaStream_t st);
+cudaError_t launch_vq_update(const VqBufs& b, int C, uint16_t* cb, int K, cudaStream_t st);
+cudaError_t launch_vq_scatter(const VqBufs& b, int m, int32_t* assign, cudaStream_t st);
+cudaError_t launch_vq_pack_scene(int n, int C, int K, const float* quat, const float* scale, const float* opacity,
+                                 const float* sh, const uint8_t* keep, const int32_t* assign,
+                                 const uint32_t* kept_offs, const uint16_t* codebook, uint16_t* q16, uint16_t* s16,
+                                 uint16_t* o16, uint32_t* sh_row, uint16_t* table, int* err, cudaStream_t st);
+cudaError_t launch_vq_check_rows(const uint32_t* sh_row, int n, uint32_t rows, int* err, cudaStream_t st);
 
 }  // namespace gs2d

@@ -129,12 +129,14 @@ __global__ void __launch_bounds__(256) preprocess_cull_kernel(ParamsDev P, CamDe
   if (n < P.n) {
     tcount[n] = 0u;
     rect[n] = make_uint2(0u, 0u);
-    const float qw = P.quat[4 * n], qx = P.quat[4 * n + 1], qy = P.quat[4 * n + 2], qz = P.quat[4 * n + 3];
+    const float4 q4 = load_quat(P, n);
+    const float qw = q4.x, qx = q4.y, qy = q4.z, qz = q4.w;
     const df qn2 = two_prod(qw, qw) + two_prod(qx, qx) + two_prod(qy, qy) + two_prod(qz, qz);
     const V3<float> mu = {P.mu[3 * n], P.mu[3 * n + 1], P.mu[3 * n + 2]};
     V3<float> p = rot<float>(cam.Rf, mu);
     p.x += cam.tf[0]; p.y += cam.tf[1]; p.z += cam.tf[2];
-    const float R = 3.0f * fmaxf(P.scale[2 * n], P.scale[2 * n + 1]) * sqrtf(set.rho_max / 9.0f);
+    const float2 s2 = load_scale(P, n);
+    const float R = 3.0f * fmaxf(s2.x, s2.y) * sqrtf(set.rho_max / 9.0f);
     // FP32 error of p is far below this margin (a few ulp of |mu| + |t|)
     const float eps = 1e-4f * (fabsf(mu.x) + fabsf(mu.y) + fabsf(mu.z) + cam.tabs + 1.0f) + 1e-3f * R;
     keep = df_pos(qn2) && p.z + R + eps > set.near_plane;
@@ -219,7 +221,8 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     const int n = (int)cand[ci];
     idx[ci] = (uint32_t)n;
     dkey[ci] = 0xFFFFFFFFu;  // not visible unless set below
-    const float qw0 = P.quat[4 * n], qx0 = P.quat[4 * n + 1], qy0 = P.quat[4 * n + 2], qz0 = P.quat[4 * n + 3];
+    const float4 q4 = load_quat(P, n);
+    const float qw0 = q4.x, qx0 = q4.y, qy0 = q4.z, qz0 = q4.w;
     const df qn2 = two_prod(qw0, qw0) + two_prod(qx0, qx0) + two_prod(qy0, qy0) + two_prod(qz0, qz0);
     if (!df_pos(qn2)) continue;
     const df iq = df_rsqrt(qn2);
@@ -235,7 +238,8 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     p.y = p.y + df_make(cam.tf[1], cam.tlo[1]);
     p.z = p.z + df_make(cam.tf[2], cam.tlo[2]);
     const D3 tu = cam_rot(cam, r1), tv = cam_rot(cam, r2), nv = cam_rot(cam, r3);
-    const float su = P.scale[2 * n], sv = P.scale[2 * n + 1];
+    const float2 s2 = load_scale(P, n);
+    const float su = s2.x, sv = s2.y;
     const D3 a = {tu.x * su, tu.y * su, tu.z * su}, b = {tv.x * sv, tv.y * sv, tv.z * sv};
     const df zmin = p.z - df_sqrt((a.z * a.z + b.z * b.z) * set.rho_max);
     if (!df_pos(zmin - set.near_plane)) continue;
@@ -320,13 +324,23 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     constexpr int K = (DEG + 1) * (DEG + 1);
     float Y[16];
     sh_basis(dx * il, dy * il, dz * il, DEG, Y);
-    const float* f = P.sh + (size_t)n * K * 3;
     float col[3] = {0.f, 0.f, 0.f};
+    if (P.sh_table) {
+      const uint16_t* f = P.sh_table + (size_t)P.sh_row[n] * K * 3;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      col[0] = fmaf(f[k * 3], Y[k], col[0]);
-      col[1] = fmaf(f[k * 3 + 1], Y[k], col[1]);
-      col[2] = fmaf(f[k * 3 + 2], Y[k], col[2]);
+      for (int k = 0; k < K; ++k) {
+        col[0] = fmaf(h2f(f[k * 3]), Y[k], col[0]);
+        col[1] = fmaf(h2f(f[k * 3 + 1]), Y[k], col[1]);
+        col[2] = fmaf(h2f(f[k * 3 + 2]), Y[k], col[2]);
+      }
+    } else {
+      const float* f = P.sh + (size_t)n * K * 3;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        col[0] = fmaf(f[k * 3], Y[k], col[0]);
+        col[1] = fmaf(f[k * 3 + 1], Y[k], col[1]);
+        col[2] = fmaf(f[k * 3 + 2], Y[k], col[2]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) col[c] = fmaxf(col[c] + 0.5f, 0.f);
@@ -334,7 +348,7 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     float4* Rr = rec + (size_t)n * kRecF4;
     Rr[0] = make_float4(cx.hi, cy.hi, cx.lo, cy.lo);
     Rr[1] = r1f;
-    Rr[2] = make_float4(ef.x, ef.y, pz, P.opacity[n]);
+    Rr[2] = make_float4(ef.x, ef.y, pz, load_opacity(P, n));
     Rr[3] = make_float4(col[0], col[1], col[2], sg * df_float(nv.x));
     Rr[4] = make_float4(sg * df_float(nv.y), sg * df_float(nv.z), 0.f, 0.f);
   }
