@@ -39,6 +39,18 @@ FLOP_BLEND = 26      # per blended pair (composite of 12 planes)
 FLOP_BWD_PAIR = 140  # per blended pair in the backward (adjoints + chain)
 SM_COUNT, FP32_LANES, SM_MAX_HZ = 152, 128, 2.07e9
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_HZ / 1e12
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def measured_peak(key):
+    """A peak from the measured-peaks file at the repository root, else the
+    earlier single GB300 measurement."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_PEAKS[key]
 
 # DRAM bytes (read + write) of one blend_bwd launch on this workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the
@@ -68,6 +80,7 @@ def parse():
     ap.add_argument("--width", type=int, default=1600, help="view width (smaller views for ncu captures)")
     ap.add_argument("--height", type=int, default=900)
     ap.add_argument("--no-training", action="store_true", help="skip the 4M-surfel training-step measurement")
+    ap.add_argument("--no-vq", action="store_true", help="skip the vector-quantisation measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serving-seconds", type=float, default=8.0)
     return ap.parse_args()
@@ -280,7 +293,7 @@ def run_ours(args):
 
     contribution = measure_contribution(sc, cam, n, dev, args)
     visibility = measure_visibility(scene_np, dev, args)
-    training = None if args.no_training else measure_training(dev, args)
+    training, vq = (None, None) if args.no_training else measure_training(dev, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -313,6 +326,7 @@ def run_ours(args):
             "contribution": contribution,
             "visibility": visibility,
             "training": training,
+            "vq": vq,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -393,9 +407,81 @@ def measure_training(dev, args):
            "ms_per_step": round(ms["autograd"], 3), "steps_per_s": round(1e3 / ms["autograd"], 2),
            "ms_per_step_direct": round(ms["direct"], 3), "steps": reps,
            "loss_total": round(float(L[3]) / 4, 5)}
+    vq = None if args.no_vq else measure_vq(tr, views, dev, args)
     del tr, views
     torch.cuda.empty_cache()
-    return out
+    return out, vq
+
+
+VQ_K, VQ_RATIO, VQ_ITERS = 8192, 0.4, 10
+
+
+def measure_vq(tr, views, dev, args):
+    """Contribution-based vector quantisation of the 4M-surfel scene (Sec.
+    3.3; Appendix C: 8192 entries, ratio 0.4): the contribution over the 4
+    views (Eq. 4), then quantised set, Lloyd's K-means (10 steps, tensor
+    cores) and the compressed layout, timed end to end; the assignment
+    kernel alone through the library's profiling events (tensor roofline:
+    2 m K C FLOPs per launch against the measured dense 16-bit peak); and the
+    render of the compressed scene against the FP32 one."""
+    import torch
+    from paper_2411_00771_gb300 import binding as B
+    n = tr.n
+    B.activate(tr.raw["scale"], tr.raw["opacity"], tr.scale, tr.opacity)
+    contrib = torch.zeros(n, device=dev)
+    for cam, _, _ in views:
+        tr.scene.contribution(cam, gamma=0.5, weight=1.0 / len(views), contrib=contrib)
+    params = (tr.raw["mu"].detach(), tr.raw["quat"].detach(), tr.scale, tr.opacity, tr.raw["sh"].detach())
+    u = torch.rand(VQ_K, device=dev, generator=torch.Generator(device=dev).manual_seed(20241101))
+    B.compress(params, 3, contrib, VQ_RATIO, VQ_K, 1, u, method=1)  # warm-up
+    torch.cuda.synchronize()
+    B.profile_read()
+    B.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    comp, info = B.compress(params, 3, contrib, VQ_RATIO, VQ_K, VQ_ITERS, u, method=1)
+    e1.record()
+    torch.cuda.synchronize()
+    B.profile_enable(False)
+    compress_ms = e0.elapsed_time(e1)
+    prof = B.profile_read()
+    t_assign, n_assign = prof["vq_assign"]
+    m = info["m"]
+    C = 48
+    flops = 2.0 * m * VQ_K * C
+    ms_launch = t_assign / max(n_assign, 1)
+    peak = measured_peak("bf16_tflops")
+    achieved = flops / (ms_launch * 1e-3) / 1e12
+    obj = info["objective"].cpu().numpy()
+    # renders: compressed against FP32, the 4 views
+    csc = B.CompressedScene(comp)
+    res = {}
+    for name, scn in (("fp32", tr.scene), ("compressed", csc)):
+        for _ in range(3):
+            for cam, _, _ in views:
+                scn.render(cam, save=False)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            for cam, _, _ in views:
+                scn.render(cam, save=False)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / (5 * len(views))
+    rows = comp["sh_table"].shape[0]
+    bytes_fp32 = n * (3 + 4 + 2 + 1 + C) * 4
+    bytes_comp = n * (12 + 8 + 4 + 2 + 4) + rows * C * 2
+    csc.close()
+    return {"surfels": n, "quantised": m, "K": VQ_K, "ratio": VQ_RATIO, "iters": VQ_ITERS,
+            "compress_ms": round(compress_ms, 2), "assign_launches": n_assign,
+            "objective_first": float(obj[0]), "objective_last": float(obj[-1]),
+            "render_ms_per_view_fp32": round(res["fp32"], 4),
+            "render_ms_per_view_compressed": round(res["compressed"], 4),
+            "bytes_fp32": bytes_fp32, "bytes_compressed": bytes_comp,
+            "roofline": {"kernel": "vq_assign_tc_kernel", "bound": "tensor", "achieved": round(achieved, 2),
+                         "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                         "ms_per_launch": round(ms_launch, 4),
+                         "peak_source": "measured dense bf16 (binary16 has the same nominal tensor rate)"}}
 
 
 VIS_POINTS, VIS_VIEWS = 31_400_000, 958

@@ -527,11 +527,12 @@ gs_status gs_server_destroy(gs_server* server);
  *   their summed duration (ms) and count, and forgets them.  Groups:
  *   0 preprocess, 1 scan/sort/emit/ranges, 2 forward blend, 3 loss,
  *   4 backward blend, 5 preprocess backward, 6 densify/filter,
- *   7 trim contribution and pruning. */
+ *   7 trim contribution and pruning, 8 the vector-quantisation assignment
+ *   kernel (tensor-core or CUDA-core). */
 enum {
   GS_PROF_PREPROCESS = 0, GS_PROF_SORT = 1, GS_PROF_BLEND_FWD = 2, GS_PROF_LOSS = 3,
   GS_PROF_BLEND_BWD = 4, GS_PROF_PREPROCESS_BWD = 5, GS_PROF_DENSIFY = 6, GS_PROF_CONTRIB = 7,
-  GS_PROF_GROUPS = 8
+  GS_PROF_VQ_ASSIGN = 8, GS_PROF_GROUPS = 9
 };
 uint64_t gs_kernel_launches(void);
 gs_status gs_profile_enable(int32_t on);

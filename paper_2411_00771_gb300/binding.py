@@ -168,7 +168,7 @@ _lib.gs_kernel_launches.argtypes = []
 
 EXPORTED = list(_SIGS) + ["gs_last_error", "gs_version", "gs_kernel_launches"]
 PROF_GROUPS = ["preprocess", "sort", "blend_fwd", "loss", "blend_bwd", "preprocess_bwd", "densify",
-               "contribution"]
+               "contribution", "vq_assign"]
 
 
 def lib():

@@ -389,7 +389,8 @@ enum ProfId {
   kProfPreprocessBwd = 5,
   kProfDensify = 6,
   kProfContrib = 7,
-  kProfCount = 8
+  kProfVqAssign = 8,
+  kProfCount = 9
 };
 void count_launch(int n = 1);
 void set_last_error(const char* msg);

@@ -577,12 +577,14 @@ cudaError_t launch_tc(const VqBufs& b, int m, int K, int num_sms, cudaStream_t s
   const int ntiles = (m + kBM - 1) / kBM;
   const int grid = ntiles < num_sms ? ntiles : num_sms;
   vq_assign_tc_kernel<D><<<grid, kTcThreads, smem, st>>>(b.xt, m, b.ct, K, b.best64, b.err);
+  count_launch();
   return cudaGetLastError();
 }
 
 template <int C>
 cudaError_t launch_simt(const VqBufs& b, int m, const uint16_t* cb, int K, cudaStream_t st) {
   vq_assign_simt_kernel<C><<<blocks_for(m, 256), 256, 0, st>>>(b.xr, m, cb, b.hl, K, b.best64);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -597,9 +599,11 @@ cudaError_t launch_vq_list(const uint8_t* keep, int n, int want, uint32_t* flags
                            uint32_t* scan_tmp, uint32_t* rows, cudaStream_t st) {
   if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
   vq_flags_kernel<<<blocks_for(n, 256), 256, 0, st>>>(keep, n, want, flags);
+  count_launch();
   cudaError_t e = launch_scan(flags, offs, n, total, scan_tmp, st);
   if (e != cudaSuccess || !rows) return e;
   vq_list_kernel<<<blocks_for(n, 256), 256, 0, st>>>(keep, offs, n, want, rows);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -607,12 +611,14 @@ cudaError_t launch_vq_pack_x(const float* sh, const VqBufs& b, int m, int C, int
   const int m_pad = (m + kBM - 1) / kBM * kBM;
   if (m_pad == 0) return cudaSuccess;
   vq_pack_x_kernel<<<blocks_for((int64_t)m_pad * D, 256), 256, 0, st>>>(sh, b.rows, m, m_pad, C, D, b.xr, b.xt, b.err);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_vq_init(const VqBufs& b, int m, int C, const float* u, int K, uint16_t* cb, cudaStream_t st) {
   if (m == 0) return cudaMemsetAsync(cb, 0, sizeof(uint16_t) * (size_t)K * C, st);
   vq_init_kernel<<<blocks_for((int64_t)K * C, 256), 256, 0, st>>>(b.xr, m, C, u, K, cb);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -621,10 +627,13 @@ cudaError_t launch_vq_assign(const VqBufs& b, int m, int C, int D, const uint16_
   if (m == 0) return cudaSuccess;
   const int m_pad = (m + kBM - 1) / kBM * kBM;
   vq_norms_kernel<<<blocks_for(K, 256), 256, 0, st>>>(cb, K, C, b.hl, b.err);
+  count_launch();
   cudaError_t e = cudaMemsetAsync(b.best64, 0xFF, sizeof(unsigned long long) * (size_t)m_pad, st);
   if (e != cudaSuccess) return e;
   if (tensor) {
     vq_pack_c_kernel<<<blocks_for((int64_t)K * D, 256), 256, 0, st>>>(cb, b.hl, K, C, D, b.ct, b.err);
+    count_launch();
+    ProfScope prof(kProfVqAssign, st);
     switch (D) {
       case 16: return launch_tc<16>(b, m, K, num_sms, st);
       case 32: return launch_tc<32>(b, m, K, num_sms, st);
@@ -632,6 +641,7 @@ cudaError_t launch_vq_assign(const VqBufs& b, int m, int C, int D, const uint16_
       default: return cudaErrorInvalidValue;
     }
   }
+  ProfScope prof(kProfVqAssign, st);
   switch (C) {
     case 3: return launch_simt<3>(b, m, cb, K, st);
     case 12: return launch_simt<12>(b, m, cb, K, st);
@@ -652,17 +662,20 @@ cudaError_t launch_vq_accum(const VqBufs& b, int m, int C, const uint16_t* cb, i
   vq_accum_kernel<<<blocks_for(m, 256), 256, 0, st>>>(b.xr, m, C, b.best64, cb, K, b.best_idx,
                                                        with_sums ? b.sums : nullptr, with_sums ? b.cnt : nullptr,
                                                        objective);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_vq_update(const VqBufs& b, int C, uint16_t* cb, int K, cudaStream_t st) {
   vq_update_kernel<<<blocks_for((int64_t)K * C, 256), 256, 0, st>>>(b.sums, b.cnt, K, C, cb);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_vq_scatter(const VqBufs& b, int m, int32_t* assign, cudaStream_t st) {
   if (m == 0) return cudaSuccess;
   vq_scatter_kernel<<<blocks_for(m, 256), 256, 0, st>>>(b.rows, b.best_idx, m, assign);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -678,13 +691,16 @@ cudaError_t launch_vq_pack_scene(int n, int C, int K, const float* quat, const f
   if (n == 0) return cudaSuccess;
   vq_pack_scene_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, C, K, quat, scale, opacity, keep, assign, kept_offs,
                                                            q16, s16, o16, sh_row, err);
+  count_launch();
   vq_pack_table_kernel<<<blocks_for((int64_t)n * C, 256), 256, 0, st>>>(n, C, K, sh, keep, kept_offs, table, err);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_vq_check_rows(const uint32_t* sh_row, int n, uint32_t rows, int* err, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   vq_check_rows_kernel<<<blocks_for(n, 256), 256, 0, st>>>(sh_row, n, rows, err);
+  count_launch();
   return cudaGetLastError();
 }
 
