@@ -55,8 +55,8 @@ def measured_peak(key):
 # DRAM bytes (read + write) of one blend_bwd launch on this workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the
 # full-size view); valid only for the kernel sources it was taken on.
-BLEND_BWD_TRAFFIC = {"bytes": 173771776 + 12999168,
-                     "sources_sha256": "17b3ed2e4671a4cac1e2f0c623a753e06b44894cc0bc27355c39f731deb18eb3"}
+BLEND_BWD_TRAFFIC = {"bytes": 173429248 + 12518400,
+                     "sources_sha256": "20b3f59631248660ebecfe2aef381d2486ff5f369caebed53a0c24c25474326e"}
 
 
 def blend_bwd_traffic():

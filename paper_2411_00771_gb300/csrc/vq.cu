@@ -13,8 +13,11 @@
 //     FP32 accumulation in TMEM) with the argmin fused into the epilogue.
 //     The operands are augmented so that one product gives the score:
 //     x' = (x, 1, 1, 0...), c' = (-2 c, h, l, 0...), h + l = ||c||^2 split into
-//     two binary16 values (h = rn(||c||^2), l = rn(||c||^2 - h)).  The m x K
-//     score matrix is never stored.  A CUDA-core FP32 kernel computes the same
+//     two binary16 values (h = rn(||c||^2), l = rn(||c||^2 - h)).  The
+//     epilogue takes the minimum of each group of 32 scores with three-input
+//     mins, keeps the scores of the best group so far (selects, skipped by
+//     warps where no lane improved) and finds the position once per tile.  The m x K score matrix is never
+//     stored.  A CUDA-core FP32 kernel computes the same
 //     scores for checking and for codebooks whose size is not a multiple of 256.
 //   - update: exact.  Binary16 values are integer multiples of 2^-24, so each
 //     coordinate is summed as a 64-bit integer (order-independent atomics),
@@ -149,6 +152,21 @@ __device__ __forceinline__ unsigned long long score_key(float s, int idx) {
   const uint32_t b = __float_as_uint(s);
   const uint32_t o = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
   return ((unsigned long long)o << 32) | (uint32_t)idx;
+}
+
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+// Smallest of 32 scores with three-input mins (16 instructions).
+__device__ __forceinline__ float min32(const float (&v)[32]) {
+  float a[11];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) a[i] = fmin3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+  a[10] = fminf(v[30], v[31]);
+  const float b0 = fmin3(a[0], a[1], a[2]), b1 = fmin3(a[3], a[4], a[5]), b2 = fmin3(a[6], a[7], a[8]);
+  return fminf(fmin3(b0, b1, b2), fminf(a[9], a[10]));
 }
 
 template <int D>
@@ -291,8 +309,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint32_t g = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      // per group of 32 scores only its minimum is compared; the scores of
+      // the best group are kept to find the position at the end of the tile
       float best = __int_as_float(0x7f800000);
-      int bi = 0;
+      int grp = 0;
+      float keep[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) keep[i] = best;
       for (int c = 0; c < nch; ++c, ++g) {
         const int tb = g & 1;
         const bool w = __all_sync(0xffffffffu, mbar_wait(&S.t_full[tb], (g >> 1) & 1, abort_flag));
@@ -306,20 +329,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int p = 0; p < 4; ++p) {
           float v[32];
           tc_ld32(base + (uint32_t)(p * 32), v);
-          const int code0 = c * kBN + half * 128 + p * 32;
+          const float m = min32(v);
+          const bool take = m < best;  // an equal minimum of a later group never wins
+          best = take ? m : best;
+          grp = take ? c * kBN + half * 128 + p * 32 : grp;
+          if (__any_sync(0xffffffffu, take)) {  // improvements grow rare along the tile
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (v[i] < best) {
-              best = v[i];
-              bi = code0 + i;
-            }
+            for (int i = 0; i < 32; ++i) keep[i] = take ? v[i] : keep[i];
+          }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.t_empty[tb]);
       }
       if (!ok) break;
-      atomicMin(best64 + (size_t)t * kBM + q * 32 + lane, score_key(best, bi));
+      int pos = 0;  // the first position of the minimum in its group
+#pragma unroll
+      for (int i = 31; i >= 0; --i) pos = keep[i] == best ? i : pos;
+      atomicMin(best64 + (size_t)t * kBM + q * 32 + lane, score_key(best, grp + pos));
     }
     if (!ok) {
       *abort_flag = 1;
