@@ -106,9 +106,9 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t a_desc, uin
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// 32 consecutive FP32 columns of this thread's TMEM lane (the registers are
+// valid after tc_wait_ld()).
+__device__ __forceinline__ void tc_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
       "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -118,10 +118,8 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor, no swizzle, K-major: the operand is stored
 // as 8-row x 16-byte core matrices (each 128 contiguous bytes); lbo = byte
@@ -326,16 +324,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(tb * kBN + half * 128);
 #pragma unroll 1
-        for (int p = 0; p < 4; ++p) {
-          float v[32];
-          tc_ld32(base + (uint32_t)(p * 32), v);
-          const float m = min32(v);
-          const bool take = m < best;  // an equal minimum of a later group never wins
-          best = take ? m : best;
-          grp = take ? c * kBN + half * 128 + p * 32 : grp;
-          if (__any_sync(0xffffffffu, take)) {  // improvements grow rare along the tile
+        for (int p = 0; p < 4; p += 2) {  // two groups per wait
+          uint32_t r[2][32];
+          tc_ld32_async(base + (uint32_t)(p * 32), r[0]);
+          tc_ld32_async(base + (uint32_t)(p * 32 + 32), r[1]);
+          tc_wait_ld();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) keep[i] = take ? v[i] : keep[i];
+          for (int h = 0; h < 2; ++h) {
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[h][i]);
+            const float m = min32(v);
+            const bool take = m < best;  // an equal minimum of a later group never wins
+            best = take ? m : best;
+            grp = take ? c * kBN + half * 128 + (p + h) * 32 : grp;
+            if (__any_sync(0xffffffffu, take)) {  // improvements grow rare along the tile
+#pragma unroll
+              for (int i = 0; i < 32; ++i) keep[i] = take ? v[i] : keep[i];
+            }
           }
         }
         tc_fence_before();
