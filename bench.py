@@ -216,8 +216,12 @@ def run_ours(args):
     adj_s = torch.zeros((11, H, W), device=dev)
     adj_l = torch.zeros((11, H, W), device=dev)
     losses = torch.empty(4, device=dev)
-    grads = {k: torch.zeros_like(v) for k, v in P.items()}
-    screen = torch.zeros((3, n, 2), device=dev)
+    # the gradients and screen gradients live in one buffer: one fill per step
+    sizes = [v.numel() for v in P.values()] + [3 * n * 2]
+    flat = torch.zeros(sum(sizes), device=dev)
+    views = list(torch.split(flat, sizes))
+    grads = {k: views[i].view(v.shape) for i, (k, v) in enumerate(P.items())}
+    screen = views[-1].view(3, n, 2)
     stats = torch.zeros((n, 4), device=dev)
     tgt = torch.from_numpy(tgt_np).to(dev)
     tinv = torch.from_numpy(tinv_np).to(dev)
@@ -227,9 +231,7 @@ def run_ours(args):
     def step(keep=False):
         o, frame = sc.render(cam, out=out)
         B.loss(o, tgt, tinv, WEIGHTS, adj_total=adj_t, adj_ssim=adj_s, adj_l1=adj_l, losses=losses)
-        for g in grads.values():
-            g.zero_()
-        screen.zero_()
+        flat.zero_()
         sc.backward(frame, [adj_t, adj_s, adj_l], masks, grads, screen)
         sc.densify_accumulate(frame, screen, stats)
         mask, _, _ = B.densify_select(stats, P["scale"], OMEGA, GRAD_THR, ETA_THR)
@@ -250,7 +252,6 @@ def run_ours(args):
     clocks = ClockSampler(gpu_uuid(local))
     barrier()
     torch.cuda.synchronize()
-    B.profile_enable(True)
     l0 = B.kernel_launches()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -262,9 +263,16 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     launches = B.kernel_launches() - l0
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    # stage times and per-launch kernel times from a separate pass with the
+    # library's profiling events on (they are not part of the timed steps)
+    B.profile_read()
+    B.profile_enable(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
     B.profile_enable(False)
     prof = B.profile_read()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
     ms_step_max = max_over_ranks(ms_step, world, dist, dev)
 
     # end to end through the public API: host targets in, losses and the
@@ -320,7 +328,7 @@ def run_ours(args):
         cpu = cpu_baseline(scene_np, cam, tgt_np, tinv_np, budget_s=20.0)
     serving = None
     if not args.no_serving:
-        del grads, screen, stats, adj_t, adj_s, adj_l
+        del grads, screen, flat, views, stats, adj_t, adj_s, adj_l
         torch.cuda.empty_cache()
         serving = run_serving(args, dev, sc, P, rank)
 

@@ -16,9 +16,10 @@
 //     two binary16 values (h = rn(||c||^2), l = rn(||c||^2 - h)).  The
 //     epilogue takes the minimum of each group of 32 scores with three-input
 //     mins, keeps the scores of the best group so far (selects, skipped by
-//     warps where no lane improved) and finds the position once per tile.  The m x K score matrix is never
-//     stored.  A CUDA-core FP32 kernel computes the same
-//     scores for checking and for codebooks whose size is not a multiple of 256.
+//     warps where no lane improved) and finds the position once per tile.
+//     The m x K score matrix is never stored.  A CUDA-core FP32 kernel
+//     computes the same scores for checking and for codebooks whose size is
+//     not a multiple of 256.
 //   - update: exact.  Binary16 values are integer multiples of 2^-24, so each
 //     coordinate is summed as a 64-bit integer (order-independent atomics),
 //     and the centroid is rn16((double(sum) * 2^-24) / count); an entry with
