@@ -228,9 +228,10 @@ def run_ours(args):
     masks = [0x7 | (1 << 5), 0x7, 0x7]
     keep_frame = [None]
 
-    def step(keep=False):
+    def step(keep=False, tgt_in=None, tinv_in=None):
         o, frame = sc.render(cam, out=out)
-        B.loss(o, tgt, tinv, WEIGHTS, adj_total=adj_t, adj_ssim=adj_s, adj_l1=adj_l, losses=losses)
+        B.loss(o, tgt if tgt_in is None else tgt_in, tinv if tinv_in is None else tinv_in, WEIGHTS,
+               adj_total=adj_t, adj_ssim=adj_s, adj_l1=adj_l, losses=losses)
         flat.zero_()
         sc.backward(frame, [adj_t, adj_s, adj_l], masks, grads, screen)
         sc.densify_accumulate(frame, screen, stats)
@@ -283,19 +284,37 @@ def run_ours(args):
     mask_h = torch.empty(n, dtype=torch.uint8).pin_memory()
     e2e_steps = max(3, args.steps // 2)
 
-    def step_e2e():
-        tgt.copy_(tgt_h, non_blocking=True)
-        tinv.copy_(tinv_h, non_blocking=True)
-        mask = step()
+    # inputs double-buffered: the next step's targets are copied on a second
+    # stream while the current step computes (as a training loop prefetches)
+    tgt_d, tinv_d = [tgt, torch.empty_like(tgt)], [tinv, torch.empty_like(tinv)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    free = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def prefetch(b):
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(free[b])  # the step that last read buffer b is done
+            tgt_d[b].copy_(tgt_h, non_blocking=True)
+            tinv_d[b].copy_(tinv_h, non_blocking=True)
+            ready[b].record(copy_stream)
+
+    def step_e2e(i):
+        b = i % 2
+        torch.cuda.current_stream().wait_event(ready[b])
+        mask = step(tgt_in=tgt_d[b], tinv_in=tinv_d[b])
+        free[b].record()
+        prefetch(1 - b)
         loss_h.copy_(losses, non_blocking=True)
         mask_h.copy_(mask, non_blocking=True)
 
-    step_e2e()
+    prefetch(0)
+    step_e2e(0)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        step_e2e()
+    prefetch(0)
+    for i in range(e2e_steps):
+        step_e2e(i)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, world, dist, dev)
 
