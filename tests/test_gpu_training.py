@@ -34,16 +34,24 @@ def test_geometry_loss_matches_oracle():
     assert np.all(a[10] == np.float32(0.3 / (56 * 72)))
 
 
-def test_adam_matches_oracle():
+@pytest.mark.parametrize("n,offset", [(1 << 20, 0), (1000003, 0), (4099, 1)])
+def test_adam_matches_oracle(n, offset):
+    """Four values per thread when every array is 16-byte aligned, one at a
+    time for the tail and for misaligned arrays (offset by one float)."""
     from paper_2411_00771_gb300 import binding as B
     rng = np.random.default_rng(3)
-    n = 1 << 20
     p0 = rng.normal(size=n).astype(np.float32)
-    p, m, v = (torch.from_numpy(x).cuda() for x in (p0.copy(), np.zeros(n, np.float32), np.zeros(n, np.float32)))
+
+    def dev(x):
+        buf = torch.zeros(n + offset, device="cuda")
+        buf[offset:] = torch.from_numpy(x).cuda()
+        return buf[offset:]
+
+    p, m, v = dev(p0.copy()), dev(np.zeros(n, np.float32)), dev(np.zeros(n, np.float32))
     rp, rm, rv = p0.astype(np.float64), np.zeros(n), np.zeros(n)
     for k in range(1, 4):
         g = rng.normal(size=n).astype(np.float32)
-        B.adam_step(p, torch.from_numpy(g).cuda(), m, v, 1e-3, k)
+        B.adam_step(p, dev(g), m, v, 1e-3, k)
         rp, rm, rv = oracle.adam_step(rp, g, rm, rv, 1e-3, k)
     torch.cuda.synchronize()
     assert np.abs(p.cpu().numpy() - rp).max() <= 1e-6
