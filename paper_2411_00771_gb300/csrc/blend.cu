@@ -853,8 +853,17 @@ __global__ void __launch_bounds__(kThreads, 5) blend_bwd_kernel(
   #pragma unroll
         for (int i = 0; i < kN; ++i) v[i] = 0.f;
         const float4 e3 = s3[kk];
-        bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
-        bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
+        // a pixel row with no hit in the whole warp needs no gradient pass (a
+        // masked pair leaves the pixel's state and the sums unchanged)
+        const bool anyA = __any_sync(0xffffffffu, qa.hit), anyB = __any_sync(0xffffffffu, qb.hit);
+        if (anyA && anyB) {
+          bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
+          bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
+        } else if (anyA) {
+          bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
+        } else {
+          bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
+        }
         if (__popc(ballot) == 1) {
           if (contrib) {
   #pragma unroll
