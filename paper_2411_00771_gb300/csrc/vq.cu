@@ -14,7 +14,7 @@
 //     The operands are augmented so that one product gives the score:
 //     x' = (x, 1, 1, 0...), c' = (-2 c, h, l, 0...), h + l = ||c||^2 split into
 //     two binary16 values (h = rn(||c||^2), l = rn(||c||^2 - h)).  The
-//     epilogue takes the minimum of each group of 32 scores with three-input
+//     epilogue takes the minimum of each group of 16 scores with three-input
 //     mins, keeps the scores of the best group so far (selects, skipped by
 //     warps where no lane improved) and finds the position once per tile.
 //     The m x K score matrix is never stored.  A CUDA-core FP32 kernel
@@ -158,14 +158,12 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
   asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
   return r;
 }
-// Smallest of 32 scores with three-input mins (16 instructions).
-__device__ __forceinline__ float min32(const float (&v)[32]) {
-  float a[11];
-#pragma unroll
-  for (int i = 0; i < 10; ++i) a[i] = fmin3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-  a[10] = fminf(v[30], v[31]);
-  const float b0 = fmin3(a[0], a[1], a[2]), b1 = fmin3(a[3], a[4], a[5]), b2 = fmin3(a[6], a[7], a[8]);
-  return fminf(fmin3(b0, b1, b2), fminf(a[9], a[10]));
+// Smallest of the 16 scores v[o..o+15] with three-input mins (8 instructions).
+__device__ __forceinline__ float min16(const float (&v)[32], int o) {
+  const float a0 = fmin3(v[o], v[o + 1], v[o + 2]), a1 = fmin3(v[o + 3], v[o + 4], v[o + 5]);
+  const float a2 = fmin3(v[o + 6], v[o + 7], v[o + 8]), a3 = fmin3(v[o + 9], v[o + 10], v[o + 11]);
+  const float a4 = fmin3(v[o + 12], v[o + 13], v[o + 14]);
+  return fminf(fmin3(a0, a1, a2), fmin3(a3, a4, v[o + 15]));
 }
 
 template <int D>
@@ -312,9 +310,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // the best group are kept to find the position at the end of the tile
       float best = __int_as_float(0x7f800000);
       int grp = 0;
-      float keep[32];
+      float keep[16];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) keep[i] = best;
+      for (int i = 0; i < 16; ++i) keep[i] = best;
       for (int c = 0; c < nch; ++c, ++g) {
         const int tb = g & 1;
         const bool w = __all_sync(0xffffffffu, mbar_wait(&S.t_full[tb], (g >> 1) & 1, abort_flag));
@@ -335,13 +333,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float v[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[h][i]);
-            const float m = min32(v);
-            const bool take = m < best;  // an equal minimum of a later group never wins
-            best = take ? m : best;
-            grp = take ? c * kBN + half * 128 + (p + h) * 32 : grp;
-            if (__any_sync(0xffffffffu, take)) {  // improvements grow rare along the tile
 #pragma unroll
-              for (int i = 0; i < 32; ++i) keep[i] = take ? v[i] : keep[i];
+            for (int o = 0; o < 32; o += 16) {  // groups of 16 scores
+              const float m = min16(v, o);
+              const bool take = m < best;  // an equal minimum of a later group never wins
+              best = take ? m : best;
+              grp = take ? c * kBN + half * 128 + (p + h) * 32 + o : grp;
+              if (__any_sync(0xffffffffu, take)) {  // improvements grow rare along the tile
+#pragma unroll
+                for (int i = 0; i < 16; ++i) keep[i] = take ? v[o + i] : keep[i];
+              }
             }
           }
         }
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (!ok) break;
       int pos = 0;  // the first position of the minimum in its group
 #pragma unroll
-      for (int i = 31; i >= 0; --i) pos = keep[i] == best ? i : pos;
+      for (int i = 15; i >= 0; --i) pos = keep[i] == best ? i : pos;
       atomicMin(best64 + (size_t)t * kBM + q * 32 + lane, score_key(best, grp + pos));
     }
     if (!ok) {
