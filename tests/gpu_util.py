@@ -77,3 +77,88 @@ def visible(pre):
     'visible in this view')."""
     r = pre["rect"]
     return (pre["live"] > 0) & (r[:, 2] > r[:, 0]) & (r[:, 3] > r[:, 1])
+
+
+# ---- sampled-pixel comparison of large views ----------------------------------
+
+def cond_scale(cond):
+    """Tolerance factor of a pixel whose blended object-branch pairs have
+    centred-Jacobian condition number up to k.  The plane coordinates
+    (u, v) = Ji d come from an inverse Jacobian held in FP32, so their
+    relative error is up to about k 2^-23; rho = u^2 + v^2 doubles it, and
+    alpha = o exp(-rho / 2) turns it into a relative error of alpha of
+    (rho / 2)(2 k 2^-23) <= 9 k 2^-23 (rho <= 9), which every weighted plane
+    inherits.  Nearly edge-on surfels (large k) are common in an oblique 4K
+    view of a dense scene; where that bound exceeds the 2e-5 of the render
+    tolerance, the tolerance grows with it."""
+    return np.maximum(1.0, 9.0 * cond * 2.0 ** -23 / TOL_ABS)
+
+
+def compare_sampled(scene, cam, out, cnt, n_pix, seed):
+    """Sampled pixels against the oracle with the render tolerances, scaled
+    by cond_scale() at pixels with ill-conditioned pairs."""
+    import oracle
+    W, H = int(cam["width"]), int(cam["height"])
+    pix = np.random.default_rng(seed).choice(W * H, n_pix, replace=False)
+    ref = oracle.render(scene, cam, pixels=pix)
+    flag_any = oracle.FLAG_ALPHA | oracle.FLAG_RHO | oracle.FLAG_TSTOP | oracle.FLAG_MEDIAN
+    bad = (ref["flags"] & flag_any) != 0
+    assert bad.mean() < 0.01, bad.sum()
+    g = np.asarray(out, np.float64).reshape(12, -1)[:, pix]
+    scale = cond_scale(oracle.pixel_cond(scene, cam).reshape(-1)[pix])
+    q = np.abs(g - ref["out"]) / (plane_tolerance(ref["out"]) * scale[None, :])
+    branch = (ref["flags"] & oracle.FLAG_BRANCH) != 0
+    for p, name in enumerate(PLANES):
+        ok = ~bad & ~branch if p in DEPTH_PLANES else ~bad
+        e = q[p, ok].max() if ok.any() else 0.0
+        assert e <= 1.0, (name, e)
+    assert np.array_equal(cnt.reshape(-1)[pix][~bad], ref["count"][~bad])
+    return ref
+
+
+def crop_camera(cam, x0, y0, size):
+    c = dict(cam)
+    c["width"] = c["height"] = size
+    c["cx"] = cam["cx"] - x0
+    c["cy"] = cam["cy"] - y0
+    return c
+
+
+def check_window_backward(scene, cam, x0, y0, S, seed):
+    """The backward through a window: the full view's backward with adjoints
+    that are zero outside the S x S window at (x0, y0) must equal the backward
+    of a crop camera over that window (the same pixels and surfels), which the
+    oracle checks over every pixel and surfel (1e-3 relative).  The two renders
+    agree up to pixels with a decision at a threshold (pixel offsets are taken
+    from different tile origins, so they round differently)."""
+    import oracle
+    H, W = int(cam["height"]), int(cam["width"])
+    rng = np.random.default_rng(seed)
+    win = (rng.normal(size=(11, S, S)) * 1e-3).astype(np.float32)
+    n = scene["mu"].shape[0]
+    sc, d, out, cnt, frame = gpu_render(scene, cam)
+    adj = torch.zeros((11, H, W), device="cuda")
+    adj[:, y0:y0 + S, x0:x0 + S] = torch.from_numpy(win).cuda()
+    gf = {k: torch.zeros_like(v) for k, v in d.items()}
+    sf = torch.zeros((1, n, 2), device="cuda")
+    sc.backward(frame, [adj], [0x7FF], gf, sf)
+    frame.release()
+    cc = crop_camera(cam, x0, y0, S)
+    out_c, frame_c = sc.render(cc)
+    gc = {k: torch.zeros_like(v) for k, v in d.items()}
+    scr = torch.zeros((1, n, 2), device="cuda")
+    sc.backward(frame_c, [torch.from_numpy(win).cuda()], [0x7FF], gc, scr)
+    frame_c.release()
+    torch.cuda.synchronize()
+    full = out[:, y0:y0 + S, x0:x0 + S].cpu().numpy().astype(np.float64)
+    crop = out_c.cpu().numpy().astype(np.float64)
+    rel = np.abs(full - crop) / np.maximum(1.0, np.abs(crop))
+    assert (rel[:11] > 1e-4).any(axis=0).mean() <= 0.01
+    for k in ("mu", "quat", "scale", "opacity", "sh"):
+        e = rel_err(gf[k].cpu().numpy(), gc[k].cpu().numpy())
+        assert e <= 1e-3, (k, e)
+    ref = oracle.backward(scene, cc, win[None].astype(np.float64))
+    for k in ("mu", "quat", "scale", "opacity", "sh"):
+        e = rel_err(gc[k].cpu().numpy(), ref[k].reshape(gc[k].shape))
+        assert e <= 1e-3, (k, e)
+    assert rel_err(scr.cpu().numpy()[0], ref["screen"][0]) <= 1e-3

@@ -274,3 +274,20 @@ def test_statistics_take_each_views_own_screen_gradient(autograd):
     torch.cuda.synchronize()
     assert float(a.stats[:, 3].sum()) > 0
     assert torch.allclose(a.stats, b.stats, rtol=1e-5, atol=1e-9)
+
+
+def test_training_workload_view_at_full_size():
+    """One view of the 4M-surfel training workload as the benchmark builds it
+    (orbit 200 m up, 1600x900): 10 000 sampled pixels against the oracle, and
+    the backward through a 256x256 window against a crop camera and the
+    oracle."""
+    scene, info = syn.city_scene(seed=20241101 + 3, n=4_000_000)
+    rng = np.random.default_rng(20241101 + 4)
+    cam = syn.orbit_camera(rng, 1600, 900, radius=rng.uniform(150.0, 250.0), altitude=200.0)
+    sc, d, out, cnt, frame = gu.gpu_render(scene, cam)
+    frame.release()
+    ref = gu.compare_sampled(scene, cam, out.cpu().numpy(), cnt.cpu().numpy(), 10_000, seed=3)
+    assert (ref["count"] > 0).mean() > 0.5
+    del sc, d, out, cnt
+    torch.cuda.empty_cache()
+    gu.check_window_backward(scene, cam, 672, 324, 256, seed=4)
