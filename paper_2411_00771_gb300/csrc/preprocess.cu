@@ -562,8 +562,14 @@ cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDe
   if (e != cudaSuccess) return e;
   compact_kernel<<<div_up(P.n, 256), 256, 0, st>>>(flags, dkey, P.n, cand);
   // candidates are a subset of the surfels; a grid-stride loop over the
-  // device-side count, two CTAs per SM
-  const unsigned blocks = div_up(P.n, 256) < 304u ? div_up(P.n, 256) : 304u;
+  // device-side count, three CTAs per SM (what its registers allow)
+  static const unsigned resident = [] {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return 3u * (unsigned)sms;
+  }();
+  const unsigned blocks = div_up(P.n, 256) < resident ? div_up(P.n, 256) : resident;
   switch (P.sh_degree) {
     case 0: preprocess_main_kernel<0><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
     case 1: preprocess_main_kernel<1><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
