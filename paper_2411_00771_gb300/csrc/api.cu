@@ -631,7 +631,7 @@ gs_status gs_backward(gs_scene* sc, gs_frame* f, const float* const* adj_sets,
   const SetDev set = to_dev(sc->settings);
   if (e == cudaSuccess)
     e = launch_blend_bwd(f->cam, set, f->order, f->rec, f->geom, f->vals, f->ranges, f->out, f->last, f->med, adj,
-                         grec, screen_grads, n, f->counters, st);
+                         grec, screen_grads, n, f->K, f->counters, st);
   if (e == cudaSuccess) e = launch_preprocess_bwd(sc->P, f->cam, f->cand, f->ncand, f->tcount, grec, *grads, st);
   sc->al.put(grec, sizeof(float) * kGradRec * (size_t)(n > 0 ? n : 1), st);
   if (e != cudaSuccess) return cuda_fail(e, "gs_backward");

@@ -575,6 +575,10 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_batched_kernel(BlendBatch 
 // Backward.
 
 constexpr int kMaxSets = 3;
+// Average tile-list length from which the backward takes the 4-CTA variant:
+// 200 (the 1M-surfel aerial view) ran best with 5 CTAs per SM, 590 (the
+// 4M-surfel orbit view) with 4.
+constexpr int kDenseListLen = 400;
 
 // Per-pair gradient vector.  General layout (any adjoint planes):
 //   [0..15] per-surfel record (d Ji, d e, d c, d p_z, d opacity, d rgb,
@@ -772,8 +776,10 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
   }
 }
 
-template <bool kLoss>
-__global__ void __launch_bounds__(kThreads, 5) blend_bwd_kernel(
+// kMinCtas: the CTAs per SM the register budget is sized for (5: 96
+// registers; 4: up to 128, for dense lists of small footprints).
+template <bool kLoss, int kMinCtas>
+__global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
     CamDev cam, SetDev set, float rf, const uint32_t* __restrict__ order, const float4* __restrict__ rec,
     const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals, const int2* __restrict__ ranges,
     const float* __restrict__ out, const int32_t* __restrict__ last, const int32_t* __restrict__ med,
@@ -1062,7 +1068,7 @@ cudaError_t launch_blend_fwd_batched(const BlendBatch& batch, int grid, cudaStre
 cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
                              const RowGeom* geom, const uint32_t* vals, const int2* ranges, const float* out,
                              const int32_t* last, const int32_t* med, const AdjDev& adj,
-                             float* grec, float* screen, int n, unsigned long long* counters,
+                             float* grec, float* screen, int n, int64_t K, unsigned long long* counters,
                              cudaStream_t st) {
   const unsigned grid = (unsigned)cam.tiles_x * (unsigned)cam.tiles_y;
   const float rf = (float)sqrt((double)set.rho_max / (double)set.sinv);
@@ -1070,13 +1076,21 @@ cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const uint32_
   // the other sets through colour: a leaner kernel for that layout
   bool loss_layout = (adj.mask[0] & ~(GS_MASK_RGB | (1u << GS_PLANE_INVDEPTH))) == 0u;
   for (int s = 1; s < adj.n_sets; ++s) loss_layout = loss_layout && (adj.mask[s] & ~GS_MASK_RGB) == 0u;
+  // long lists (many small footprints per tile) run faster with more
+  // registers per thread than with a fifth CTA per SM; both compute the same
+  const bool dense = K >= (int64_t)kDenseListLen * (int64_t)grid;
   ProfScope ps(kProfBlendBwd, st);
-  if (loss_layout)
-    blend_bwd_kernel<true><<<grid, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out, last,
-                                                      med, adj, grec, screen, n, counters);
-  else
-    blend_bwd_kernel<false><<<grid, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out, last,
-                                                       med, adj, grec, screen, n, counters);
+#define GS_BWD(L, M)                                                                                           \
+  blend_bwd_kernel<L, M><<<grid, kThreads, 0, st>>>(cam, set, rf, order, rec, geom, vals, ranges, out, last, med, \
+                                                    adj, grec, screen, n, counters)
+  if (loss_layout) {
+    if (dense) GS_BWD(true, 4);
+    else GS_BWD(true, 5);
+  } else {
+    if (dense) GS_BWD(false, 4);
+    else GS_BWD(false, 5);
+  }
+#undef GS_BWD
   count_launch();
   return cudaGetLastError();
 }

@@ -297,7 +297,7 @@ constexpr int kGradRec = 16;  // Ji(4) e(2) c(2) p_z(1) opacity(1) rgb(3) n(3)
 cudaError_t launch_blend_bwd(const CamDev& cam, const SetDev& set, const uint32_t* order, const float4* rec,
                              const RowGeom* geom, const uint32_t* vals, const int2* ranges, const float* out,
                              const int32_t* last, const int32_t* med, const AdjDev& adj,
-                             float* grec, float* screen, int n, unsigned long long* counters,
+                             float* grec, float* screen, int n, int64_t K, unsigned long long* counters,
                              cudaStream_t st);
 
 // Trim contribution (Sec. 3.3, Eq. 3) of one view over the frame's tile
