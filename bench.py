@@ -55,8 +55,8 @@ def measured_peak(key):
 # DRAM bytes (read + write) of one blend_bwd launch on this workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the
 # full-size view); valid only for the kernel sources it was taken on.
-BLEND_BWD_TRAFFIC = {"bytes": 173365504 + 12559104,
-                     "sources_sha256": "fd8111bcf166cfa209caee05c93c53b192528d900cf3bfbfddb2c62bc4819f61"}
+BLEND_BWD_TRAFFIC = {"bytes": 173498880 + 12352256,
+                     "sources_sha256": "1cd9e09a91486b181251c0e18ac59717778c8cb85654a43281f1d093b2313cd1"}
 
 
 def blend_bwd_traffic():
