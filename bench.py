@@ -59,15 +59,21 @@ BLEND_BWD_TRAFFIC = {"bytes": 173498880 + 12352256,
                      "sources_sha256": "1cd9e09a91486b181251c0e18ac59717778c8cb85654a43281f1d093b2313cd1"}
 
 
-def blend_bwd_traffic():
-    """The captured traffic if blend.cu + gs2d_internal.cuh are unchanged, else None."""
+def blend_sources_sha256():
+    """SHA-256 of blend.cu followed by gs2d_internal.cuh."""
     import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
     h = hashlib.sha256()
     for f in ("blend.cu", "gs2d_internal.cuh"):
         with open(os.path.join(here, "paper_2411_00771_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return BLEND_BWD_TRAFFIC["bytes"] if h.hexdigest() == BLEND_BWD_TRAFFIC["sources_sha256"] else None
+    return h.hexdigest()
+
+
+def blend_bwd_traffic():
+    """The captured traffic if blend.cu + gs2d_internal.cuh are unchanged, else None."""
+    ok = blend_sources_sha256() == BLEND_BWD_TRAFFIC["sources_sha256"]
+    return BLEND_BWD_TRAFFIC["bytes"] if ok else None
 
 
 def parse(argv=None):
