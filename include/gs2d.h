@@ -155,6 +155,7 @@ typedef struct {
   int64_t bwd_warp_entries;    /* (warp, entry) steps with a blended pair     */
   int64_t bwd_warp_lanes;      /* blended pairs summed over those steps       */
   int32_t tiles_x, tiles_y;
+  int64_t n_candidates;     /* surfels the conservative cull kept (sorted)   */
 } gs_frame_info;
 /* Counters of a frame (synchronises `stream`). */
 gs_status gs_frame_get_info(gs_frame* frame, gs_frame_info* info, void* stream);
@@ -166,6 +167,30 @@ gs_status gs_frame_get_info(gs_frame* frame, gs_frame_info* info, void* stream);
  * (device int32, may be NULL). */
 gs_status gs_frame_copy_lists(gs_frame* frame, int32_t* values, int64_t cap, int32_t* ranges,
                               int32_t* rects, void* stream);
+
+/* Debug / parity access to what the tile binning (Eq. 1's front-to-back
+ * order needs every surfel listed in each tile its {rho <= rho_max} set
+ * reaches) was computed from, per surfel, so that a checker can rebuild the
+ * tile lists and ranges independently:
+ *  geom:       device [n][14] 32-bit words (may be NULL), the FP32 footprint
+ *              shape: words 0-3 the projected centre as two-float sums
+ *              (c_x hi, c_x lo, c_y hi, c_y lo); words 4-9 the ellipse
+ *              {rho_obj <= rho_max} relative to c, (d - e0)^T G^-1 (d - e0) <= 1
+ *              given as (e0_x, e0_y, hy = sqrt(G22), t = G12 / sqrt(G11),
+ *              slope = G12 / G22, wsc = sqrt(det G) / G22), hy < 0 when the
+ *              disk has no ellipse; words 10-13 (int32) the pixel-centre box
+ *              [ilo, ihi] x [jlo, jhi] of the whole footprint, clipped to the
+ *              image.  A tile row lists the tile columns whose pixel centres
+ *              in that row band meet the ellipse or the screen-filter disk
+ *              |d| <= sqrt(rho_max / screen_inv_sigma2), each side widened
+ *              by an FP32 rounding margin;
+ *  depth:      device float [n] (may be NULL), the FP32 centre depth that
+ *              orders each tile's list (ties by surfel index);
+ *  tile_count: device int32 [n] (may be NULL), the number of tiles listing
+ *              the surfel; geom and depth are defined only where it is > 0.
+ * Asynchronous on `stream`; GS_ERR_ARG for a null frame. */
+gs_status gs_frame_copy_cover(gs_frame* frame, int32_t* geom, float* depth, int32_t* tile_count,
+                              void* stream);
 
 /* Sec. 3.1 and 3.2 losses: L1 = mean |C - C*|, SSIM with an 11x11 Gaussian
  * window (sigma 1.5, zero padded, C1 = 0.01^2, C2 = 0.03^2) averaged over
@@ -502,6 +527,7 @@ typedef struct {
   int64_t batches, batched_views;   /* blend launches and views they carried */
   int64_t bytes_in_use;             /* resident device buffers               */
   double latency_p50_ms, latency_p99_ms, latency_mean_ms; /* submit to done  */
+  int64_t pairs_evaluated, pairs_blended; /* blend work of the served views    */
 } gs_server_stats_t;
 gs_status gs_server_create(gs_server** out, size_t budget_bytes, int32_t max_slots,
                            const gs_allocator* alloc);

@@ -78,7 +78,7 @@ class gs_frame_info(ctypes.Structure):
                 ("pairs_evaluated", ctypes.c_int64), ("pairs_blended", ctypes.c_int64),
                 ("bwd_pairs_evaluated", ctypes.c_int64), ("bwd_warp_entries", ctypes.c_int64),
                 ("bwd_warp_lanes", ctypes.c_int64), ("tiles_x", ctypes.c_int32),
-                ("tiles_y", ctypes.c_int32)]
+                ("tiles_y", ctypes.c_int32), ("n_candidates", ctypes.c_int64)]
 
 
 class gs_request(ctypes.Structure):
@@ -91,7 +91,8 @@ class gs_server_stats_t(ctypes.Structure):
                 ("in_flight", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("batched_views", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
                 ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
-                ("latency_mean_ms", ctypes.c_double)]
+                ("latency_mean_ms", ctypes.c_double), ("pairs_evaluated", ctypes.c_int64),
+                ("pairs_blended", ctypes.c_int64)]
 
 
 class gs_loss_weights(ctypes.Structure):
@@ -113,6 +114,7 @@ _SIGS = {
     "gs_frame_release": [_V, _V],
     "gs_frame_get_info": [_V, ctypes.POINTER(gs_frame_info), _V],
     "gs_frame_copy_lists": [_V, _V, ctypes.c_int64, _V, _V, _V],
+    "gs_frame_copy_cover": [_V, _V, _V, _V, _V],
     "gs_loss": [ctypes.c_int32, ctypes.c_int32, _V, _V, _V, ctypes.POINTER(gs_loss_weights), _V, _V,
                 _V, _V, _V],
     "gs_loss_noalloc": [ctypes.c_int32, ctypes.c_int32, _V, _V, _V, ctypes.POINTER(gs_loss_weights), _V,
@@ -246,6 +248,19 @@ class Frame:
                                         _ptr(rects, torch.int32) if self.scene.n > 0 else None,
                                         _stream(stream)))
         return vals[:K], ranges, rects[:self.scene.n]
+
+    def cover(self, stream=None):
+        """Per-surfel footprint shapes [n][14] (int32 words: 10 FP32 values
+        then 4 int32), FP32 centre depths [n] and tile counts [n] (the
+        inputs of the tile binning; see gs_frame_copy_cover)."""
+        n = self.scene.n
+        dev = self.out.device
+        geom = torch.zeros((max(n, 1), 14), dtype=torch.int32, device=dev)
+        depth = torch.zeros(max(n, 1), dtype=torch.float32, device=dev)
+        tcount = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
+        _check(_lib.gs_frame_copy_cover(self.handle, _ptr(geom, torch.int32), _ptr(depth, torch.float32),
+                                        _ptr(tcount, torch.int32), _stream(stream)))
+        return geom[:n], depth[:n], tcount[:n]
 
     def release(self, stream=None):
         if self.handle:

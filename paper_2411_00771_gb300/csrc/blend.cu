@@ -21,6 +21,7 @@
 // memory once per (surfel, tile).
 #include <math.h>
 
+#include "gs2d_df.cuh"
 #include "gs2d_internal.cuh"
 
 namespace gs2d {
@@ -51,26 +52,76 @@ __device__ __forceinline__ int local_x(int t) { return (((t >> 5) & 1) << 3) | (
 __device__ __forceinline__ int local_y(int t) { return ((t >> 6) << 3) | ((t >> 3) & 3); }
 
 // Staged entry: s0 = (c.x, c.y relative to the tile origin, e.x, e.y),
-// s1 = Ji, s2 = (p_z, opacity, r, g), s3 = (b, n.x, n.y, n.z); wmask bit w
-// set when the footprint may reach warp w's pixel block.
+// s2 = (p_z, opacity, r, g), s3 = (b, n.x, n.y, n.z); wmask bit w set when
+// the footprint may reach warp w's pixel block, kPrecise set for the split
+// evaluation below.  Direct evaluation: s1 = Ji, s4 = s5 = 0, and
+// (u, v) den = Ji d with d = x - c in FP32, whose error is small for a
+// well-conditioned footprint (the preprocess decides; see its record).
+// Split evaluation: s1 = Jh, s4 = Jl, s5 = (nu0h, nv0h, nu0l, nv0l).
+//
+// Tile-relative ray-splat coordinates.  For a pixel at offset (lx, ly) from
+// the tile origin o, Ji d = Ji (o - c) + Ji (lx, ly) = n0 + Ji (lx, ly).  Held
+// in FP32 as Ji d, the coordinates of an ill-conditioned footprint (a nearly
+// edge-on or elongated disk: large Ji, pixel far from c along the long axis)
+// would carry an absolute error of about 2^-24 |Ji| |d|, far above the
+// error of the exact value near the support boundary.  Instead, per (entry,
+// tile): n0 is computed in double-float and both n0 and Ji are split on a
+// common power-of-two grid 2^g chosen from their magnitudes, the high parts
+// (nu0h on multiples of 2^g, Jh on multiples of 2^(g+1)) so coarse that
+// nu0h + Jh (lx, ly) is exact in FP32 for every pixel of the tile (lx, ly are
+// half-integers below 16), and the low parts (nu0l, Jl, at most about 2^g)
+// small enough that their FP32 rounding is negligible.  Then
+// Ji d = [nu0h + Jh (lx, ly)] + [nu0l + Jl (lx, ly)] is accurate to the FP32
+// rounding of the result itself, whatever the conditioning of Ji.
 struct Staged {
-  float4 s0, s1, s2, s3;
+  float4 s0, s1, s2, s3, s4, s5;
   uint32_t wmask;
 };
+constexpr uint32_t kPrecise = 1u << 31;
+
+__device__ __forceinline__ float pow2i(int k) { return __int_as_float((k + 127) << 23); }  // |k| <= 126
 
 __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
                                               const RowGeom* __restrict__ geom, uint32_t s,
                                               int tx0, int ty0, int H, float rf) {
   const float4* R = rec + (size_t)s * kRecF4;
-  const float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4];
+  const float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4], r5 = R[5];
   Staged e;
   // centre relative to the tile origin: (c_hi - x0) + c_lo keeps the
   // offset accurate to its own rounding
   e.s0 = make_float4(__fadd_rn(__fsub_rn(r0.x, (float)tx0), r0.z),
                      __fadd_rn(__fsub_rn(r0.y, (float)ty0), r0.w), r2.x, r2.y);
-  e.s1 = r1;
   e.s2 = make_float4(r2.z, r2.w, r3.x, r3.y);
   e.s3 = make_float4(r3.z, r3.w, r4.x, r4.y);
+  const bool precise = r4.z != 0.f;
+  if (!precise) {
+    e.s1 = r1;
+    e.s4 = e.s5 = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    // n0 = Ji (o - c) in double-float
+    const df d0x = two_sum((float)tx0, -r0.x) - r0.z;
+    const df d0y = two_sum((float)ty0, -r0.y) - r0.w;
+    const df nu0 = df_make(r1.x, r5.x) * d0x + df_make(r1.y, r5.y) * d0y;
+    const df nv0 = df_make(r1.z, r5.z) * d0x + df_make(r1.w, r5.w) * d0y;
+    // grid: every partial sum of nu0h + Jh (lx, ly) stays below 2^(g+24)
+    const float M = __fmul_rn(fmaxf(__fmaf_rn(16.f, __fadd_rn(fabsf(r1.x), fabsf(r1.y)), fabsf(nu0.hi)),
+                                    __fmaf_rn(16.f, __fadd_rn(fabsf(r1.z), fabsf(r1.w)), fabsf(nv0.hi))),
+                              1.0009765625f);
+    const int E = min(max(((__float_as_int(M) >> 23) & 0xff) - 127, -100), 100);  // M < 2^(E+1)
+    const int g = E - 21;
+    const float ug = pow2i(-g), dg = pow2i(g), uj = pow2i(-g - 1), dj = pow2i(g + 1);
+    float4 jh;
+    jh.x = __fmul_rn(rintf(__fmul_rn(r1.x, uj)), dj);
+    jh.y = __fmul_rn(rintf(__fmul_rn(r1.y, uj)), dj);
+    jh.z = __fmul_rn(rintf(__fmul_rn(r1.z, uj)), dj);
+    jh.w = __fmul_rn(rintf(__fmul_rn(r1.w, uj)), dj);
+    e.s1 = jh;
+    e.s4 = make_float4(__fadd_rn(__fsub_rn(r1.x, jh.x), r5.x), __fadd_rn(__fsub_rn(r1.y, jh.y), r5.y),
+                       __fadd_rn(__fsub_rn(r1.z, jh.z), r5.z), __fadd_rn(__fsub_rn(r1.w, jh.w), r5.w));
+    const float uh = __fmul_rn(rintf(__fmul_rn(nu0.hi, ug)), dg);
+    const float vh = __fmul_rn(rintf(__fmul_rn(nv0.hi, ug)), dg);
+    e.s5 = make_float4(uh, vh, __fadd_rn(__fsub_rn(nu0.hi, uh), nu0.lo), __fadd_rn(__fsub_rn(nv0.hi, vh), nv0.lo));
+  }
   const RowGeom g = geom[s];
   uint32_t m = 0u;
 #pragma unroll
@@ -82,7 +133,7 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
     if (ilo <= tx0 + 7 && ihi >= tx0) m |= 1u << (2 * b);
     if (ilo <= tx0 + 15 && ihi >= tx0 + 8) m |= 1u << (2 * b + 1);
   }
-  e.wmask = m;
+  e.wmask = m | (precise ? kPrecise : 0u);
   return e;
 }
 
@@ -91,10 +142,11 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
 // below visit only their set bits, so entries that miss the block cost
 // nothing (long lists, where most entries miss a given block).
 constexpr int kWords = kBatch / 32;
+template <int NW = kWords>
 __device__ __forceinline__ void warp_entry_bits(const uint32_t* sm, int nb, int warp, int lane,
                                                 uint32_t* wb) {
 #pragma unroll
-  for (int j = 0; j < kWords; ++j) {
+  for (int j = 0; j < NW; ++j) {
     const int e = 32 * j + lane;
     const uint32_t w = __ballot_sync(0xffffffffu, e < nb && ((sm[e] >> warp) & 1u));
     if (lane == 0) wb[j] = w;
@@ -113,16 +165,16 @@ struct Pair {
   bool hit;        // rho <= rho_max and alpha >= alpha_min
 };
 
-// Shared by both blends; explicit round-to-nearest operations so that the
-// forward and the backward take bit-identical decisions.
-__device__ __forceinline__ Pair eval_pair(float lx, float ly, float4 s0, float4 s1, float opac,
-                                          const SetDev& set) {
-  Pair q;
+// The rest of one pair's evaluation from its plane coordinates (nu, nv) =
+// Ji d.  Shared by every blend; explicit round-to-nearest operations so that
+// the forward and the backward take bit-identical decisions.
+__device__ __forceinline__ void finish_pair(float lx, float ly, float4 s0, float nu, float nv, float opac,
+                                            const SetDev& set, Pair& q) {
   q.dx = __fsub_rn(lx, s0.x);
   q.dy = __fsub_rn(ly, s0.y);
   const float den = __fmaf_rn(s0.z, q.dx, __fmaf_rn(s0.w, q.dy, 1.0f));
-  q.nu = __fmaf_rn(s1.x, q.dx, __fmul_rn(s1.y, q.dy));
-  q.nv = __fmaf_rn(s1.z, q.dx, __fmul_rn(s1.w, q.dy));
+  q.nu = nu;
+  q.nv = nv;
   q.rden = rcp_approx(den);
   const float u = __fmul_rn(q.nu, q.rden), v = __fmul_rn(q.nv, q.rden);
   const float rho_obj = den > 0.f ? __fmaf_rn(u, u, __fmul_rn(v, v)) : INFINITY;
@@ -132,7 +184,40 @@ __device__ __forceinline__ Pair eval_pair(float lx, float ly, float4 s0, float4 
   q.G = ex2_approx(__fmul_rn(kNegHalfLog2e, q.rho));
   q.alpha = fminf(set.alpha_max, __fmul_rn(opac, q.G));
   q.hit = (q.rho <= set.rho_max) && (q.alpha >= set.alpha_min);
-  return q;
+}
+
+// Direct evaluation of one pixel: (nu, nv) = Ji d in FP32.
+__device__ __forceinline__ void eval_direct(float lx, float ly, float4 s0, float4 ji, float opac,
+                                            const SetDev& set, Pair& q) {
+  const float dx = __fsub_rn(lx, s0.x), dy = __fsub_rn(ly, s0.y);
+  finish_pair(lx, ly, s0, __fmaf_rn(ji.x, dx, __fmul_rn(ji.y, dy)), __fmaf_rn(ji.z, dx, __fmul_rn(ji.w, dy)),
+              opac, set, q);
+}
+
+// One entry against a thread's two pixels, (lx, ly) and (lx, ly + 4) from
+// the tile origin: the exact grid sums nu0h + Jh (lx, ly) (row B adds 4 Jh
+// exactly), plus the small low-part corrections (see Staged).
+__device__ __forceinline__ void eval_two(float lx, float ly, float4 s0, float4 jh, float4 jl, float4 n0,
+                                         float opac, const SetDev& set, Pair& qa, Pair& qb) {
+  const float suA = __fmaf_rn(jh.x, lx, __fmaf_rn(jh.y, ly, n0.x));
+  const float svA = __fmaf_rn(jh.z, lx, __fmaf_rn(jh.w, ly, n0.y));
+  const float cuA = __fmaf_rn(jl.x, lx, __fmaf_rn(jl.y, ly, n0.z));
+  const float cvA = __fmaf_rn(jl.z, lx, __fmaf_rn(jl.w, ly, n0.w));
+  const float suB = __fmaf_rn(jh.y, 4.f, suA), svB = __fmaf_rn(jh.w, 4.f, svA);
+  const float cuB = __fmaf_rn(jl.y, 4.f, cuA), cvB = __fmaf_rn(jl.w, 4.f, cvA);
+  finish_pair(lx, ly, s0, __fadd_rn(suA, cuA), __fadd_rn(svA, cvA), opac, set, qa);
+  finish_pair(lx, __fadd_rn(ly, 4.f), s0, __fadd_rn(suB, cuB), __fadd_rn(svB, cvB), opac, set, qb);
+}
+
+// Either evaluation, by the entry's flag (the same for the whole warp).
+__device__ __forceinline__ void eval_entry(uint32_t wm, float lx, float ly, float4 s0, float4 s1, float4 s4,
+                                           float4 s5, float opac, const SetDev& set, Pair& qa, Pair& qb) {
+  if (wm & kPrecise) {
+    eval_two(lx, ly, s0, s1, s4, s5, opac, set, qa, qb);
+  } else {
+    eval_direct(lx, ly, s0, s1, opac, set, qa);
+    eval_direct(lx, __fadd_rn(ly, 4.f), s0, s1, opac, set, qb);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -219,7 +304,7 @@ __device__ __forceinline__ void fwd_store(const FwdPix& p, const CamDev& cam, co
 
 // Shared-memory staging area of one CTA.
 struct FwdSmem {
-  float4 s0[kBatch], s1[kBatch], s2[kBatch], s3[kBatch];
+  float4 s0[kBatch], s1[kBatch], s2[kBatch], s3[kBatch], s4[kBatch], s5[kBatch];
   uint32_t sm[kBatch];
   uint32_t wbits[kThreads / 32][kWords];
   unsigned long long tot[2];
@@ -236,7 +321,7 @@ __device__ __forceinline__ void blend_fwd_tile(
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
   const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
   const int warp = threadIdx.x >> 5;
-  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f;
   const int2 rg = ranges[tile];
   const int len = rg.y - rg.x;
   if (lseg > 0 && len > lseg) return;  // a long list: composited in segments
@@ -254,6 +339,8 @@ __device__ __forceinline__ void blend_fwd_tile(
         sh.s1[t] = e.s1;
         sh.s2[t] = e.s2;
         sh.s3[t] = e.s3;
+        sh.s4[t] = e.s4;
+        sh.s5[t] = e.s5;
         sh.sm[t] = e.wmask;
       }
     }
@@ -266,8 +353,8 @@ __device__ __forceinline__ void blend_fwd_tile(
         const int k = 32 * j + __ffs(bits) - 1;
         bits &= bits - 1u;
         const float4 e0 = sh.s0[k], e1 = sh.s1[k], e2 = sh.s2[k], e3 = sh.s3[k];
-        const Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
-        const Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+        Pair qa, qb;
+        eval_entry(sh.sm[k], lx, lyA, e0, e1, sh.s4[k], sh.s5[k], e2.y, set, qa, qb);
         fwd_step(a, qa, e2, e3, b0 + k, set);
         fwd_step(b, qb, e2, e3, b0 + k, set);
       }
@@ -362,6 +449,8 @@ __device__ __forceinline__ void stage_batch(FwdSmem& sh, const float4* __restric
       sh.s1[t] = e.s1;
       sh.s2[t] = e.s2;
       sh.s3[t] = e.s3;
+      sh.s4[t] = e.s4;
+      sh.s5[t] = e.s5;
       sh.sm[t] = e.wmask;
     }
   }
@@ -378,7 +467,7 @@ __global__ void __launch_bounds__(kThreads) seg_trans_kernel(
   const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
   const int warp = threadIdx.x >> 5;
-  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f;
   const int2 rg = ranges[tile];
   const int e0 = s * lseg, e1 = min(rg.y - rg.x, e0 + lseg);
   float TA = 1.f, TB = 1.f;
@@ -394,8 +483,8 @@ __global__ void __launch_bounds__(kThreads) seg_trans_kernel(
         const int k = 32 * j + __ffs(bits) - 1;
         bits &= bits - 1u;
         const float4 f0 = sh.s0[k], f1 = sh.s1[k], f2 = sh.s2[k];
-        const Pair qa = eval_pair(lx, lyA, f0, f1, f2.y, set);
-        const Pair qb = eval_pair(lx, lyB, f0, f1, f2.y, set);
+        Pair qa, qb;
+        eval_entry(sh.sm[k], lx, lyA, f0, f1, sh.s4[k], sh.s5[k], f2.y, set, qa, qb);
         TA = qa.hit ? TA * (1.f - qa.alpha) : TA;
         TB = qb.hit ? TB * (1.f - qb.alpha) : TB;
       }
@@ -426,7 +515,7 @@ __global__ void __launch_bounds__(kThreads) seg_blend_kernel(
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
   const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
   const int warp = threadIdx.x >> 5;
-  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f;
   const int2 rg = ranges[tile];
   const int e0 = s * lseg, e1 = min(rg.y - rg.x, e0 + lseg);
   const bool inA = px < cam.W && pyA < cam.H, inB = px < cam.W && pyB < cam.H;
@@ -454,8 +543,8 @@ __global__ void __launch_bounds__(kThreads) seg_blend_kernel(
         const int k = 32 * j + __ffs(bits) - 1;
         bits &= bits - 1u;
         const float4 f0 = sh.s0[k], f1 = sh.s1[k], f2 = sh.s2[k], f3 = sh.s3[k];
-        const Pair qa = eval_pair(lx, lyA, f0, f1, f2.y, set);
-        const Pair qb = eval_pair(lx, lyB, f0, f1, f2.y, set);
+        Pair qa, qb;
+        eval_entry(sh.sm[k], lx, lyA, f0, f1, sh.s4[k], sh.s5[k], f2.y, set, qa, qb);
         fwd_step<true>(a, qa, f2, f3, b0 + k, set);
         fwd_step<true>(b, qb, f2, f3, b0 + k, set);
       }
@@ -567,7 +656,7 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_batched_kernel(BlendBatch 
     const BlendJob& jb = batch.job[j];
     const int local = t - jb.tile_begin;
     blend_fwd_tile(sh, jb.cam, jb.set, jb.rf, jb.rec, jb.geom, jb.vals, jb.ranges, jb.out, jb.n_contrib,
-                   nullptr, nullptr, nullptr, local % jb.cam.tiles_x, local / jb.cam.tiles_x);
+                   nullptr, nullptr, batch.work, local % jb.cam.tiles_x, local / jb.cam.tiles_x);
   }
 }
 
@@ -575,6 +664,10 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_batched_kernel(BlendBatch 
 // Backward.
 
 constexpr int kMaxSets = 3;
+// Entries staged per batch in the backward: its gradient accumulators and
+// the six staged vectors per entry must fit five CTAs per SM.
+constexpr int kBatchB = 224;
+constexpr int kWordsB = kBatchB / 32;
 // Average tile-list length from which the backward takes the 4-CTA variant:
 // 200 (the 1M-surfel aerial view) ran best with 5 CTAs per SM, 590 (the
 // 4M-surfel orbit view) with 4.
@@ -787,18 +880,19 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
     unsigned long long* __restrict__ counters) {
   using LY = Layout<kLoss>;
   constexpr int kN = LY::kN;
-  __shared__ float4 s0[kBatch], s1[kBatch], s2[kBatch], s3[kBatch];
-  __shared__ uint32_t sm[kBatch];
-  __shared__ uint32_t sid[kBatch];
-  __shared__ float acc[kBatch][kN + 1];
-  __shared__ uint32_t wbits[kThreads / 32][kWords];
+  constexpr int kAcc = kN | 1;  // odd row stride: the flush's column reads are conflict-free
+  __shared__ float4 s0[kBatchB], s1[kBatchB], s2[kBatchB], s3[kBatchB], s4[kBatchB], s5[kBatchB];
+  __shared__ uint32_t sm[kBatchB];
+  __shared__ uint32_t sid[kBatchB];
+  __shared__ float acc[kBatchB][kAcc];
+  __shared__ uint32_t wbits[kThreads / 32][kWordsB];
   __shared__ int smax;
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
   const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
   const int warp = threadIdx.x >> 5;
-  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f;
   const int2 rg = ranges[tile];
   const size_t HW = (size_t)cam.W * cam.H;
   const int lane = threadIdx.x & 31;
@@ -815,39 +909,37 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
   const int maxlast = smax;
   unsigned replayed = 0, wentries = 0, wlanes = 0;
 
-  for (int bend = maxlast; bend > 0; bend -= kBatch) {
-    const int b0 = bend > kBatch ? bend - kBatch : 0;
+  for (int bend = maxlast; bend > 0; bend -= kBatchB) {
+    const int b0 = bend > kBatchB ? bend - kBatchB : 0;
     const int nb = bend - b0;
     __syncthreads();
-#pragma unroll
-    for (int h = 0; h < kBatch / kThreads; ++h) {
-      const int t = threadIdx.x + h * kThreads;
-      if (t < nb) {
-        const uint32_t s = vals[rg.x + b0 + t];
-        sid[t] = s;
-        const Staged e = stage_entry(rec, geom, s, tx0, ty0, cam.H, rf);
-        s0[t] = e.s0;
-        s1[t] = e.s1;
-        s2[t] = e.s2;
-        s3[t] = e.s3;
-        sm[t] = e.wmask;
-      }
+    for (int t = threadIdx.x; t < nb; t += kThreads) {
+      const uint32_t s = vals[rg.x + b0 + t];
+      sid[t] = s;
+      const Staged e = stage_entry(rec, geom, s, tx0, ty0, cam.H, rf);
+      s0[t] = e.s0;
+      s1[t] = e.s1;
+      s2[t] = e.s2;
+      s3[t] = e.s3;
+      s4[t] = e.s4;
+      s5[t] = e.s5;
+      sm[t] = e.wmask;
     }
-    for (int i = threadIdx.x; i < nb * (kN + 1); i += kThreads) (&acc[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < nb * kAcc; i += kThreads) (&acc[0][0])[i] = 0.f;
     __syncthreads();
-    warp_entry_bits(sm, nb, warp, lane, wbits[warp]);
-    for (int j = kWords - 1; j >= 0; --j) {
+    warp_entry_bits<kWordsB>(sm, nb, warp, lane, wbits[warp]);
+    for (int j = kWordsB - 1; j >= 0; --j) {
       uint32_t bits = wbits[warp][j];
       while (bits != 0u) {  // back to front: highest set bit first
         const int hb = 31 - __clz(bits);
         bits &= ~(1u << hb);
         const int kk = 32 * j + hb;
         const int k = b0 + kk;
-        const float4 e0 = s0[kk], e1 = s1[kk], e2 = s2[kk];
+        const float4 e0 = s0[kk], jh = s1[kk], jl = s4[kk], e2 = s2[kk];
         const bool liveA = k < a.last, liveB = k < b.last;
         replayed += (unsigned)liveA + (unsigned)liveB;
-        Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
-        Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+        Pair qa, qb;
+        eval_entry(sm[kk], lx, lyA, e0, jh, jl, s5[kk], e2.y, set, qa, qb);
         mask_pair(qa, liveA);
         mask_pair(qb, liveB);
         const bool contrib = qa.hit || qb.hit;
@@ -859,6 +951,8 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
   #pragma unroll
         for (int i = 0; i < kN; ++i) v[i] = 0.f;
         const float4 e3 = s3[kk];
+        // Ji = Jh + Jl (FP32; Jl = 0 for direct entries) for the chain rule
+        const float4 e1 = make_float4(jh.x + jl.x, jh.y + jl.y, jh.z + jl.z, jh.w + jl.w);
         // a pixel row with no hit in the whole warp needs no gradient pass (a
         // masked pair leaves the pixel's state and the sums unchanged)
         const bool anyA = __any_sync(0xffffffffu, qa.hit), anyB = __any_sync(0xffffffffu, qb.hit);
@@ -946,7 +1040,7 @@ __global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
     CamDev cam, SetDev set, float rf, float gamma, const uint32_t* __restrict__ order,
     const float4* __restrict__ rec, const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals,
     const int2* __restrict__ ranges, float* __restrict__ csum, uint32_t* __restrict__ ccnt) {
-  __shared__ float4 s0[kBatch], s1[kBatch], s2[kBatch];
+  __shared__ float4 s0[kBatch], s1[kBatch], s2[kBatch], s4[kBatch], s5[kBatch];
   __shared__ uint32_t sm[kBatch], sid[kBatch];
   __shared__ float asum[kBatch];
   __shared__ uint32_t acnt[kBatch];
@@ -956,7 +1050,7 @@ __global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
   const int px = tx0 + lxi, pyA = ty0 + lyi, pyB = pyA + 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f, lyB = lyA + 4.f;
+  const float lx = (float)lxi + 0.5f, lyA = (float)lyi + 0.5f;
   const bool inA = px < cam.W && pyA < cam.H, inB = px < cam.W && pyB < cam.H;
   const int2 rg = ranges[tile];
   const int len = rg.y - rg.x;
@@ -974,6 +1068,8 @@ __global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
         s0[t] = e.s0;
         s1[t] = e.s1;
         s2[t] = e.s2;
+        s4[t] = e.s4;
+        s5[t] = e.s5;
         sm[t] = e.wmask;
         sid[t] = sidx;
         asum[t] = 0.f;
@@ -988,8 +1084,8 @@ __global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
         const int k = 32 * j + __ffs(bits) - 1;
         bits &= bits - 1u;
         const float4 e0 = s0[k], e1 = s1[k], e2 = s2[k];
-        const Pair qa = eval_pair(lx, lyA, e0, e1, e2.y, set);
-        const Pair qb = eval_pair(lx, lyB, e0, e1, e2.y, set);
+        Pair qa, qb;
+        eval_entry(sm[k], lx, lyA, e0, e1, s4[k], s5[k], e2.y, set, qa, qb);
         const unsigned ba = __ballot_sync(0xffffffffu, inA && qa.rho <= set.rho_max);
         const unsigned bb = __ballot_sync(0xffffffffu, inB && qb.rho <= set.rho_max);
         const uint32_t cnt = (uint32_t)(__popc(ba) + __popc(bb));

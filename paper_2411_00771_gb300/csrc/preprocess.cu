@@ -211,7 +211,8 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
                                                               uint32_t* __restrict__ tcount,
                                                               uint32_t* __restrict__ dkey,
                                                               uint32_t* __restrict__ idx,
-                                                              RowGeom* __restrict__ geom) {
+                                                              RowGeom* __restrict__ geom,
+                                                              uint32_t* __restrict__ tile_cnt) {
   const uint32_t total = *ncand;
   const df rf = df_sqrt(df_make(set.rho_max) / df_make(set.sinv));
   const float rff = df_float(rf);
@@ -296,7 +297,11 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     uint32_t cnt = 0;
     for (int ty = ty0; ty < ty1; ++ty) {
       int a0, a1;
-      if (row_tiles(gm, ty, rff, &a0, &a1)) cnt += (uint32_t)(a1 - a0);
+      if (row_tiles(gm, ty, rff, &a0, &a1)) {
+        cnt += (uint32_t)(a1 - a0);
+        if (tile_cnt)
+          for (int tx = a0; tx < a1; ++tx) atomicAdd(&tile_cnt[ty * cam.tiles_x + tx], 1u);
+      }
     }
     if (cnt == 0) continue;
     geom[n] = gm;
@@ -304,18 +309,23 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     const float pz = df_float(p.z);
     dkey[ci] = __float_as_uint(pz);
     const df det = J11 * J22 - J12 * J21;
-    float4 r1f;
+    float4 r1f, r5f;
     float2 ef;
     if (df_nonzero(det)) {
       const df id = df_rcp(det);
       const df i11 = J22 * id, i12 = -(J12 * id), i21 = -(J21 * id), i22 = J11 * id;
       r1f = make_float4(df_float(i11), df_float(i12), df_float(i21), df_float(i22));
+      // what FP32 leaves of Ji: the blends evaluate (u, v) relative to each
+      // tile from the double-float Ji (see blend.cu)
+      r5f = make_float4(df_float(i11 - r1f.x), df_float(i12 - r1f.y), df_float(i21 - r1f.z),
+                        df_float(i22 - r1f.w));
       ef = make_float2(df_float(-(i11 * w1 + i21 * w2)), df_float(-(i12 * w1 + i22 * w2)));
     } else {
       // edge-on disk: no object-space footprint (rho_obj is NaN, the
       // screen filter decides)
       const float qnan = __int_as_float(0x7fffffff);
       r1f = make_float4(qnan, qnan, qnan, qnan);
+      r5f = make_float4(0.f, 0.f, 0.f, 0.f);
       ef = make_float2(0.f, 0.f);
     }
     // colour: SH at the world direction from the camera centre
@@ -350,7 +360,19 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     Rr[1] = r1f;
     Rr[2] = make_float4(ef.x, ef.y, pz, load_opacity(P, n));
     Rr[3] = make_float4(col[0], col[1], col[2], sg * df_float(nv.x));
-    Rr[4] = make_float4(sg * df_float(nv.y), sg * df_float(nv.z), 0.f, 0.f);
+    // How far FP32 can evaluate (u, v) = Ji d directly from the centre: its
+    // error in u is about 3 2^-24 R D (R the larger row sum of |Ji|, D the
+    // half-extent of the ellipse {rho_obj <= rho_max} in pixels), so alpha =
+    // o exp(-(u^2 + v^2) / 2) carries a relative error up to 9 2^-24 R D at
+    // the support boundary.  Above R D = 12 (about 6.4e-6, a condition number
+    // of the centred Jacobian of roughly 3 and up: nearly edge-on or
+    // elongated disks) the blends evaluate the pair relative to the tile
+    // origin in the exact split form instead (see blend.cu).
+    const float Rs = fmaxf(fabsf(r1f.x) + fabsf(r1f.y), fabsf(r1f.z) + fabsf(r1f.w));
+    const float Ds = fmaxf(fmaxf(fabsf(df_float(x0)), fabsf(df_float(x1))), fmaxf(fabsf(df_float(y0)), fabsf(df_float(y1))));
+    const bool precise = isfinite(Rs) && !(Rs * Ds <= 12.f);
+    Rr[4] = make_float4(sg * df_float(nv.y), sg * df_float(nv.z), precise ? 1.f : 0.f, 0.f);
+    Rr[5] = r5f;
   }
 }
 
@@ -551,7 +573,7 @@ void launch_bwd_deg(const ParamsDev& P, const CamDev& cam, const uint32_t* cand,
 cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
                               float4* rec, uint2* rect, uint32_t* tcount, uint32_t* dkey,
                               uint32_t* idx, uint32_t* cand, uint32_t* ncand, RowGeom* geom,
-                              uint32_t* flags, uint32_t* scan_tmp, cudaStream_t st) {
+                              uint32_t* flags, uint32_t* scan_tmp, cudaStream_t st, uint32_t* tile_cnt) {
   if (P.n == 0) return cudaMemsetAsync(ncand, 0, sizeof(uint32_t), st);
   ProfScope ps(kProfPreprocess, st);
   preprocess_cull_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, set, rect, tcount, flags);
@@ -571,10 +593,10 @@ cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDe
   }();
   const unsigned blocks = div_up(P.n, 256) < resident ? div_up(P.n, 256) : resident;
   switch (P.sh_degree) {
-    case 0: preprocess_main_kernel<0><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
-    case 1: preprocess_main_kernel<1><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
-    case 2: preprocess_main_kernel<2><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
-    default: preprocess_main_kernel<3><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
+    case 0: preprocess_main_kernel<0><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom, tile_cnt); break;
+    case 1: preprocess_main_kernel<1><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom, tile_cnt); break;
+    case 2: preprocess_main_kernel<2><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom, tile_cnt); break;
+    default: preprocess_main_kernel<3><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom, tile_cnt); break;
   }
   count_launch(2);
   return cudaGetLastError();

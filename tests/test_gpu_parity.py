@@ -222,7 +222,7 @@ def test_training_loss_gradients_and_densify_stats():
     L = oracle.loss(r["out"], tgt, tinv, w)
     assert abs(float(losses[3]) - L["total"]) < 1e-4
     ref = oracle.backward(scene, cam, L["adj"])
-    _assert_grads(grads, screen, ref, tol=2e-3)
+    _assert_grads(grads, screen, ref)
     pre = oracle.preprocess(scene, cam)
     st = oracle.densify_accumulate(ref["screen"], gu.visible(pre))
     assert gu.rel_err(stats.cpu().numpy(), st) <= 1e-3
@@ -254,8 +254,13 @@ def test_densify_select_threshold_decisions():
 
 
 def test_gradients_against_finite_differences_on_64_surfels():
-    """The GPU gradient against central finite differences of the FP64
-    oracle's loss, on a 64-surfel subset (parameters away from kinks)."""
+    """The GPU gradient of every parameter kind (mu, the raw quaternion through
+    its normalisation and rotation, scale, opacity, SH) against central finite
+    differences of the FP64 oracle's loss, on 64 surfels, at 1e-3 relative.
+    A point is used only where the loss is smooth across the step: the
+    central differences at h and h/2 must agree (a pair crossing the alpha
+    cutoff, the support boundary, the transmittance stop or the object/screen
+    switch inside the step makes them disagree)."""
     scene, cam, tgt, tinv = syn.tiny_scene(seed=77, n=300, width=48, height=48, fx=48.0,
                                            sh_degree=1, log_scale_range=(-3.0, -1.5))
     from paper_2411_00771_gb300 import binding as B
@@ -265,27 +270,37 @@ def test_gradients_against_finite_differences_on_64_surfels():
     grads = {k: torch.zeros_like(v) for k, v in d.items()}
     sc.backward(frame, [adj_t], [0x7 | (1 << 5)], grads)
     torch.cuda.synchronize()
+    g = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
     s64 = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in scene.items()}
     f = lambda s: oracle.loss(oracle.render(s, cam)["out"], tgt, tinv, w)["total"]
     rng = np.random.default_rng(0)
     pre = oracle.preprocess(scene, cam)
     subset = rng.choice(np.nonzero(pre["tiles"] > 0)[0], 64, replace=False)
-    checked = 0
+    K = (scene["sh_degree"] + 1) ** 2
+    checked, skipped = 0, 0
     for i in subset:
-        for key, comp in (("mu", rng.integers(3)), ("opacity", None), ("scale", rng.integers(2))):
+        for key, comp in (("mu", (rng.integers(3),)), ("quat", (rng.integers(4),)),
+                          ("scale", (rng.integers(2),)), ("opacity", ()),
+                          ("sh", (rng.integers(K), rng.integers(3)))):
             a = s64[key]
-            idx = (i,) if comp is None else (i, comp)
-            h = 1e-6 * max(1.0, abs(a[idx]))
-            a[idx] += h
-            lp = f(s64)
-            a[idx] -= 2 * h
-            lm = f(s64)
-            a[idx] += h
-            fd = (lp - lm) / (2 * h)
-            gv = float(grads[key][idx].cpu())
-            assert abs(gv - fd) <= 1e-3 * max(abs(fd), 1e-4), (key, idx, gv, fd)
+            idx = (i,) + tuple(int(c) for c in comp)
+            x0 = a[idx]
+            h = 1e-6 * max(1.0, abs(x0))
+            fd = {}
+            for hh in (h, h / 2):
+                a[idx] = x0 + hh
+                lp = f(s64)
+                a[idx] = x0 - hh
+                lm = f(s64)
+                fd[hh] = (lp - lm) / (2 * hh)
+            a[idx] = x0
+            if abs(fd[h] - fd[h / 2]) > 1e-5 * max(abs(fd[h]), 1e-4):
+                skipped += 1
+                continue
+            gv = g[key][idx]
+            assert abs(gv - fd[h]) <= 1e-3 * max(abs(fd[h]), 1e-4), (key, idx, gv, fd[h])
             checked += 1
-    assert checked == 192
+    assert checked + skipped == 320 and checked >= 300, (checked, skipped)
 
 
 def _dense_small_view():
@@ -310,4 +325,4 @@ def test_long_lists_backward_after_segmented_forward():
     rng = np.random.default_rng(9)
     adj = rng.normal(size=(1, 11, 64, 64))
     grads, screen, ref, _ = _backward_case(scene, cam, adj, [0x7FF])
-    _assert_grads(grads, screen, ref, tol=2e-3)
+    _assert_grads(grads, screen, ref)

@@ -38,6 +38,9 @@ def test_strip_4k_forward_on_sampled_pixels(strip):
     assert info["n_visible"] > 1_000_000 and info["n_instances"] > info["n_visible"]
     ref = gu.compare_sampled(scene, cam, out.cpu().numpy(), cnt.cpu().numpy(), 20_000, seed=1)
     assert (ref["count"] > 0).mean() > 0.5  # the samples land on the city, not on the sky
+    # the oblique 4K view holds many nearly edge-on disks: the plain
+    # tolerance above holds at ill-conditioned pairs too
+    assert np.percentile(ref["cond"], 99) > 100, np.percentile(ref["cond"], 99)
 
 
 def test_strip_4k_backward_through_a_window(strip):

@@ -30,7 +30,7 @@ def test_geometry_loss_matches_oracle():
     a = adj.cpu().numpy()
     for p in (3, 6, 7, 8, 9):
         scale = np.abs(radj[p]).max()
-        assert np.abs(a[p] - radj[p]).max() <= 2e-3 * scale + 1e-12, p
+        assert np.abs(a[p] - radj[p]).max() <= 1e-3 * scale + 1e-12, p
     assert np.all(a[10] == np.float32(0.3 / (56 * 72)))
 
 
@@ -163,31 +163,39 @@ def test_training_loss_gradient_against_finite_differences(autograd):
     rng = np.random.default_rng(0)
     pre = oracle.preprocess(scene, cam)
     subset = rng.choice(np.nonzero(pre["tiles"] > 0)[0], 64, replace=False)
-    bad = 0
+    K = (scene["sh_degree"] + 1) ** 2
+
+    def perturbed(key, idx, dx):
+        s = dict(s64)
+        if key in ("scale", "opacity"):  # the trained (raw) parametrisation
+            r = raw[key].copy()
+            r[idx] += dx
+            s[key] = np.exp(r) if key == "scale" else 1 / (1 + np.exp(-r))
+        else:
+            s[key] = s64[key].copy()
+            s[key][idx] += dx
+        return s
+
+    # A point is used only where the loss is smooth across the step: the
+    # central differences at h and h/2 agree.  The normal-consistency term
+    # follows the median depth, whose pair changes by a jump when a
+    # transmittance crosses 1/2; a step across such a switch (or across the
+    # alpha cutoff, the support boundary, the stop) breaks the agreement.
+    checked, skipped = 0, 0
     for i in subset:
-        for key, comp in (("mu", rng.integers(3)), ("opacity", None), ("scale", rng.integers(2))):
-            idx = (i,) if comp is None else (i, comp)
+        for key, comp in (("mu", (rng.integers(3),)), ("quat", (rng.integers(4),)),
+                          ("scale", (rng.integers(2),)), ("opacity", ()),
+                          ("sh", (rng.integers(K), rng.integers(3)))):
+            idx = (i,) + tuple(int(c) for c in comp)
             h = 1e-6
-            vals = []
-            for sgn in (1, -1):
-                s = dict(s64)
-                if key == "mu":
-                    s["mu"] = s64["mu"].copy()
-                    s["mu"][idx] += sgn * h
-                elif key == "scale":
-                    r = raw["scale"].copy()
-                    r[idx] += sgn * h
-                    s["scale"] = np.exp(r)
-                else:
-                    r = raw["opacity"].copy()
-                    r[idx] += sgn * h
-                    s["opacity"] = 1 / (1 + np.exp(-r))
-                vals.append(f(s))
-            fd = (vals[0] - vals[1]) / (2 * h)
+            fd = {hh: (f(perturbed(key, idx, hh)) - f(perturbed(key, idx, -hh))) / (2 * hh) for hh in (h, h / 2)}
+            if abs(fd[h] - fd[h / 2]) > 1e-5 * max(abs(fd[h]), 1e-4):
+                skipped += 1
+                continue
             gv = grads[key][idx]
-            if abs(gv - fd) > 2e-3 * max(abs(fd), 1e-4):
-                bad += 1
-    assert bad <= 2, bad  # median-depth selections may switch within the FD step
+            assert abs(gv - fd[h]) <= 1e-3 * max(abs(fd[h]), 1e-4), (key, idx, gv, fd[h])
+            checked += 1
+    assert checked + skipped == 320 and checked >= 290, (checked, skipped)
 
 
 def test_trainer_reduces_the_loss_and_densifies():
