@@ -293,63 +293,35 @@ gs_status build_lists(gs_scene* sc, gs_frame* f, const char* who, cudaStream_t s
     if (e != cudaSuccess) return failed(cuda_fail(e, #expr)); \
   } while (0)
   GS_CKC(cudaMemsetAsync(f->counters, 0, 8 * sizeof(unsigned long long), st));
-  // Lists by tile buckets (count, scan, scatter, per-tile sort) when the
-  // image's tiles fit the one-block scan and no list is longer than a CTA
-  // sorts; otherwise by the two-level radix sort.  Both give the same lists.
-  const bool bucket = tile_order_supported(ntiles);
-  uint32_t* tile_cnt = bucket ? tmp.get<uint32_t>(3 * (size_t)ntiles + 2, st) : nullptr;
-  if (bucket && !tile_cnt) return failed(fail(GS_ERR_OOM, std::string(who) + ": device allocation failed"));
-  uint32_t* tile_start = bucket ? tile_cnt + ntiles : nullptr;
-  uint32_t* cursor = bucket ? tile_cnt + 2 * ntiles : nullptr;
-  uint32_t* out2 = bucket ? tile_cnt + 3 * ntiles : nullptr;
-  if (bucket) GS_CKC(cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)ntiles, st));
-  // candidates (possibly visible surfels) in index order
+  // candidates (possibly visible surfels) in index order; only they are sorted
   uint32_t* ncand = reinterpret_cast<uint32_t*>(f->counters + 6);
   f->ncand = ncand;
   GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, f->cand, ncand, f->geom,
-                           cnts, rtmp + radix_tmp_words(n), st, tile_cnt));
+                           cnts, rtmp + radix_tmp_words(n), st));
+  uint32_t *skey = dkey, *sidx = idx;
+  GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st, ncand));
+  GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st, ncand));
+  GS_CKC(launch_scan(cnts, offs, n, total, rtmp + radix_tmp_words(n), st, ncand));
+  uint32_t Kh = 0;
+  GS_CKC(cudaMemcpyAsync(&Kh, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  GS_CKC(cudaStreamSynchronize(st));
+  const int64_t K = Kh;
+  if (K >= (int64_t(1) << 31)) return failed(fail(GS_ERR_CAPACITY, std::string(who) + ": more than 2^31 tile instances"));
+  f->K = K;
+  uint32_t* keys = tmp.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* vals = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* keys2 = tmp.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* vals2 = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
+  uint32_t* ktmp = tmp.get<uint32_t>(radix_tmp_words(K), st);
+  if (!keys || !vals || !keys2 || !vals2 || !ktmp)
+    return failed(fail(GS_ERR_OOM, std::string(who) + ": device allocation failed (tile lists)"));
   const float rf = (float)sqrt((double)sc->settings.rho_max / (double)sc->settings.screen_inv_sigma2);
-  uint32_t h2[2] = {0u, 0u};
-  if (bucket) {
-    GS_CKC(launch_tile_scan(tile_cnt, ntiles, tile_start, out2, st));
-    GS_CKC(cudaMemcpyAsync(h2, out2, sizeof h2, cudaMemcpyDeviceToHost, st));
-    GS_CKC(cudaStreamSynchronize(st));
-  }
-  if (bucket && (int64_t)h2[1] <= (int64_t)kBucketMaxLen) {
-    const int64_t K = h2[0];
-    f->K = K;
-    unsigned long long* keys64 = tmp.get<unsigned long long>(K > 0 ? K : 1, st);
-    uint32_t* vals = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
-    if (!keys64 || !vals) return failed(fail(GS_ERR_OOM, std::string(who) + ": device allocation failed (tile lists)"));
-    GS_CKC(launch_bucket_lists(f->cand, dkey, f->tcount, f->rect, f->geom, rf, n, ncand, cam.tiles_x, ntiles, tile_cnt,
-                               tile_start, cursor, keys64, (int)h2[1], vals, f->ranges, st));
-    f->vals = vals;
-  } else {
-    // only the candidates are sorted, by depth (stable: ties keep index order)
-    uint32_t *skey = dkey, *sidx = idx;
-    GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st, ncand));
-    GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st, ncand));
-    GS_CKC(launch_scan(cnts, offs, n, total, rtmp + radix_tmp_words(n), st, ncand));
-    uint32_t Kh = 0;
-    GS_CKC(cudaMemcpyAsync(&Kh, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    GS_CKC(cudaStreamSynchronize(st));
-    const int64_t K = Kh;
-    if (K >= (int64_t(1) << 31)) return failed(fail(GS_ERR_CAPACITY, std::string(who) + ": more than 2^31 tile instances"));
-    f->K = K;
-    uint32_t* keys = tmp.get<uint32_t>(K > 0 ? K : 1, st);
-    uint32_t* vals = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
-    uint32_t* keys2 = tmp.get<uint32_t>(K > 0 ? K : 1, st);
-    uint32_t* vals2 = f->buf.get<uint32_t>(K > 0 ? K : 1, st);
-    uint32_t* ktmp = tmp.get<uint32_t>(radix_tmp_words(K), st);
-    if (!keys || !vals || !keys2 || !vals2 || !ktmp)
-      return failed(fail(GS_ERR_OOM, std::string(who) + ": device allocation failed (tile lists)"));
-    GS_CKC(launch_emit(sidx, offs, cnts, f->rect, f->geom, rf, n, cam.tiles_x, keys, vals, st, ncand));
-    uint32_t *tk = keys, *tv = vals;
-    GS_CKC(radix_sort_pairs(keys, vals, keys2, vals2, K, bits_for(ntiles), ktmp, &tk, &tv, st));
-    f->vals = tv;
-    f->buf.release(tv == vals ? vals2 : vals, st);
-    GS_CKC(launch_ranges(tk, K, f->ranges, ntiles, st));
-  }
+  GS_CKC(launch_emit(sidx, offs, cnts, f->rect, f->geom, rf, n, cam.tiles_x, keys, vals, st, ncand));
+  uint32_t *tk = keys, *tv = vals;
+  GS_CKC(radix_sort_pairs(keys, vals, keys2, vals2, K, bits_for(ntiles), ktmp, &tk, &tv, st));
+  f->vals = tv;
+  f->buf.release(tv == vals ? vals2 : vals, st);
+  GS_CKC(launch_ranges(tk, K, f->ranges, ntiles, st));
   if (tile_order_supported(ntiles)) GS_CKC(launch_tile_order(f->ranges, ntiles, f->order, st));
   else f->order = nullptr;  // natural tile order (the buffer stays owned by f->buf)
 #undef GS_CKC

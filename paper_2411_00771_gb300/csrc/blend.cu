@@ -52,12 +52,9 @@ __device__ __forceinline__ int local_x(int t) { return (((t >> 5) & 1) << 3) | (
 __device__ __forceinline__ int local_y(int t) { return ((t >> 6) << 3) | ((t >> 3) & 3); }
 
 // Staged entry: s0 = (c.x, c.y relative to the tile origin, e.x, e.y),
-// s2 = (p_z, opacity, r, g), s3 = (b, n.x, n.y, n.z); wmask bit w set when
-// the footprint may reach warp w's pixel block, kPrecise set for the split
-// evaluation below.  Direct evaluation: s1 = Ji, s4 = s5 = 0, and
-// (u, v) den = Ji d with d = x - c in FP32, whose error is small for a
-// well-conditioned footprint (the preprocess decides; see its record).
-// Split evaluation: s1 = Jh, s4 = Jl, s5 = (nu0h, nv0h, nu0l, nv0l).
+// s1 = Jh, s2 = (p_z, opacity, r, g), s3 = (b, n.x, n.y, n.z), s4 = Jl,
+// s5 = (nu0h, nv0h, nu0l, nv0l); wmask bit w set when the footprint may
+// reach warp w's pixel block.
 //
 // Tile-relative ray-splat coordinates.  For a pixel at offset (lx, ly) from
 // the tile origin o, Ji d = Ji (o - c) + Ji (lx, ly) = n0 + Ji (lx, ly).  Held
@@ -77,7 +74,6 @@ struct Staged {
   float4 s0, s1, s2, s3, s4, s5;
   uint32_t wmask;
 };
-constexpr uint32_t kPrecise = 1u << 31;
 
 __device__ __forceinline__ float pow2i(int k) { return __int_as_float((k + 127) << 23); }  // |k| <= 126
 
@@ -93,11 +89,7 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
                      __fadd_rn(__fsub_rn(r0.y, (float)ty0), r0.w), r2.x, r2.y);
   e.s2 = make_float4(r2.z, r2.w, r3.x, r3.y);
   e.s3 = make_float4(r3.z, r3.w, r4.x, r4.y);
-  const bool precise = r4.z != 0.f;
-  if (!precise) {
-    e.s1 = r1;
-    e.s4 = e.s5 = make_float4(0.f, 0.f, 0.f, 0.f);
-  } else {
+  {
     // n0 = Ji (o - c) in double-float
     const df d0x = two_sum((float)tx0, -r0.x) - r0.z;
     const df d0y = two_sum((float)ty0, -r0.y) - r0.w;
@@ -133,7 +125,7 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
     if (ilo <= tx0 + 7 && ihi >= tx0) m |= 1u << (2 * b);
     if (ilo <= tx0 + 15 && ihi >= tx0 + 8) m |= 1u << (2 * b + 1);
   }
-  e.wmask = m | (precise ? kPrecise : 0u);
+  e.wmask = m;
   return e;
 }
 
@@ -186,14 +178,6 @@ __device__ __forceinline__ void finish_pair(float lx, float ly, float4 s0, float
   q.hit = (q.rho <= set.rho_max) && (q.alpha >= set.alpha_min);
 }
 
-// Direct evaluation of one pixel: (nu, nv) = Ji d in FP32.
-__device__ __forceinline__ void eval_direct(float lx, float ly, float4 s0, float4 ji, float opac,
-                                            const SetDev& set, Pair& q) {
-  const float dx = __fsub_rn(lx, s0.x), dy = __fsub_rn(ly, s0.y);
-  finish_pair(lx, ly, s0, __fmaf_rn(ji.x, dx, __fmul_rn(ji.y, dy)), __fmaf_rn(ji.z, dx, __fmul_rn(ji.w, dy)),
-              opac, set, q);
-}
-
 // One entry against a thread's two pixels, (lx, ly) and (lx, ly + 4) from
 // the tile origin: the exact grid sums nu0h + Jh (lx, ly) (row B adds 4 Jh
 // exactly), plus the small low-part corrections (see Staged).
@@ -207,17 +191,6 @@ __device__ __forceinline__ void eval_two(float lx, float ly, float4 s0, float4 j
   const float cuB = __fmaf_rn(jl.y, 4.f, cuA), cvB = __fmaf_rn(jl.w, 4.f, cvA);
   finish_pair(lx, ly, s0, __fadd_rn(suA, cuA), __fadd_rn(svA, cvA), opac, set, qa);
   finish_pair(lx, __fadd_rn(ly, 4.f), s0, __fadd_rn(suB, cuB), __fadd_rn(svB, cvB), opac, set, qb);
-}
-
-// Either evaluation, by the entry's flag (the same for the whole warp).
-__device__ __forceinline__ void eval_entry(uint32_t wm, float lx, float ly, float4 s0, float4 s1, float4 s4,
-                                           float4 s5, float opac, const SetDev& set, Pair& qa, Pair& qb) {
-  if (wm & kPrecise) {
-    eval_two(lx, ly, s0, s1, s4, s5, opac, set, qa, qb);
-  } else {
-    eval_direct(lx, ly, s0, s1, opac, set, qa);
-    eval_direct(lx, __fadd_rn(ly, 4.f), s0, s1, opac, set, qb);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -354,7 +327,7 @@ __device__ __forceinline__ void blend_fwd_tile(
         bits &= bits - 1u;
         const float4 e0 = sh.s0[k], e1 = sh.s1[k], e2 = sh.s2[k], e3 = sh.s3[k];
         Pair qa, qb;
-        eval_entry(sh.sm[k], lx, lyA, e0, e1, sh.s4[k], sh.s5[k], e2.y, set, qa, qb);
+        eval_two(lx, lyA, e0, e1, sh.s4[k], sh.s5[k], e2.y, set, qa, qb);
         fwd_step(a, qa, e2, e3, b0 + k, set);
         fwd_step(b, qb, e2, e3, b0 + k, set);
       }
@@ -484,7 +457,7 @@ __global__ void __launch_bounds__(kThreads) seg_trans_kernel(
         bits &= bits - 1u;
         const float4 f0 = sh.s0[k], f1 = sh.s1[k], f2 = sh.s2[k];
         Pair qa, qb;
-        eval_entry(sh.sm[k], lx, lyA, f0, f1, sh.s4[k], sh.s5[k], f2.y, set, qa, qb);
+        eval_two(lx, lyA, f0, f1, sh.s4[k], sh.s5[k], f2.y, set, qa, qb);
         TA = qa.hit ? TA * (1.f - qa.alpha) : TA;
         TB = qb.hit ? TB * (1.f - qb.alpha) : TB;
       }
@@ -544,7 +517,7 @@ __global__ void __launch_bounds__(kThreads) seg_blend_kernel(
         bits &= bits - 1u;
         const float4 f0 = sh.s0[k], f1 = sh.s1[k], f2 = sh.s2[k], f3 = sh.s3[k];
         Pair qa, qb;
-        eval_entry(sh.sm[k], lx, lyA, f0, f1, sh.s4[k], sh.s5[k], f2.y, set, qa, qb);
+        eval_two(lx, lyA, f0, f1, sh.s4[k], sh.s5[k], f2.y, set, qa, qb);
         fwd_step<true>(a, qa, f2, f3, b0 + k, set);
         fwd_step<true>(b, qb, f2, f3, b0 + k, set);
       }
@@ -869,6 +842,65 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
   }
 }
 
+// Shared-memory staging of the backward (one batch of kBatchB entries).
+template <int kAcc>
+struct BwdSmem {
+  float4 s0[kBatchB], s1[kBatchB], s2[kBatchB], s3[kBatchB], s4[kBatchB], s5[kBatchB];
+  uint32_t sm[kBatchB];
+  uint32_t sid[kBatchB];
+  float acc[kBatchB][kAcc];
+  uint32_t wbits[kThreads / 32][kWordsB];
+  int smax;
+};
+
+// Reverse replay of entry kk (list position k) for a thread's two pixels:
+// the pair's gradients, reduced over the warp into the entry's accumulator.
+template <bool kLoss, int kN, int kAcc>
+__device__ __forceinline__ void bwd_entry(BwdSmem<kAcc>& sh, int kk, int k, float lx, float ly, BwdPix& a,
+                                          BwdPix& b, int nsets, const SetDev& set, int lane, int myslot,
+                                          unsigned& replayed, unsigned& wentries, unsigned& wlanes) {
+  const float4 e0 = sh.s0[kk], jh = sh.s1[kk], e2 = sh.s2[kk];
+  const bool liveA = k < a.last, liveB = k < b.last;
+  replayed += (unsigned)liveA + (unsigned)liveB;
+  Pair qa, qb;
+  const float4 jl = sh.s4[kk];
+  eval_two(lx, ly, e0, jh, jl, sh.s5[kk], e2.y, set, qa, qb);
+  mask_pair(qa, liveA);
+  mask_pair(qb, liveB);
+  const bool contrib = qa.hit || qb.hit;
+  const unsigned ballot = __ballot_sync(0xffffffffu, contrib);
+  if (ballot == 0u) return;
+  ++wentries;
+  wlanes += __popc(ballot);
+  float v[kN];
+#pragma unroll
+  for (int i = 0; i < kN; ++i) v[i] = 0.f;
+  const float4 e3 = sh.s3[kk];
+  // Ji = Jh + Jl (FP32) for the chain rule
+  const float4 e1 = make_float4(jh.x + jl.x, jh.y + jl.y, jh.z + jl.z, jh.w + jl.w);
+  // a pixel row with no hit in the whole warp needs no gradient pass (a
+  // masked pair leaves the pixel's state and the sums unchanged)
+  const bool anyA = __any_sync(0xffffffffu, qa.hit), anyB = __any_sync(0xffffffffu, qb.hit);
+  if (anyA && anyB) {
+    bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
+    bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
+  } else if (anyA) {
+    bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
+  } else {
+    bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
+  }
+  if (__popc(ballot) == 1) {
+    if (contrib) {
+#pragma unroll
+      for (int i = 0; i < kN; ++i)
+        if (v[i] != 0.f) atomicAdd(&sh.acc[kk][i], v[i]);
+    }
+  } else {
+    rs_level<16, kN>(v, lane);
+    if (myslot >= 0 && v[0] != 0.f) atomicAdd(&sh.acc[kk][myslot], v[0]);
+  }
+}
+
 // kMinCtas: the CTAs per SM the register budget is sized for (5: 96
 // registers; 4: up to 128, for dense lists of small footprints).
 template <bool kLoss, int kMinCtas>
@@ -881,12 +913,7 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
   using LY = Layout<kLoss>;
   constexpr int kN = LY::kN;
   constexpr int kAcc = kN | 1;  // odd row stride: the flush's column reads are conflict-free
-  __shared__ float4 s0[kBatchB], s1[kBatchB], s2[kBatchB], s3[kBatchB], s4[kBatchB], s5[kBatchB];
-  __shared__ uint32_t sm[kBatchB];
-  __shared__ uint32_t sid[kBatchB];
-  __shared__ float acc[kBatchB][kAcc];
-  __shared__ uint32_t wbits[kThreads / 32][kWordsB];
-  __shared__ int smax;
+  __shared__ BwdSmem<kAcc> sh;
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
@@ -902,11 +929,11 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
   BwdPix a, b;
   bwd_init<kLoss>(a, inA, inA ? (size_t)pyA * cam.W + px : 0, HW, out, last, med, adj, set);
   bwd_init<kLoss>(b, inB, inB ? (size_t)pyB * cam.W + px : 0, HW, out, last, med, adj, set);
-  if (threadIdx.x == 0) smax = 0;
+  if (threadIdx.x == 0) sh.smax = 0;
   __syncthreads();
-  atomicMax(&smax, max(a.last, b.last));
+  atomicMax(&sh.smax, max(a.last, b.last));
   __syncthreads();
-  const int maxlast = smax;
+  const int maxlast = sh.smax;
   unsigned replayed = 0, wentries = 0, wlanes = 0;
 
   for (int bend = maxlast; bend > 0; bend -= kBatchB) {
@@ -915,81 +942,42 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += kThreads) {
       const uint32_t s = vals[rg.x + b0 + t];
-      sid[t] = s;
+      sh.sid[t] = s;
       const Staged e = stage_entry(rec, geom, s, tx0, ty0, cam.H, rf);
-      s0[t] = e.s0;
-      s1[t] = e.s1;
-      s2[t] = e.s2;
-      s3[t] = e.s3;
-      s4[t] = e.s4;
-      s5[t] = e.s5;
-      sm[t] = e.wmask;
+      sh.s0[t] = e.s0;
+      sh.s1[t] = e.s1;
+      sh.s2[t] = e.s2;
+      sh.s3[t] = e.s3;
+      sh.s4[t] = e.s4;
+      sh.s5[t] = e.s5;
+      sh.sm[t] = e.wmask;
     }
-    for (int i = threadIdx.x; i < nb * kAcc; i += kThreads) (&acc[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < nb * kAcc; i += kThreads) (&sh.acc[0][0])[i] = 0.f;
     __syncthreads();
-    warp_entry_bits<kWordsB>(sm, nb, warp, lane, wbits[warp]);
+    warp_entry_bits<kWordsB>(sh.sm, nb, warp, lane, sh.wbits[warp]);
     for (int j = kWordsB - 1; j >= 0; --j) {
-      uint32_t bits = wbits[warp][j];
+      uint32_t bits = sh.wbits[warp][j];
       while (bits != 0u) {  // back to front: highest set bit first
         const int hb = 31 - __clz(bits);
         bits &= ~(1u << hb);
-        const int kk = 32 * j + hb;
-        const int k = b0 + kk;
-        const float4 e0 = s0[kk], jh = s1[kk], jl = s4[kk], e2 = s2[kk];
-        const bool liveA = k < a.last, liveB = k < b.last;
-        replayed += (unsigned)liveA + (unsigned)liveB;
-        Pair qa, qb;
-        eval_entry(sm[kk], lx, lyA, e0, jh, jl, s5[kk], e2.y, set, qa, qb);
-        mask_pair(qa, liveA);
-        mask_pair(qb, liveB);
-        const bool contrib = qa.hit || qb.hit;
-        const unsigned ballot = __ballot_sync(0xffffffffu, contrib);
-        if (ballot == 0u) continue;
-        ++wentries;
-        wlanes += __popc(ballot);
-        float v[kN];
-  #pragma unroll
-        for (int i = 0; i < kN; ++i) v[i] = 0.f;
-        const float4 e3 = s3[kk];
-        // Ji = Jh + Jl (FP32; Jl = 0 for direct entries) for the chain rule
-        const float4 e1 = make_float4(jh.x + jl.x, jh.y + jl.y, jh.z + jl.z, jh.w + jl.w);
-        // a pixel row with no hit in the whole warp needs no gradient pass (a
-        // masked pair leaves the pixel's state and the sums unchanged)
-        const bool anyA = __any_sync(0xffffffffu, qa.hit), anyB = __any_sync(0xffffffffu, qb.hit);
-        if (anyA && anyB) {
-          bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
-          bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
-        } else if (anyA) {
-          bwd_pair<kLoss>(a, qa, e0, e1, e2, e3, k, nsets, set, v);
-        } else {
-          bwd_pair<kLoss>(b, qb, e0, e1, e2, e3, k, nsets, set, v);
-        }
-        if (__popc(ballot) == 1) {
-          if (contrib) {
-  #pragma unroll
-            for (int i = 0; i < kN; ++i)
-              if (v[i] != 0.f) atomicAdd(&acc[kk][i], v[i]);
-          }
-        } else {
-          rs_level<16, kN>(v, lane);
-          if (myslot >= 0 && v[0] != 0.f) atomicAdd(&acc[kk][myslot], v[0]);
-        }
+        bwd_entry<kLoss, kN, kAcc>(sh, 32 * j + hb, b0 + 32 * j + hb, lx, lyA, a, b, nsets, set, lane, myslot,
+                                   replayed, wentries, wlanes);
       }
     }
     __syncthreads();
     // flush this batch: one (surfel, tile) gradient record per entry
     for (int t = threadIdx.x; t < nb; t += kThreads) {
-      const uint32_t s = sid[t];
+      const uint32_t s = sh.sid[t];
       float* g = grec + (size_t)s * kGradRec;
 #pragma unroll
       for (int i = 0; i < LY::kRec; ++i) {
-        const float x = acc[t][i];
+        const float x = sh.acc[t][i];
         if (x != 0.f) atomicAdd(&g[i], x);
       }
       if (screen) {
         for (int st = 0; st < nsets; ++st) {
-          const float x0 = acc[t][LY::kRec + 2 * st];
-          const float x1 = acc[t][LY::kRec + 2 * st + 1];
+          const float x0 = sh.acc[t][LY::kRec + 2 * st];
+          const float x1 = sh.acc[t][LY::kRec + 2 * st + 1];
           float* sg = screen + ((size_t)st * n + s) * 2;
           if (x0 != 0.f) atomicAdd(&sg[0], x0);
           if (x1 != 0.f) atomicAdd(&sg[1], x1);
@@ -1085,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
         bits &= bits - 1u;
         const float4 e0 = s0[k], e1 = s1[k], e2 = s2[k];
         Pair qa, qb;
-        eval_entry(sm[k], lx, lyA, e0, e1, s4[k], s5[k], e2.y, set, qa, qb);
+        eval_two(lx, lyA, e0, e1, s4[k], s5[k], e2.y, set, qa, qb);
         const unsigned ba = __ballot_sync(0xffffffffu, inA && qa.rho <= set.rho_max);
         const unsigned bb = __ballot_sync(0xffffffffu, inB && qb.rho <= set.rho_max);
         const uint32_t cnt = (uint32_t)(__popc(ba) + __popc(bb));

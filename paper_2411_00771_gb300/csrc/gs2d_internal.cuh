@@ -60,8 +60,7 @@ struct SetDev {
 //  r1 = (Ji11, Ji12, Ji21, Ji22)           inverse of the centred Jacobian
 //  r2 = (e.x, e.y, p_z, opacity)           projective row, centre depth
 //  r3 = (r, g, b, n.x)                     colour, view-space normal
-//  r4 = (n.y, n.z, precise, 0)            precise: 1 when (u, v) needs the
-//                                          tile-relative split evaluation
+//  r4 = (n.y, n.z, 0, 0)
 //  r5 = (Ji11, Ji12, Ji21, Ji22) low parts: Ji = r1 + r5 to about 48 bits
 // For a pixel offset d = x - c:  den = 1 + e.d,  (u, v) = Ji d / den,
 // rho_obj = u^2 + v^2, z_obj = p_z / den.
@@ -190,12 +189,10 @@ __device__ __forceinline__ float load_opacity(const ParamsDev& P, int n) {
 // depth_key[i] (FP32 depth bits, or all ones when not visible) and idx[i]
 // (surfel index); per surfel: rec, rect, tcount, geom.  flags and scan_tmp
 // are scratch (n and scan_tmp_words(n) words).
-// tile_cnt (may be null): [tiles] instance counts, added to (zero it first).
 cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
                               float4* rec, uint2* rect, uint32_t* tcount, uint32_t* depth_key,
                               uint32_t* idx, uint32_t* cand, uint32_t* ncand, RowGeom* geom,
-                              uint32_t* flags, uint32_t* scan_tmp, cudaStream_t st,
-                              uint32_t* tile_cnt = nullptr);
+                              uint32_t* flags, uint32_t* scan_tmp, cudaStream_t st);
 
 // device-wide exclusive scan of n uint32 values; total (uint32) written to
 // *total_dev; tmp must hold scan_tmp_words(n) uint32 words.
@@ -220,19 +217,6 @@ cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint3
                         uint32_t* keys, uint32_t* vals, cudaStream_t st, const uint32_t* n_dev = nullptr);
 cudaError_t launch_ranges(const uint32_t* keys, int64_t K, int2* ranges, int ntiles,
                           cudaStream_t st);
-// Tile lists by buckets (sort.cu): the preprocess counts each tile's
-// instances into tile_cnt (zeroed before); launch_tile_scan writes the
-// tiles' starts and out2 = (instances, longest list); launch_bucket_lists
-// fills keys ([instances] 64-bit scratch) and writes the lists (vals) and
-// ranges, for lists of at most kBucketMaxLen entries (the same lists as the
-// radix path).  cursor: [ntiles] scratch.
-constexpr int kBucketMaxLen = 8192;
-cudaError_t launch_tile_scan(const uint32_t* cnt, int ntiles, uint32_t* start, uint32_t* out2, cudaStream_t st);
-cudaError_t launch_bucket_lists(const uint32_t* cand, const uint32_t* dkey, const uint32_t* tcount, const uint2* rect,
-                                const RowGeom* geom, float rf, int64_t n, const uint32_t* n_dev, int tiles_x,
-                                int ntiles, const uint32_t* tile_cnt, const uint32_t* start, uint32_t* cursor,
-                                unsigned long long* keys, int longest, uint32_t* vals, int2* ranges,
-                                cudaStream_t st);
 // Tile ids ordered by list length, longest first (launch order of the blends);
 // for images with more tiles than the ordering kernel holds, nothing is
 // written and the blends take the natural order (pass a null order).

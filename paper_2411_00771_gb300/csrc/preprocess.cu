@@ -211,8 +211,7 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
                                                               uint32_t* __restrict__ tcount,
                                                               uint32_t* __restrict__ dkey,
                                                               uint32_t* __restrict__ idx,
-                                                              RowGeom* __restrict__ geom,
-                                                              uint32_t* __restrict__ tile_cnt) {
+                                                              RowGeom* __restrict__ geom) {
   const uint32_t total = *ncand;
   const df rf = df_sqrt(df_make(set.rho_max) / df_make(set.sinv));
   const float rff = df_float(rf);
@@ -297,11 +296,7 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     uint32_t cnt = 0;
     for (int ty = ty0; ty < ty1; ++ty) {
       int a0, a1;
-      if (row_tiles(gm, ty, rff, &a0, &a1)) {
-        cnt += (uint32_t)(a1 - a0);
-        if (tile_cnt)
-          for (int tx = a0; tx < a1; ++tx) atomicAdd(&tile_cnt[ty * cam.tiles_x + tx], 1u);
-      }
+      if (row_tiles(gm, ty, rff, &a0, &a1)) cnt += (uint32_t)(a1 - a0);
     }
     if (cnt == 0) continue;
     geom[n] = gm;
@@ -360,18 +355,7 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     Rr[1] = r1f;
     Rr[2] = make_float4(ef.x, ef.y, pz, load_opacity(P, n));
     Rr[3] = make_float4(col[0], col[1], col[2], sg * df_float(nv.x));
-    // How far FP32 can evaluate (u, v) = Ji d directly from the centre: its
-    // error in u is about 3 2^-24 R D (R the larger row sum of |Ji|, D the
-    // half-extent of the ellipse {rho_obj <= rho_max} in pixels), so alpha =
-    // o exp(-(u^2 + v^2) / 2) carries a relative error up to 9 2^-24 R D at
-    // the support boundary.  Above R D = 12 (about 6.4e-6, a condition number
-    // of the centred Jacobian of roughly 3 and up: nearly edge-on or
-    // elongated disks) the blends evaluate the pair relative to the tile
-    // origin in the exact split form instead (see blend.cu).
-    const float Rs = fmaxf(fabsf(r1f.x) + fabsf(r1f.y), fabsf(r1f.z) + fabsf(r1f.w));
-    const float Ds = fmaxf(fmaxf(fabsf(df_float(x0)), fabsf(df_float(x1))), fmaxf(fabsf(df_float(y0)), fabsf(df_float(y1))));
-    const bool precise = isfinite(Rs) && !(Rs * Ds <= 12.f);
-    Rr[4] = make_float4(sg * df_float(nv.y), sg * df_float(nv.z), precise ? 1.f : 0.f, 0.f);
+    Rr[4] = make_float4(sg * df_float(nv.y), sg * df_float(nv.z), 0.f, 0.f);
     Rr[5] = r5f;
   }
 }
@@ -573,7 +557,7 @@ void launch_bwd_deg(const ParamsDev& P, const CamDev& cam, const uint32_t* cand,
 cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDev& set,
                               float4* rec, uint2* rect, uint32_t* tcount, uint32_t* dkey,
                               uint32_t* idx, uint32_t* cand, uint32_t* ncand, RowGeom* geom,
-                              uint32_t* flags, uint32_t* scan_tmp, cudaStream_t st, uint32_t* tile_cnt) {
+                              uint32_t* flags, uint32_t* scan_tmp, cudaStream_t st) {
   if (P.n == 0) return cudaMemsetAsync(ncand, 0, sizeof(uint32_t), st);
   ProfScope ps(kProfPreprocess, st);
   preprocess_cull_kernel<<<div_up(P.n, 256), 256, 0, st>>>(P, cam, set, rect, tcount, flags);
@@ -593,10 +577,10 @@ cudaError_t launch_preprocess(const ParamsDev& P, const CamDev& cam, const SetDe
   }();
   const unsigned blocks = div_up(P.n, 256) < resident ? div_up(P.n, 256) : resident;
   switch (P.sh_degree) {
-    case 0: preprocess_main_kernel<0><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom, tile_cnt); break;
-    case 1: preprocess_main_kernel<1><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom, tile_cnt); break;
-    case 2: preprocess_main_kernel<2><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom, tile_cnt); break;
-    default: preprocess_main_kernel<3><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom, tile_cnt); break;
+    case 0: preprocess_main_kernel<0><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
+    case 1: preprocess_main_kernel<1><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
+    case 2: preprocess_main_kernel<2><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
+    default: preprocess_main_kernel<3><<<blocks, 256, 0, st>>>(P, cam, set, cand, ncand, rec, rect, tcount, dkey, idx, geom); break;
   }
   count_launch(2);
   return cudaGetLastError();

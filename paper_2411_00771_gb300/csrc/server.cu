@@ -73,12 +73,12 @@ struct Slot {
   SlotState state = kIdle;
   cudaStream_t st = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
-  uint32_t* k_host = nullptr;  // pinned: instances, longest tile list
+  uint32_t* k_host = nullptr;  // pinned
   Ticket* t = nullptr;
   // resident buffers
   Buf rec, geom, rect, tcount, dkey, idx, dkey2, idx2, cnts, offs, cand, rtmp;  // per surfel
   Buf keys, vals, keys2, vals2, ktmp;                                             // per instance
-  Buf ranges, tiles;                                                              // per tile
+  Buf ranges;                                                                     // per tile
   Buf seg_tiles, seg_list, seg_trans, seg_part;  // long lists composited in segments
   int lseg = 0;                                  // 0: whole tiles
   unsigned nseg_max = 0;
@@ -88,15 +88,13 @@ struct Slot {
   ParamsDev P{};
   float rf = 0.f;
   int64_t K = 0;
-  int64_t longest = 0;       // longest tile list (bucket path)
-  bool bucket = false;       // lists by tile buckets (else the radix path)
   uint32_t* sidx = nullptr;  // sorted surfel order (one of idx / idx2)
   uint32_t* ncand = nullptr; // device count of sorted candidates
   uint32_t* vals_final = nullptr;
   size_t bytes() const {
     return rec.bytes + geom.bytes + rect.bytes + tcount.bytes + dkey.bytes + idx.bytes + dkey2.bytes +
            idx2.bytes + cnts.bytes + offs.bytes + cand.bytes + rtmp.bytes + keys.bytes + vals.bytes +
-           keys2.bytes + vals2.bytes + ktmp.bytes + ranges.bytes + tiles.bytes + seg_tiles.bytes + seg_list.bytes +
+           keys2.bytes + vals2.bytes + ktmp.bytes + ranges.bytes + seg_tiles.bytes + seg_list.bytes +
            seg_trans.bytes + seg_part.bytes;
   }
 };
@@ -173,14 +171,13 @@ int ensure(gs_server* s, Buf& b, size_t bytes, cudaStream_t st) {
 size_t stage_a_bytes_needed(int64_t n, int ntiles) {
   const size_t N = (size_t)(n > 0 ? n : 1);
   return N * (kRecF4 * sizeof(float4) + sizeof(RowGeom) + sizeof(uint2) + 9 * sizeof(uint32_t)) +
-         (radix_tmp_words(n) + scan_tmp_words(n) + 4) * sizeof(uint32_t) + ntiles * sizeof(int2) +
-         (3 * (size_t)ntiles + 2) * sizeof(uint32_t);
+         (radix_tmp_words(n) + scan_tmp_words(n) + 4) * sizeof(uint32_t) + ntiles * sizeof(int2);
 }
 
 void release_all(gs_server* s, Slot& sl) {
   Buf* all[] = {&sl.rec, &sl.geom, &sl.rect, &sl.tcount, &sl.dkey, &sl.idx, &sl.dkey2, &sl.idx2, &sl.cnts,
                 &sl.offs, &sl.cand, &sl.rtmp, &sl.keys, &sl.vals, &sl.keys2, &sl.vals2, &sl.ktmp, &sl.ranges,
-                &sl.tiles, &sl.seg_tiles, &sl.seg_list, &sl.seg_trans, &sl.seg_part};
+                &sl.seg_tiles, &sl.seg_list, &sl.seg_trans, &sl.seg_part};
   for (Buf* b : all) dev_free(s, *b, sl.st);
 }
 
@@ -219,7 +216,7 @@ gs_status stage_a(gs_server* s, Slot& sl, std::string* msg) {
               {&sl.rect, N * sizeof(uint2)}, {&sl.tcount, N * 4}, {&sl.dkey, N * 4}, {&sl.idx, N * 4},
               {&sl.dkey2, N * 4}, {&sl.idx2, N * 4}, {&sl.cnts, N * 4}, {&sl.offs, N * 4},
               {&sl.cand, N * 4}, {&sl.rtmp, (radix_tmp_words(n) + scan_tmp_words(n) + 4) * 4},
-              {&sl.ranges, (size_t)ntiles * sizeof(int2)}, {&sl.tiles, (3 * (size_t)ntiles + 2) * 4}};
+              {&sl.ranges, (size_t)ntiles * sizeof(int2)}};
   for (const Need& x : need) {
     const int r = ensure(s, *x.b, x.bytes, st);
     if (r == 1) {
@@ -235,38 +232,26 @@ gs_status stage_a(gs_server* s, Slot& sl, std::string* msg) {
   uint32_t* total = rtmp + radix_tmp_words(n) + scan_tmp_words(n);
   uint32_t* ncand = total + 1;
   sl.ncand = ncand;
-  // the same choice of path as a lone render (both give the same lists)
-  sl.bucket = tile_order_supported(ntiles);
-  uint32_t* tile_cnt = (uint32_t*)sl.tiles.p;
-  cudaError_t e = cudaSuccess;
-  if (sl.bucket) e = cudaMemsetAsync(tile_cnt, 0, sizeof(uint32_t) * (size_t)ntiles, st);
+  cudaError_t e = launch_preprocess(sl.P, sl.cam, sl.set, (float4*)sl.rec.p, (uint2*)sl.rect.p,
+                                    (uint32_t*)sl.tcount.p, (uint32_t*)sl.dkey.p, (uint32_t*)sl.idx.p,
+                                    (uint32_t*)sl.cand.p, ncand, (RowGeom*)sl.geom.p, (uint32_t*)sl.cnts.p,
+                                    rtmp + radix_tmp_words(n), st);
+  uint32_t *skey = nullptr, *sidx = nullptr;
   if (e == cudaSuccess)
-    e = launch_preprocess(sl.P, sl.cam, sl.set, (float4*)sl.rec.p, (uint2*)sl.rect.p, (uint32_t*)sl.tcount.p,
-                          (uint32_t*)sl.dkey.p, (uint32_t*)sl.idx.p, (uint32_t*)sl.cand.p, ncand,
-                          (RowGeom*)sl.geom.p, (uint32_t*)sl.cnts.p, rtmp + radix_tmp_words(n), st,
-                          sl.bucket ? tile_cnt : nullptr);
-  if (sl.bucket) {
-    uint32_t* out2 = tile_cnt + 3 * ntiles;
-    if (e == cudaSuccess) e = launch_tile_scan(tile_cnt, ntiles, tile_cnt + ntiles, out2, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.k_host, out2, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-  } else {
-    uint32_t *skey = nullptr, *sidx = nullptr;
-    if (e == cudaSuccess)
-      e = radix_sort_pairs((uint32_t*)sl.dkey.p, (uint32_t*)sl.idx.p, (uint32_t*)sl.dkey2.p,
-                           (uint32_t*)sl.idx2.p, n, 32, rtmp, &skey, &sidx, st, ncand);
-    if (e == cudaSuccess)
-      e = launch_gather_counts(sidx, (uint32_t*)sl.tcount.p, (uint32_t*)sl.cnts.p, n, st, ncand);
-    if (e == cudaSuccess)
-      e = launch_scan((uint32_t*)sl.cnts.p, (uint32_t*)sl.offs.p, n, total, rtmp + radix_tmp_words(n), st,
-                      ncand);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sl.k_host, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
-    sl.sidx = sidx;
-  }
+    e = radix_sort_pairs((uint32_t*)sl.dkey.p, (uint32_t*)sl.idx.p, (uint32_t*)sl.dkey2.p,
+                         (uint32_t*)sl.idx2.p, n, 32, rtmp, &skey, &sidx, st, ncand);
+  if (e == cudaSuccess)
+    e = launch_gather_counts(sidx, (uint32_t*)sl.tcount.p, (uint32_t*)sl.cnts.p, n, st, ncand);
+  if (e == cudaSuccess)
+    e = launch_scan((uint32_t*)sl.cnts.p, (uint32_t*)sl.offs.p, n, total, rtmp + radix_tmp_words(n), st,
+                    ncand);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sl.k_host, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(sl.ev_a, st);
   if (e != cudaSuccess) {
     *msg = std::string("stage A: ") + cudaGetErrorString(e);
     return GS_ERR_CUDA;
   }
+  sl.sidx = sidx;
   return GS_OK;
 }
 
@@ -287,7 +272,7 @@ int stage_b(gs_server* s, Slot& sl, std::string* msg) {
   const size_t tiles_words = 2 * (size_t)ntiles_v + 1 + scan_tmp_words(ntiles_v);
   Buf* bufs[] = {&sl.keys, &sl.vals, &sl.keys2, &sl.vals2, &sl.ktmp, &sl.seg_tiles, &sl.seg_list, &sl.seg_trans,
                  &sl.seg_part};
-  const size_t sizes[] = {KK * 8, KK * 4, KK * 4, KK * 4, radix_tmp_words(K) * 4,
+  const size_t sizes[] = {KK * 4, KK * 4, KK * 4, KK * 4, radix_tmp_words(K) * 4,
                           sl.lseg ? tiles_words * 4 : 0, (size_t)nmax * 2 * 4, (size_t)nmax * 256 * 4,
                           (size_t)nmax * 256 * seg_part_bytes()};
   for (int i = 0; i < 9; ++i) {
@@ -302,40 +287,9 @@ int stage_b(gs_server* s, Slot& sl, std::string* msg) {
   const int ntiles = sl.cam.tiles_x * sl.cam.tiles_y;
   int bits = 0;
   while ((int64_t(1) << bits) < ntiles) ++bits;
-  cudaError_t e = cudaSuccess;
-  const int64_t n = sl.P.n;
-  uint32_t* rtmp = (uint32_t*)sl.rtmp.p;
-  uint32_t* tile_cnt = (uint32_t*)sl.tiles.p;
-  if (sl.bucket && sl.longest <= kBucketMaxLen) {
-    // keys holds the 64-bit bucket keys (keys and keys2 are adjacent in size: 8 bytes per instance)
-    e = launch_bucket_lists((uint32_t*)sl.cand.p, (uint32_t*)sl.dkey.p, (uint32_t*)sl.tcount.p, (uint2*)sl.rect.p,
-                            (RowGeom*)sl.geom.p, sl.rf, n, sl.ncand, sl.cam.tiles_x, ntiles, tile_cnt,
-                            tile_cnt + ntiles, tile_cnt + 2 * ntiles, (unsigned long long*)sl.keys.p,
-                            (int)sl.longest, (uint32_t*)sl.vals.p, (int2*)sl.ranges.p, st);
-    if (e == cudaSuccess) e = cudaEventRecord(sl.ev_b, st);
-    if (e != cudaSuccess) {
-      *msg = std::string("stage B: ") + cudaGetErrorString(e);
-      return -1;
-    }
-    sl.vals_final = (uint32_t*)sl.vals.p;
-    return 1;
-  }
-  if (sl.bucket) {
-    // lists too long for the per-tile sort: the radix path, from the depth sort
-    uint32_t *skey = nullptr, *sidx = nullptr;
-    uint32_t* total = rtmp + radix_tmp_words(n) + scan_tmp_words(n);
-    e = radix_sort_pairs((uint32_t*)sl.dkey.p, (uint32_t*)sl.idx.p, (uint32_t*)sl.dkey2.p, (uint32_t*)sl.idx2.p, n,
-                         32, rtmp, &skey, &sidx, st, sl.ncand);
-    if (e == cudaSuccess)
-      e = launch_gather_counts(sidx, (uint32_t*)sl.tcount.p, (uint32_t*)sl.cnts.p, n, st, sl.ncand);
-    if (e == cudaSuccess)
-      e = launch_scan((uint32_t*)sl.cnts.p, (uint32_t*)sl.offs.p, n, total, rtmp + radix_tmp_words(n), st,
-                      sl.ncand);
-    sl.sidx = sidx;
-  }
-  if (e == cudaSuccess)
-    e = launch_emit(sl.sidx, (uint32_t*)sl.offs.p, (uint32_t*)sl.cnts.p, (uint2*)sl.rect.p, (RowGeom*)sl.geom.p,
-                    sl.rf, sl.P.n, sl.cam.tiles_x, (uint32_t*)sl.keys.p, (uint32_t*)sl.vals.p, st, sl.ncand);
+  cudaError_t e = launch_emit(sl.sidx, (uint32_t*)sl.offs.p, (uint32_t*)sl.cnts.p, (uint2*)sl.rect.p,
+                              (RowGeom*)sl.geom.p, sl.rf, sl.P.n, sl.cam.tiles_x, (uint32_t*)sl.keys.p,
+                              (uint32_t*)sl.vals.p, st, sl.ncand);
   uint32_t *tk = nullptr, *tv = nullptr;
   if (e == cudaSuccess)
     e = radix_sort_pairs((uint32_t*)sl.keys.p, (uint32_t*)sl.vals.p, (uint32_t*)sl.keys2.p,
@@ -474,8 +428,7 @@ void worker_loop(gs_server* s) {
           progress = true;
           continue;
         }
-        sl.K = sl.k_host[0];
-        sl.longest = sl.bucket ? sl.k_host[1] : 0;
+        sl.K = *sl.k_host;
         sl.state = kWaitMem;
         progress = true;
       }
@@ -649,7 +602,7 @@ gs_status gs_server_create(gs_server** out, size_t budget_bytes, int32_t max_slo
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_a, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev_b, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.k_host, 2 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.k_host, sizeof(uint32_t));
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->blend_st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->counters, sizeof(unsigned) * 8);

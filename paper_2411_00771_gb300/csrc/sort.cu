@@ -340,170 +340,7 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const int2* __restrict
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) order[atomicAdd(&cur[oct[t]], 1u)] = (uint32_t)t;
 }
 
-// ---- tile buckets ----------------------------------------------------------
-//
-// The same lists by counting instead of sorting surfels: the preprocess
-// counts each tile's instances; one block scans the counts into the tiles'
-// starts (these are the ranges); every candidate writes its (depth bits,
-// index) key into a slot of each tile it reaches (slots taken with atomics,
-// so in no particular order); one CTA per tile then sorts its keys in shared
-// memory, which leaves the list in (depth, index) order, the compositing
-// order, exactly as the radix path does (the keys are unique).
-
-__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t ws[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t inc = warp_incl_scan(v);
-  if (lane == 31) ws[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    const uint32_t x = ws[lane];
-    const uint32_t xi = warp_incl_scan(x);
-    ws[lane] = xi - x;
-    if (lane == 31) *total = xi;
-  }
-  __syncthreads();
-  return ws[w] + inc - v;
-}
-
-// Exclusive scan of the tile counts into start[]; out2 = (total, longest).
-__global__ void __launch_bounds__(1024) tile_scan_kernel(const uint32_t* __restrict__ cnt, int ntiles,
-                                                         uint32_t* __restrict__ start, uint32_t* __restrict__ out2) {
-  const int per = (ntiles + 1023) / 1024;
-  const int t0 = threadIdx.x * per;
-  uint32_t s = 0, mx = 0;
-  for (int i = 0; i < per; ++i) {
-    const int t = t0 + i;
-    if (t < ntiles) {
-      const uint32_t c = cnt[t];
-      s += c;
-      mx = max(mx, c);
-    }
-  }
-  __shared__ uint32_t tot, wmax[32];
-  uint32_t run = block_excl_scan_1024(s, &tot);
-  for (int i = 0; i < per; ++i) {
-    const int t = t0 + i;
-    if (t < ntiles) {
-      start[t] = run;
-      run += cnt[t];
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint32_t m = wmax[threadIdx.x];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) {
-      out2[0] = tot;
-      out2[1] = m;
-    }
-  }
-}
-
-// Candidate ci (surfel cand[ci], depth bits dkey[ci]) into the buckets of
-// the tiles the row rule lists it in.
-__global__ void emit_bucket_kernel(const uint32_t* __restrict__ cand, const uint32_t* __restrict__ dkey,
-                                   const uint32_t* __restrict__ tcount, const uint2* __restrict__ rect,
-                                   const RowGeom* __restrict__ geom, float rf, int64_t n_max,
-                                   const uint32_t* __restrict__ n_dev, int tiles_x,
-                                   const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ start,
-                                   uint32_t* __restrict__ cursor, unsigned long long* __restrict__ keys) {
-  const int64_t n = item_count(n_max, n_dev);
-  const int64_t ci = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (ci >= n) return;
-  const uint32_t s = cand[ci];
-  if (tcount[s] == 0u) return;
-  const unsigned long long key = ((unsigned long long)dkey[ci] << 32) | (unsigned long long)s;
-  const uint2 rc = rect[s];
-  const int ty0 = rc.x >> 16, ty1 = rc.y >> 16;
-  const RowGeom g = geom[s];
-  for (int ty = ty0; ty < ty1; ++ty) {
-    int a, b;
-    if (!row_tiles(g, ty, rf, &a, &b)) continue;
-    for (int tx = a; tx < b; ++tx) {
-      const int t = ty * tiles_x + tx;
-      const uint32_t slot = atomicAdd(&cursor[t], 1u);
-      if (slot < cnt[t]) keys[start[t] + slot] = key;  // the same rule counted them: always true
-    }
-  }
-}
-
-// One CTA per tile: bitonic sort of the tile's keys (padded to a power of
-// two with all-ones keys) in shared memory; the surfel indices become the
-// tile's list, and the tile's range is written.
-__global__ void __launch_bounds__(256) tile_sort_kernel(const uint32_t* __restrict__ cnt,
-                                                        const uint32_t* __restrict__ start,
-                                                        const unsigned long long* __restrict__ keys,
-                                                        uint32_t* __restrict__ vals, int2* __restrict__ ranges) {
-  extern __shared__ unsigned long long sk[];
-  const int t = blockIdx.x;
-  const int len = (int)cnt[t];
-  const int s0 = (int)start[t];
-  if (threadIdx.x == 0) ranges[t] = len > 0 ? make_int2(s0, s0 + len) : make_int2(0, 0);
-  if (len <= 1) {
-    if (len == 1 && threadIdx.x == 0) vals[s0] = (uint32_t)(keys[s0] & 0xFFFFFFFFull);
-    return;
-  }
-  int P = 2;
-  while (P < len) P <<= 1;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < len ? keys[s0 + i] : ~0ull;
-  __syncthreads();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
-        const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-        const int hi = lo + j;
-        const unsigned long long a = sk[lo], b = sk[hi];
-        const bool up = (lo & k) == 0;
-        if ((a > b) == up) {
-          sk[lo] = b;
-          sk[hi] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = threadIdx.x; i < len; i += blockDim.x) vals[s0 + i] = (uint32_t)(sk[i] & 0xFFFFFFFFull);
-}
-
 }  // namespace
-
-cudaError_t launch_tile_scan(const uint32_t* cnt, int ntiles, uint32_t* start, uint32_t* out2, cudaStream_t st) {
-  ProfScope ps(kProfSort, st);
-  count_launch();
-  tile_scan_kernel<<<1, 1024, 0, st>>>(cnt, ntiles, start, out2);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bucket_lists(const uint32_t* cand, const uint32_t* dkey, const uint32_t* tcount, const uint2* rect,
-                                const RowGeom* geom, float rf, int64_t n, const uint32_t* n_dev, int tiles_x,
-                                int ntiles, const uint32_t* tile_cnt, const uint32_t* start, uint32_t* cursor,
-                                unsigned long long* keys, int longest, uint32_t* vals, int2* ranges,
-                                cudaStream_t st) {
-  if (longest > kBucketMaxLen) return cudaErrorInvalidValue;
-  ProfScope ps(kProfSort, st);
-  cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * (size_t)ntiles, st);
-  if (e != cudaSuccess) return e;
-  if (n > 0) {
-    count_launch();
-    emit_bucket_kernel<<<div_up(n, 256), 256, 0, st>>>(cand, dkey, tcount, rect, geom, rf, n, n_dev, tiles_x,
-                                                       tile_cnt, start, cursor, keys);
-  }
-  int P = 2;
-  while (P < longest) P <<= 1;
-  const size_t smem = sizeof(unsigned long long) * (size_t)P;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  count_launch();
-  tile_sort_kernel<<<(unsigned)ntiles, 256, smem, st>>>(tile_cnt, start, keys, vals, ranges);
-  return cudaGetLastError();
-}
 
 // block sums, then the last-block counter
 size_t scan_tmp_words(int64_t n) { return (size_t)div_up(n > 0 ? n : 1, kTileItems) + 2; }

@@ -38,3 +38,32 @@ def test_config_names_the_workload_without_model_keys():
     assert c["views_per_step"] == 2 and c["surfels"] == bench.N_SURFELS
     assert not {"model", "global_batch", "seq_len"} & set(c)
     assert "L2" in c["l2"]
+
+
+def test_step_time_summary_shows_a_stall():
+    s = bench.step_time_summary([2.0, 2.1, 1.9, 9.0], host_ms=15.2)
+    assert s["median_ms"] == 2.1 and s["min_ms"] == 1.9 and s["max_ms"] == 9.0
+    assert s["host_wall_ms_per_step"] == 3.8
+
+
+def test_fp32_peak_from_unit_counts():
+    # 152 SMs x 128 lanes x 2 FLOPs x 2070 MHz
+    assert abs(bench.fp32_peak_tflops(152, 2070.0) - 80.55) < 0.01
+
+
+def test_stage_bytes_are_the_stated_per_unit_sums():
+    b = bench.stage_bytes(N=10, C=4, V=3, K=7, ntiles=2, npix=5)
+    assert b["preprocess"] == 10 * 48 + 4 * (4 + 192 + 96 + 56 + 8)
+    assert b["sort"] == 4 * 152 + 7 * 44 + 2 * 20
+    assert b["loss"] == 5 * 72
+    assert b["preprocess_bwd"] == 4 * 8 + 3 * (64 + 3 * 232)
+    assert b["densify"] == 10 * 118
+
+
+def test_stage_roofline_fractions():
+    info = {"n_candidates": 4, "n_visible": 3, "n_instances": 7, "tiles_x": 2, "tiles_y": 1,
+            "pairs_evaluated": 100, "pairs_blended": 40, "bwd_pairs_evaluated": 90}
+    r = bench.stage_roofline(info, {"loss": 1e-3, "blend_fwd": 1e-3}, 10, 5, 152, 2070.0, 1000.0)
+    assert r["loss"]["frac"] == round(5 * 72 / 1e-6 / 1e9 / 1000.0, 4)
+    flops = bench.FLOP_EVAL * 100 + bench.FLOP_BLEND * 40
+    assert r["blend_fwd"]["flops"] == flops and "blend_bwd" not in r

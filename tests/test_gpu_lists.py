@@ -45,8 +45,7 @@ def _city():
 
 def _dense(n):
     """n surfels seen at 64x64: 16 tiles with lists of thousands of entries
-    (30k: up to 6.7k entries, sorted per tile in shared memory; 60k: up to
-    13k, more than a CTA sorts, so the lists come from the radix path)."""
+    (30k: up to 6.7k entries; 60k: up to 13k)."""
     def make():
         scene, cam, _, _ = syn.tiny_scene(seed=77, n=n, width=64, height=64, fx=64.0, sh_degree=1,
                                           log_scale_range=(-4.0, -2.5))
