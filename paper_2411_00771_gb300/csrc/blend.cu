@@ -816,16 +816,19 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
   const float gdx = ob ? dnu * e1.x + dnv * e1.z + dden * e0.z : drho * rx;
   const float gdy = ob ? dnu * e1.y + dnv * e1.w + dden * e0.w : drho * ry;
   const float gpz = ob ? dzv * q.rden : dzv;
-  v[0] += ob ? dnu * q.dx : 0.f;
-  v[1] += ob ? dnu * q.dy : 0.f;
-  v[2] += ob ? dnv * q.dx : 0.f;
-  v[3] += ob ? dnv * q.dy : 0.f;
-  v[4] += ob ? dden * q.dx : 0.f;
-  v[5] += ob ? dden * q.dy : 0.f;
+  // the object-space terms of Ji and e, zero (and finite) where the screen
+  // branch was taken
+  const float dnu_o = ob ? dnu : 0.f, dnv_o = ob ? dnv : 0.f, dden_o = ob ? dden : 0.f;
+  v[0] = fmaf(dnu_o, q.dx, v[0]);
+  v[1] = fmaf(dnu_o, q.dy, v[1]);
+  v[2] = fmaf(dnv_o, q.dx, v[2]);
+  v[3] = fmaf(dnv_o, q.dy, v[3]);
+  v[4] = fmaf(dden_o, q.dx, v[4]);
+  v[5] = fmaf(dden_o, q.dy, v[5]);
   v[6] -= gdx;
   v[7] -= gdy;
   v[8] += gpz;
-  v[9] += unclamped ? dLda[0] * q.G : 0.f;
+  v[9] = fmaf(dLda[0], unclamped ? q.G : 0.f, v[9]);
   v[10] += w * p.gC[0][0];
   v[11] += w * p.gC[0][1];
   v[12] += w * p.gC[0][2];

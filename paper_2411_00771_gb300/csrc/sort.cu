@@ -272,28 +272,85 @@ __global__ void gather_counts_kernel(const uint32_t* __restrict__ order,
 
 // Instances of surfel order[r] at offsets offs[r]..: for every tile row of
 // its rectangle, the tile columns its footprint reaches (the same row rule,
-// on the same stored doubles, that counted them in the preprocess).
-__global__ void emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offs,
-                            const uint32_t* __restrict__ counts, const uint2* __restrict__ rect,
-                            const RowGeom* __restrict__ geom, float rf, int64_t n_max,
-                            const uint32_t* __restrict__ n_dev, int tiles_x,
-                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// on the same stored doubles, that counted them in the preprocess), row by
+// row, left to right.  A warp takes 32 consecutive candidates and spreads
+// their tile rows over its lanes (a long footprint's rows go to several
+// lanes instead of keeping one lane busy while the others wait); each row's
+// place within its surfel's run comes from a segmented prefix sum of the
+// rows' tile counts.
+__global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order,
+                                                   const uint32_t* __restrict__ offs,
+                                                   const uint32_t* __restrict__ counts,
+                                                   const uint2* __restrict__ rect,
+                                                   const RowGeom* __restrict__ geom, float rf, int64_t n_max,
+                                                   const uint32_t* __restrict__ n_dev, int tiles_x,
+                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  constexpr unsigned kFull = 0xffffffffu;
   const int64_t n = item_count(n_max, n_dev);
+  const int lane = threadIdx.x & 31;
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n || counts[r] == 0) return;
-  const uint32_t s = order[r];
-  const uint2 rc = rect[s];
-  const int ty0 = rc.x >> 16, ty1 = rc.y >> 16;
-  const RowGeom g = geom[s];
-  uint32_t o = offs[r];
-  for (int ty = ty0; ty < ty1; ++ty) {
-    int a, b;
-    if (!row_tiles(g, ty, rf, &a, &b)) continue;
-    for (int tx = a; tx < b; ++tx) {
-      keys[o] = (uint32_t)(ty * tiles_x + tx);
-      vals[o] = s;
-      ++o;
+  const bool valid = r < n && counts[r] > 0u;
+  uint32_t s = 0u, base = 0u;
+  int ty0 = 0, nrows = 0;
+  if (valid) {
+    s = order[r];
+    const uint2 rc = rect[s];
+    ty0 = (int)(rc.x >> 16);
+    nrows = (int)(rc.y >> 16) - ty0;
+    base = offs[r];
+  }
+  // exclusive prefix of the row counts over the warp: lane i's rows are
+  // flattened rows [first, first + nrows)
+  int incl = nrows;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int first = incl - nrows;
+  const int total = __shfl_sync(kFull, incl, 31);
+  uint32_t done = 0u;  // tiles written so far for lane's own surfel
+  for (int c0 = 0; c0 < total; c0 += 32) {
+    const int j = c0 + lane;
+    // the row's owner: the last lane whose first row is <= j (lanes with no
+    // rows share the next lane's first row and are passed over)
+    int own = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int cand = own + step;
+      const int fc = __shfl_sync(kFull, first, cand & 31);
+      if (cand < 32 && fc <= j) own = cand;
     }
+    const bool live = j < total;
+    const uint32_t so = __shfl_sync(kFull, s, own);
+    const int tyo = __shfl_sync(kFull, ty0, own) + (j - __shfl_sync(kFull, first, own));
+    const uint32_t bo = __shfl_sync(kFull, base, own);
+    const uint32_t prev = __shfl_sync(kFull, done, own);
+    int a = 0, b = 0;
+    if (live) {
+      const RowGeom g = geom[so];
+      if (!row_tiles(g, tyo, rf, &a, &b)) a = b = 0;
+    }
+    const int t = b - a;
+    // tiles of the owner's earlier rows in this chunk: segmented exclusive scan
+    int sc = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(kFull, sc, o);
+      if (lane >= o) sc += x;
+    }
+    const int sx = sc - t;  // exclusive
+    const int seg0 = max(__shfl_sync(kFull, first, own) - c0, 0);  // owner's first lane in this chunk
+    const int within = sx - __shfl_sync(kFull, sx, seg0);
+    uint32_t o = bo + prev + (uint32_t)within;
+    for (int tx = a; tx < b; ++tx, ++o) {
+      keys[o] = (uint32_t)(tyo * tiles_x + tx);
+      vals[o] = so;
+    }
+    // each surfel's tiles in this chunk, added to its running count
+    const int l0 = max(first - c0, 0), l1 = min(first + nrows - c0, 32) - 1;
+    const int sum = __shfl_sync(kFull, sc, max(l1, 0)) - __shfl_sync(kFull, sx, min(l0, 31));
+    if (nrows > 0 && l0 <= l1) done += (uint32_t)sum;
   }
 }
 
