@@ -21,7 +21,6 @@
 // memory once per (surfel, tile).
 #include <math.h>
 
-#include "gs2d_df.cuh"
 #include "gs2d_internal.cuh"
 
 namespace gs2d {
@@ -61,27 +60,30 @@ __device__ __forceinline__ int local_y(int t) { return ((t >> 6) << 3) | ((t >> 
 // in FP32 as Ji d, the coordinates of an ill-conditioned footprint (a nearly
 // edge-on or elongated disk: large Ji, pixel far from c along the long axis)
 // would carry an absolute error of about 2^-24 |Ji| |d|, far above the
-// error of the exact value near the support boundary.  Instead, per (entry,
-// tile): n0 is computed in double-float and both n0 and Ji are split on a
-// common power-of-two grid 2^g chosen from their magnitudes, the high parts
-// (nu0h on multiples of 2^g, Jh on multiples of 2^(g+1)) so coarse that
-// nu0h + Jh (lx, ly) is exact in FP32 for every pixel of the tile (lx, ly are
-// half-integers below 16), and the low parts (nu0l, Jl, at most about 2^g)
-// small enough that their FP32 rounding is negligible.  Then
-// Ji d = [nu0h + Jh (lx, ly)] + [nu0l + Jl (lx, ly)] is accurate to the FP32
-// rounding of the result itself, whatever the conditioning of Ji.
+// error of the exact value near the support boundary.  The preprocess splits
+// Ji = Jh + Jl and the offset of the surfel's first tile origin o_ref,
+// Ji (o_ref - c) = nref_h + nref_l, on a power-of-two grid 2^g chosen from the
+// magnitudes over the surfel's tile rectangle: the high parts (nref_h on
+// multiples of 2^g, Jh on multiples of 2^(g+1)) are so coarse that
+// nref_h + Jh (o - o_ref) + Jh (lx, ly) is exact in FP32 (o - o_ref are
+// multiples of 16, lx, ly half-integers below 16, every partial sum stays
+// below 2^(g+24)); the low parts (about 2^g) carry the rest with negligible
+// FP32 rounding.  Per (entry, tile) the staging forms
+// n0h = nref_h + Jh (o - o_ref) (exact) and n0l = nref_l + Jl (o - o_ref) with
+// four FMAs each; per pixel
+// Ji d = [n0h + Jh (lx, ly)] + [n0l + Jl (lx, ly)] is then accurate to the
+// FP32 rounding of the result itself, whatever the conditioning of Ji.
 struct Staged {
   float4 s0, s1, s2, s3, s4, s5;
   uint32_t wmask;
 };
 
-__device__ __forceinline__ float pow2i(int k) { return __int_as_float((k + 127) << 23); }  // |k| <= 126
 
 __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
                                               const RowGeom* __restrict__ geom, uint32_t s,
                                               int tx0, int ty0, int H, float rf) {
   const float4* R = rec + (size_t)s * kRecF4;
-  const float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4], r5 = R[5];
+  const float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4], r5 = R[5], r6 = R[6];
   Staged e;
   // centre relative to the tile origin: (c_hi - x0) + c_lo keeps the
   // offset accurate to its own rounding
@@ -89,31 +91,20 @@ __device__ __forceinline__ Staged stage_entry(const float4* __restrict__ rec,
                      __fadd_rn(__fsub_rn(r0.y, (float)ty0), r0.w), r2.x, r2.y);
   e.s2 = make_float4(r2.z, r2.w, r3.x, r3.y);
   e.s3 = make_float4(r3.z, r3.w, r4.x, r4.y);
-  {
-    // n0 = Ji (o - c) in double-float
-    const df d0x = two_sum((float)tx0, -r0.x) - r0.z;
-    const df d0y = two_sum((float)ty0, -r0.y) - r0.w;
-    const df nu0 = df_make(r1.x, r5.x) * d0x + df_make(r1.y, r5.y) * d0y;
-    const df nv0 = df_make(r1.z, r5.z) * d0x + df_make(r1.w, r5.w) * d0y;
-    // grid: every partial sum of nu0h + Jh (lx, ly) stays below 2^(g+24)
-    const float M = __fmul_rn(fmaxf(__fmaf_rn(16.f, __fadd_rn(fabsf(r1.x), fabsf(r1.y)), fabsf(nu0.hi)),
-                                    __fmaf_rn(16.f, __fadd_rn(fabsf(r1.z), fabsf(r1.w)), fabsf(nv0.hi))),
-                              1.0009765625f);
-    const int E = min(max(((__float_as_int(M) >> 23) & 0xff) - 127, -100), 100);  // M < 2^(E+1)
-    const int g = E - 21;
-    const float ug = pow2i(-g), dg = pow2i(g), uj = pow2i(-g - 1), dj = pow2i(g + 1);
-    float4 jh;
-    jh.x = __fmul_rn(rintf(__fmul_rn(r1.x, uj)), dj);
-    jh.y = __fmul_rn(rintf(__fmul_rn(r1.y, uj)), dj);
-    jh.z = __fmul_rn(rintf(__fmul_rn(r1.z, uj)), dj);
-    jh.w = __fmul_rn(rintf(__fmul_rn(r1.w, uj)), dj);
-    e.s1 = jh;
-    e.s4 = make_float4(__fadd_rn(__fsub_rn(r1.x, jh.x), r5.x), __fadd_rn(__fsub_rn(r1.y, jh.y), r5.y),
-                       __fadd_rn(__fsub_rn(r1.z, jh.z), r5.z), __fadd_rn(__fsub_rn(r1.w, jh.w), r5.w));
-    const float uh = __fmul_rn(rintf(__fmul_rn(nu0.hi, ug)), dg);
-    const float vh = __fmul_rn(rintf(__fmul_rn(nv0.hi, ug)), dg);
-    e.s5 = make_float4(uh, vh, __fadd_rn(__fsub_rn(nu0.hi, uh), nu0.lo), __fadd_rn(__fsub_rn(nv0.hi, vh), nv0.lo));
-  }
+  e.s1 = r1;
+  e.s4 = r5;
+  // n0 at this tile's origin (o - o_ref: multiples of 16, exact); the low
+  // part's grid rounding q moves to the high part (both sums exact), so the
+  // low part stays below 2^(g-1) whatever the tile's distance from o_ref
+  const uint32_t rt = __float_as_uint(r6.z);
+  const float dox = (float)(tx0 - (int)(rt & 0xFFFFu) * kTile), doy = (float)(ty0 - (int)(rt >> 16) * kTile);
+  const float ug = r6.w, dg = __frcp_rn(ug);
+  const float hu = __fmaf_rn(r1.x, dox, __fmaf_rn(r1.y, doy, r4.z));
+  const float hv = __fmaf_rn(r1.z, dox, __fmaf_rn(r1.w, doy, r4.w));
+  const float lu = __fmaf_rn(r5.x, dox, __fmaf_rn(r5.y, doy, r6.x));
+  const float lv = __fmaf_rn(r5.z, dox, __fmaf_rn(r5.w, doy, r6.y));
+  const float qu = __fmul_rn(rintf(__fmul_rn(lu, ug)), dg), qv = __fmul_rn(rintf(__fmul_rn(lv, ug)), dg);
+  e.s5 = make_float4(__fadd_rn(hu, qu), __fadd_rn(hv, qv), __fsub_rn(lu, qu), __fsub_rn(lv, qv));
   const RowGeom g = geom[s];
   uint32_t m = 0u;
 #pragma unroll

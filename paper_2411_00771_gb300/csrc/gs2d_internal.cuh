@@ -11,7 +11,7 @@
 namespace gs2d {
 
 constexpr int kTile = 16;              // 16 x 16 pixel tiles
-constexpr int kRecF4 = 6;              // per-surfel blend record, 6 x float4
+constexpr int kRecF4 = 7;              // per-surfel blend record, 7 x float4
 
 // Camera as the kernels see it (by value).  Geometry that decides where a
 // surfel lands on screen is carried in double precision.
@@ -57,13 +57,20 @@ struct SetDev {
 
 // Per-surfel blend record (written by the preprocess, read by both blends):
 //  r0 = (c_hi.x, c_hi.y, c_lo.x, c_lo.y)   projected centre, two-float split
-//  r1 = (Ji11, Ji12, Ji21, Ji22)           inverse of the centred Jacobian
+//  r1 = Jh                                 inverse of the centred Jacobian,
+//  r5 = Jl                                 split Ji = Jh + Jl on the surfel's grid
 //  r2 = (e.x, e.y, p_z, opacity)           projective row, centre depth
 //  r3 = (r, g, b, n.x)                     colour, view-space normal
-//  r4 = (n.y, n.z, 0, 0)
-//  r5 = (Ji11, Ji12, Ji21, Ji22) low parts: Ji = r1 + r5 to about 48 bits
+//  r4 = (n.y, n.z, nref_h.u, nref_h.v)     Ji (o_ref - c), high parts
+//  r6 = (nref_l.u, nref_l.v, tile, 2^-g)   its low parts; o_ref the origin of
+//                                          the rectangle's first tile, whose
+//                                          indices are packed in `tile`'s bits
+//                                          (x | y << 16); g the grid exponent
 // For a pixel offset d = x - c:  den = 1 + e.d,  (u, v) = Ji d / den,
-// rho_obj = u^2 + v^2, z_obj = p_z / den.
+// rho_obj = u^2 + v^2, z_obj = p_z / den.  Jh and nref_h lie on a grid 2^g
+// coarse enough that nref_h + Jh (o - o_ref) + Jh (lx, ly) sums exactly in
+// FP32 for every tile origin o and pixel offset (lx, ly) of the rectangle
+// (see the preprocess).
 
 // Footprint shape for tile-row coverage, FP32 (offsets from c): the ellipse
 // {rho_obj <= rho_max} is (d - e0)^T G^-1 (d - e0) <= 1; its boundary at

@@ -304,23 +304,49 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     const float pz = df_float(p.z);
     dkey[ci] = __float_as_uint(pz);
     const df det = J11 * J22 - J12 * J21;
-    float4 r1f, r5f;
+    // Ji, split for the blends' exact tile-relative evaluation of (u, v):
+    // on a power-of-two grid 2^g chosen so that |Ji d| < 2^(g+22) for every
+    // pixel and tile origin of the surfel's tile rectangle, Jh (multiples of
+    // 2^(g+1)) and nref_h (Ji (o_ref - c) on multiples of 2^g, o_ref the
+    // rectangle's first tile origin) make every partial sum of
+    // nref_h + Jh (o - o_ref) + Jh (lx, ly) exact in FP32; the low parts Jl =
+    // Ji - Jh and nref_l = Ji (o_ref - c) - nref_h (both about 2^g) carry the
+    // rest (see blend.cu).
+    float4 jh, jl, nref;  // nref = (nref_h.u, nref_h.v, nref_l.u, nref_l.v)
+    float ugrid = 1.f;    // 2^-g
     float2 ef;
+    const float orx = (float)(tx0 * kTile), ory = (float)(ty0 * kTile);
     if (df_nonzero(det)) {
       const df id = df_rcp(det);
       const df i11 = J22 * id, i12 = -(J12 * id), i21 = -(J21 * id), i22 = J11 * id;
-      r1f = make_float4(df_float(i11), df_float(i12), df_float(i21), df_float(i22));
-      // what FP32 leaves of Ji: the blends evaluate (u, v) relative to each
-      // tile from the double-float Ji (see blend.cu)
-      r5f = make_float4(df_float(i11 - r1f.x), df_float(i12 - r1f.y), df_float(i21 - r1f.z),
-                        df_float(i22 - r1f.w));
+      const float4 r1f = make_float4(df_float(i11), df_float(i12), df_float(i21), df_float(i22));
+      const float4 r5f = make_float4(df_float(i11 - r1f.x), df_float(i12 - r1f.y), df_float(i21 - r1f.z),
+                                     df_float(i22 - r1f.w));
       ef = make_float2(df_float(-(i11 * w1 + i21 * w2)), df_float(-(i12 * w1 + i22 * w2)));
+      const df d0x = two_sum(orx, -cx.hi) - cx.lo, d0y = two_sum(ory, -cy.hi) - cy.lo;
+      const df nu0 = i11 * d0x + i12 * d0y, nv0 = i21 * d0x + i22 * d0y;
+      const float Dx = fmaxf(fabsf(orx - cx.hi), fabsf((float)(tx1 * kTile) - cx.hi));
+      const float Dy = fmaxf(fabsf(ory - cy.hi), fabsf((float)(ty1 * kTile) - cy.hi));
+      const float Rs = fmaxf(fabsf(r1f.x) + fabsf(r1f.y), fabsf(r1f.z) + fabsf(r1f.w));
+      const float M = __fmul_rn(__fmul_rn(Rs, fmaxf(Dx, Dy) + 2.f), 1.0009765625f);
+      const int E = min(max(((__float_as_int(M) >> 23) & 0xff) - 127, -100), 100);  // M < 2^(E+1)
+      const int g = E - 21;
+      const float ug = __int_as_float((127 - g) << 23), dg = __int_as_float((127 + g) << 23);
+      const float uj = __int_as_float((126 - g) << 23), dj = __int_as_float((128 + g) << 23);
+      jh = make_float4(__fmul_rn(rintf(__fmul_rn(r1f.x, uj)), dj), __fmul_rn(rintf(__fmul_rn(r1f.y, uj)), dj),
+                       __fmul_rn(rintf(__fmul_rn(r1f.z, uj)), dj), __fmul_rn(rintf(__fmul_rn(r1f.w, uj)), dj));
+      jl = make_float4(__fadd_rn(__fsub_rn(r1f.x, jh.x), r5f.x), __fadd_rn(__fsub_rn(r1f.y, jh.y), r5f.y),
+                       __fadd_rn(__fsub_rn(r1f.z, jh.z), r5f.z), __fadd_rn(__fsub_rn(r1f.w, jh.w), r5f.w));
+      const float uh = __fmul_rn(rintf(__fmul_rn(nu0.hi, ug)), dg);
+      const float vh = __fmul_rn(rintf(__fmul_rn(nv0.hi, ug)), dg);
+      nref = make_float4(uh, vh, __fadd_rn(__fsub_rn(nu0.hi, uh), nu0.lo), __fadd_rn(__fsub_rn(nv0.hi, vh), nv0.lo));
+      ugrid = ug;
     } else {
       // edge-on disk: no object-space footprint (rho_obj is NaN, the
       // screen filter decides)
       const float qnan = __int_as_float(0x7fffffff);
-      r1f = make_float4(qnan, qnan, qnan, qnan);
-      r5f = make_float4(0.f, 0.f, 0.f, 0.f);
+      jh = make_float4(qnan, qnan, qnan, qnan);
+      jl = nref = make_float4(0.f, 0.f, 0.f, 0.f);
       ef = make_float2(0.f, 0.f);
     }
     // colour: SH at the world direction from the camera centre
@@ -352,11 +378,13 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
     const float sg = df_pos(dot3(nv, p)) ? -1.f : 1.f;
     float4* Rr = rec + (size_t)n * kRecF4;
     Rr[0] = make_float4(cx.hi, cy.hi, cx.lo, cy.lo);
-    Rr[1] = r1f;
+    Rr[1] = jh;
     Rr[2] = make_float4(ef.x, ef.y, pz, load_opacity(P, n));
     Rr[3] = make_float4(col[0], col[1], col[2], sg * df_float(nv.x));
-    Rr[4] = make_float4(sg * df_float(nv.y), sg * df_float(nv.z), 0.f, 0.f);
-    Rr[5] = r5f;
+    Rr[4] = make_float4(sg * df_float(nv.y), sg * df_float(nv.z), nref.x, nref.y);
+    Rr[5] = jl;
+    // the first tile of the rectangle (tile indices, packed) and 2^-g, g the grid's exponent
+    Rr[6] = make_float4(nref.z, nref.w, __uint_as_float((uint32_t)tx0 | ((uint32_t)ty0 << 16)), ugrid);
   }
 }
 
