@@ -28,6 +28,7 @@ namespace {
 
 constexpr int kThreads = 128;  // threads per tile CTA, two pixels each
 constexpr int kBatch = 256;    // list entries staged per batch
+constexpr int kTilePix = 2 * kThreads;  // pixels of a tile, two per thread
 
 // Hardware approximations (relative error about 2^-22), the same
 // instructions in both blends so that the replay reproduces the forward's
@@ -294,9 +295,7 @@ __device__ __forceinline__ void blend_fwd_tile(
   fwd_init(b, px < cam.W && pyB < cam.H);
   for (int b0 = 0; b0 < len; b0 += kBatch) {
     if (__syncthreads_count(a.done && b.done) == kThreads) break;
-#pragma unroll
-    for (int h = 0; h < kBatch / kThreads; ++h) {
-      const int t = threadIdx.x + h * kThreads;
+    for (int t = threadIdx.x; t < kBatch; t += kThreads) {
       if (b0 + t < len) {
         const Staged e = stage_entry(rec, geom, vals[rg.x + b0 + t], tx0, ty0, cam.H, rf);
         sh.s0[t] = e.s0;
@@ -404,9 +403,7 @@ __device__ __forceinline__ bool seg_of(const uint32_t* seg_tile, const uint32_t*
 __device__ __forceinline__ void stage_batch(FwdSmem& sh, const float4* __restrict__ rec,
                                             const RowGeom* __restrict__ geom, const uint32_t* __restrict__ vals,
                                             int base, int nb, int tx0, int ty0, int H, float rf) {
-#pragma unroll
-  for (int h = 0; h < kBatch / kThreads; ++h) {
-    const int t = threadIdx.x + h * kThreads;
+  for (int t = threadIdx.x; t < kBatch; t += kThreads) {
     if (t < nb) {
       const Staged e = stage_entry(rec, geom, vals[base + t], tx0, ty0, H, rf);
       sh.s0[t] = e.s0;
@@ -454,8 +451,8 @@ __global__ void __launch_bounds__(kThreads) seg_trans_kernel(
       }
     }
   }
-  trans[(size_t)blockIdx.x * kBatch + threadIdx.x] = TA;
-  trans[(size_t)blockIdx.x * kBatch + kThreads + threadIdx.x] = TB;
+  trans[(size_t)blockIdx.x * kTilePix + threadIdx.x] = TA;
+  trans[(size_t)blockIdx.x * kTilePix + kThreads + threadIdx.x] = TB;
 }
 
 __device__ __forceinline__ void seg_store(const FwdPix& p, bool inside, SegPart* __restrict__ part, int slot) {
@@ -489,8 +486,8 @@ __global__ void __launch_bounds__(kThreads) seg_blend_kernel(
   // transmittance in front: the segments before this one (contiguous)
   const int first = (int)blockIdx.x - s;
   for (int q = 0; q < s; ++q) {
-    a.T *= trans[(size_t)(first + q) * kBatch + threadIdx.x];
-    b.T *= trans[(size_t)(first + q) * kBatch + kThreads + threadIdx.x];
+    a.T *= trans[(size_t)(first + q) * kTilePix + threadIdx.x];
+    b.T *= trans[(size_t)(first + q) * kTilePix + kThreads + threadIdx.x];
   }
   const float zref = rec[(size_t)vals[rg.x] * kRecF4 + 2].z;  // the tile's first centre depth
   a.zr = zref;
@@ -514,7 +511,7 @@ __global__ void __launch_bounds__(kThreads) seg_blend_kernel(
       }
     }
   }
-  SegPart* pp = part + (size_t)blockIdx.x * kBatch;
+  SegPart* pp = part + (size_t)blockIdx.x * kTilePix;
   seg_store(a, inA, pp, threadIdx.x);
   seg_store(b, inB, pp, kThreads + threadIdx.x);
   if (counters) {
@@ -540,7 +537,7 @@ __device__ __forceinline__ FwdPix seg_merge_pixel(const SegPart* __restrict__ pa
   p.zr = zref;
   bool stopped = false;
   for (int q = 0; q < nseg_tile && !stopped; ++q) {
-    const SegPart g = part[(size_t)(first + q) * kBatch + slot];
+    const SegPart g = part[(size_t)(first + q) * kTilePix + slot];
     p.C0 += g.f0.x;
     p.C1 += g.f0.y;
     p.C2 += g.f0.z;
@@ -628,10 +625,13 @@ __global__ void __launch_bounds__(kThreads) blend_fwd_batched_kernel(BlendBatch 
 // Backward.
 
 constexpr int kMaxSets = 3;
-// Entries staged per batch in the backward: its gradient accumulators and
-// the six staged vectors per entry must fit five CTAs per SM.
-constexpr int kBatchB = 224;
-constexpr int kWordsB = kBatchB / 32;
+// Entries staged per batch in the backward, by the CTAs per SM its variant
+// is sized for: 128 for five (a small batch leaves more of the SM's shared
+// memory to L1: 0.939 -> 0.921 ms on the 1M-surfel view, against 224), 224
+// for four (the dense variant's long lists: 128 made the 4M-surfel training
+// step 2.5 % slower).  The gradient accumulators and the six staged vectors
+// per entry fit either way.
+constexpr int batch_b(int min_ctas) { return min_ctas >= 5 ? 128 : 224; }
 // Average tile-list length from which the backward takes the 4-CTA variant:
 // 200 (the 1M-surfel aerial view) ran best with 5 CTAs per SM, 590 (the
 // 4M-surfel orbit view) with 4.
@@ -836,21 +836,21 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
   }
 }
 
-// Shared-memory staging of the backward (one batch of kBatchB entries).
-template <int kAcc>
+// Shared-memory staging of the backward (one batch of kBB entries).
+template <int kAcc, int kBB>
 struct BwdSmem {
-  float4 s0[kBatchB], s1[kBatchB], s2[kBatchB], s3[kBatchB], s4[kBatchB], s5[kBatchB];
-  uint32_t sm[kBatchB];
-  uint32_t sid[kBatchB];
-  float acc[kBatchB][kAcc];
-  uint32_t wbits[kThreads / 32][kWordsB];
+  float4 s0[kBB], s1[kBB], s2[kBB], s3[kBB], s4[kBB], s5[kBB];
+  uint32_t sm[kBB];
+  uint32_t sid[kBB];
+  float acc[kBB][kAcc];
+  uint32_t wbits[kThreads / 32][kBB / 32];
   int smax;
 };
 
 // Reverse replay of entry kk (list position k) for a thread's two pixels:
 // the pair's gradients, reduced over the warp into the entry's accumulator.
-template <bool kLoss, int kN, int kAcc>
-__device__ __forceinline__ void bwd_entry(BwdSmem<kAcc>& sh, int kk, int k, float lx, float ly, BwdPix& a,
+template <bool kLoss, int kN, int kAcc, int kBB>
+__device__ __forceinline__ void bwd_entry(BwdSmem<kAcc, kBB>& sh, int kk, int k, float lx, float ly, BwdPix& a,
                                           BwdPix& b, int nsets, const SetDev& set, int lane, int myslot,
                                           unsigned& replayed, unsigned& wentries, unsigned& wlanes) {
   const float4 e0 = sh.s0[kk], jh = sh.s1[kk], e2 = sh.s2[kk];
@@ -907,7 +907,8 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
   using LY = Layout<kLoss>;
   constexpr int kN = LY::kN;
   constexpr int kAcc = kN | 1;  // odd row stride: the flush's column reads are conflict-free
-  __shared__ BwdSmem<kAcc> sh;
+  constexpr int kBatchB = batch_b(kMinCtas), kWordsB = kBatchB / 32;
+  __shared__ BwdSmem<kAcc, kBatchB> sh;
   const int tile = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
   const int tx0 = (tile % cam.tiles_x) * kTile, ty0 = (tile / cam.tiles_x) * kTile;
   const int lxi = local_x(threadIdx.x), lyi = local_y(threadIdx.x);
@@ -954,7 +955,7 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
       while (bits != 0u) {  // back to front: highest set bit first
         const int hb = 31 - __clz(bits);
         bits &= ~(1u << hb);
-        bwd_entry<kLoss, kN, kAcc>(sh, 32 * j + hb, b0 + 32 * j + hb, lx, lyA, a, b, nsets, set, lane, myslot,
+        bwd_entry<kLoss, kN, kAcc, kBatchB>(sh, 32 * j + hb, b0 + 32 * j + hb, lx, lyA, a, b, nsets, set, lane, myslot,
                                    replayed, wentries, wlanes);
       }
     }
@@ -1041,9 +1042,7 @@ __global__ void __launch_bounds__(kThreads) blend_contrib_kernel(
   for (int b0 = 0; b0 < len; b0 += kBatch) {
     const int nb = min(kBatch, len - b0);
     __syncthreads();
-#pragma unroll
-    for (int h = 0; h < kBatch / kThreads; ++h) {
-      const int t = threadIdx.x + h * kThreads;
+    for (int t = threadIdx.x; t < kBatch; t += kThreads) {
       if (t < nb) {
         const uint32_t sidx = vals[rg.x + b0 + t];
         const Staged e = stage_entry(rec, geom, sidx, tx0, ty0, cam.H, rf);

@@ -153,10 +153,13 @@ void dev_free(gs_server* s, Buf& b, cudaStream_t st) {
   b.bytes = 0;
 }
 // Ensure b holds `bytes`: 0 done, 1 over the budget, 2 the allocator failed.
-int ensure(gs_server* s, Buf& b, size_t bytes, cudaStream_t st) {
+// headroom: allocate an eighth more when it fits (buffers whose size varies
+// from view to view: the instance lists); the stage-A buffers, whose sizes
+// the admission reserves exactly, take none.
+int ensure(gs_server* s, Buf& b, size_t bytes, cudaStream_t st, bool headroom = true) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return 0;
-  size_t grow = bytes + bytes / 8;  // headroom against small regrowth
+  size_t grow = headroom ? bytes + bytes / 8 : bytes;
   if (s->bytes_in_use - b.bytes + grow > s->budget) grow = bytes;
   if (s->bytes_in_use - b.bytes + grow > s->budget) return 1;
   dev_free(s, b, st);
@@ -172,6 +175,23 @@ size_t stage_a_bytes_needed(int64_t n, int ntiles) {
   const size_t N = (size_t)(n > 0 ? n : 1);
   return N * (kRecF4 * sizeof(float4) + sizeof(RowGeom) + sizeof(uint2) + 9 * sizeof(uint32_t)) +
          (radix_tmp_words(n) + scan_tmp_words(n) + 4) * sizeof(uint32_t) + ntiles * sizeof(int2);
+}
+
+// Bytes a slot's stage-A buffers must grow by for a request of n surfels
+// and ntiles tiles (the same sizes stage_a ensures).
+size_t stage_a_growth(const Slot& sl, int64_t n, int ntiles) {
+  const size_t N = (size_t)(n > 0 ? n : 1);
+  const struct {
+    const Buf* b;
+    size_t bytes;
+  } need[] = {{&sl.rec, N * kRecF4 * sizeof(float4)}, {&sl.geom, N * sizeof(RowGeom)},
+              {&sl.rect, N * sizeof(uint2)}, {&sl.tcount, N * 4}, {&sl.dkey, N * 4}, {&sl.idx, N * 4},
+              {&sl.dkey2, N * 4}, {&sl.idx2, N * 4}, {&sl.cnts, N * 4}, {&sl.offs, N * 4},
+              {&sl.cand, N * 4}, {&sl.rtmp, (radix_tmp_words(n) + scan_tmp_words(n) + 4) * 4},
+              {&sl.ranges, (size_t)ntiles * sizeof(int2)}};
+  size_t g = 0;
+  for (const auto& x : need) g += x.b->bytes < x.bytes ? x.bytes - x.b->bytes : 0;
+  return g;
 }
 
 void release_all(gs_server* s, Slot& sl) {
@@ -218,7 +238,7 @@ gs_status stage_a(gs_server* s, Slot& sl, std::string* msg) {
               {&sl.cand, N * 4}, {&sl.rtmp, (radix_tmp_words(n) + scan_tmp_words(n) + 4) * 4},
               {&sl.ranges, (size_t)ntiles * sizeof(int2)}};
   for (const Need& x : need) {
-    const int r = ensure(s, *x.b, x.bytes, st);
+    const int r = ensure(s, *x.b, x.bytes, st, false);
     if (r == 1) {
       *msg = "device buffers for the surfels do not fit the memory budget";
       return GS_ERR_CAPACITY;
@@ -509,6 +529,9 @@ void worker_loop(gs_server* s) {
     // 4. admission: queued requests into idle slots, by memory footprint
     {
       std::unique_lock<std::mutex> lk(s->mu);
+      // stage-A growth of the requests admitted in this pass (their buffers
+      // are allocated after the pass, so bytes_in_use does not hold them yet)
+      size_t reserved = 0;
       for (size_t i = 0; i < s->slots.size() && !s->queue.empty(); ++i) {
         Slot& sl = s->slots[i];
         if (sl.state != kIdle) continue;
@@ -517,8 +540,8 @@ void worker_loop(gs_server* s) {
         const ParamsDev& P = scene_params(sc);
         const int tx = (t->req.camera.width + kTile - 1) / kTile, ty = (t->req.camera.height + kTile - 1) / kTile;
         const size_t need = stage_a_bytes_needed(P.n, tx * ty);
-        const size_t have = sl.bytes();
-        if (need > have && s->bytes_in_use - have + need > s->budget) {
+        size_t grow = stage_a_growth(sl, P.n, tx * ty);
+        if (grow > 0 && s->bytes_in_use + reserved + grow > s->budget) {
           bool others = false;
           for (const Slot& o : s->slots) others = others || o.state != kIdle;
           if (others) break;  // wait for memory to free up (head of line keeps its place)
@@ -535,7 +558,9 @@ void worker_loop(gs_server* s) {
             progress = true;
             continue;
           }
+          grow = need;
         }
+        reserved += grow;
         s->queue.pop_front();
         t->state = 1;
         incoming.push_back(t);
