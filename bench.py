@@ -55,7 +55,7 @@ def stage_bytes(N, C, V, K, ntiles, npix, sh_coeffs=16, n_sets=3):
     visible surfels, K (surfel, tile) instances, npix pixels.
       preprocess: every surfel reads mu, q, s (36 B) and writes its tile rect
         and count (12 B); every candidate reads opacity and SH (4 + 12 k B for
-        k SH coefficients per channel) and writes its blend record (96 B),
+        k SH coefficients per channel) and writes its blend record (112 B),
         footprint shape (56 B), depth key and index (8 B);
       order: per candidate 4 depth-sort passes of (key, value) read and
         written (64 B), the count gather and scan (16 B) and the emission's
@@ -75,7 +75,7 @@ def stage_bytes(N, C, V, K, ntiles, npix, sh_coeffs=16, n_sets=3):
         elongation filter (scales 8 B, keep 1 B)."""
     P = 36 + 4 + 12 * sh_coeffs
     return {
-        "preprocess": N * 48 + C * (4 + 12 * sh_coeffs + 96 + 56 + 8),
+        "preprocess": N * 48 + C * (4 + 12 * sh_coeffs + 112 + 56 + 8),
         "sort": C * (64 + 16 + 72) + K * (8 + 32 + 4) + ntiles * 20,
         "loss": npix * 72,
         "preprocess_bwd": C * 8 + V * (64 + 3 * P),
@@ -122,8 +122,8 @@ def measured_peak(key):
 # DRAM bytes (read + write) of one blend_bwd launch on this workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the
 # full-size view); valid only for the kernel sources it was taken on.
-BLEND_BWD_TRAFFIC = {"bytes": 174625536 + 9846016,
-                     "sources_sha256": "709c7e8a9e2e5466b2034c354a4b8aa40c8d71b24ebbb542dae497697890a95e"}
+BLEND_BWD_TRAFFIC = {"bytes": 182270464 + 11189760,
+                     "sources_sha256": "e1e4b75b66bcd6ab17ea489f5296a1097e48eb859d0507120eda720ecfc77118"}
 
 
 def blend_sources_sha256():

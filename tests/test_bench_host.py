@@ -53,7 +53,7 @@ def test_fp32_peak_from_unit_counts():
 
 def test_stage_bytes_are_the_stated_per_unit_sums():
     b = bench.stage_bytes(N=10, C=4, V=3, K=7, ntiles=2, npix=5)
-    assert b["preprocess"] == 10 * 48 + 4 * (4 + 192 + 96 + 56 + 8)
+    assert b["preprocess"] == 10 * 48 + 4 * (4 + 192 + 112 + 56 + 8)
     assert b["sort"] == 4 * 152 + 7 * 44 + 2 * 20
     assert b["loss"] == 5 * 72
     assert b["preprocess_bwd"] == 4 * 8 + 3 * (64 + 3 * 232)
