@@ -299,8 +299,8 @@ gs_status build_lists(gs_scene* sc, gs_frame* f, const char* who, cudaStream_t s
   GS_CKC(launch_preprocess(sc->P, cam, set, f->rec, f->rect, f->tcount, dkey, idx, f->cand, ncand, f->geom,
                            cnts, rtmp + radix_tmp_words(n), st));
   uint32_t *skey = dkey, *sidx = idx;
-  GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st, ncand));
-  GS_CKC(launch_gather_counts(sidx, f->tcount, cnts, n, st, ncand));
+  // the last pass also gathers each sorted candidate's instance count
+  GS_CKC(radix_sort_pairs(dkey, idx, dkey2, idx2, n, 32, rtmp, &skey, &sidx, st, ncand, f->tcount, cnts));
   GS_CKC(launch_scan(cnts, offs, n, total, rtmp + radix_tmp_words(n), st, ncand));
   uint32_t Kh = 0;
   GS_CKC(cudaMemcpyAsync(&Kh, total, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));

@@ -210,12 +210,14 @@ cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
 
 // LSD radix sort of (key, value) pairs over key bits [0, bits); stable.
 // Result ends in (keys_out, vals_out) (double-buffering through the alt
-// buffers); tmp must hold radix_tmp_words(n) uint32 words.
+// buffers); tmp must hold radix_tmp_words(n) uint32 words.  gsrc/gout
+// (optional): also gout[i] = gsrc[vals_out[i]] for the sorted pairs.
 size_t radix_tmp_words(int64_t n);
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, uint32_t* tmp,
                              uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st,
-                             const uint32_t* n_dev = nullptr);
+                             const uint32_t* n_dev = nullptr, const uint32_t* gsrc = nullptr,
+                             uint32_t* gout = nullptr);
 
 cudaError_t launch_gather_counts(const uint32_t* order, const uint32_t* tcount, uint32_t* out,
                                  int64_t n, cudaStream_t st, const uint32_t* n_dev = nullptr);

@@ -259,9 +259,8 @@ gs_status stage_a(gs_server* s, Slot& sl, std::string* msg) {
   uint32_t *skey = nullptr, *sidx = nullptr;
   if (e == cudaSuccess)
     e = radix_sort_pairs((uint32_t*)sl.dkey.p, (uint32_t*)sl.idx.p, (uint32_t*)sl.dkey2.p,
-                         (uint32_t*)sl.idx2.p, n, 32, rtmp, &skey, &sidx, st, ncand);
-  if (e == cudaSuccess)
-    e = launch_gather_counts(sidx, (uint32_t*)sl.tcount.p, (uint32_t*)sl.cnts.p, n, st, ncand);
+                         (uint32_t*)sl.idx2.p, n, 32, rtmp, &skey, &sidx, st, ncand, (uint32_t*)sl.tcount.p,
+                         (uint32_t*)sl.cnts.p);
   if (e == cudaSuccess)
     e = launch_scan((uint32_t*)sl.cnts.p, (uint32_t*)sl.offs.p, n, total, rtmp + radix_tmp_words(n), st,
                     ncand);

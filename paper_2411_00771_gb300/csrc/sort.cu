@@ -14,10 +14,19 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kItems = 16;
-constexpr int kTileItems = kThreads * kItems;  // 4096 items per block
 constexpr int kWarps = kThreads / 32;
 constexpr int kRadixBits = 8;
 constexpr int kBins = 1 << kRadixBits;
+
+// Items per thread of the scans and radix passes, by the grid's item bound:
+// a small block (1024 items) spreads a few hundred thousand items over all
+// SMs and keeps each block's serial ranking short; large inputs take 4096
+// to keep the per-block digit counts (and the offsets scan over them) small.
+inline int items_per_thread(int64_t n) { return n <= (int64_t(1) << 22) ? 4 : (n <= (int64_t(1) << 24) ? 8 : 16); }
+inline int64_t blocks_for(int64_t n) {
+  const int64_t ti = (int64_t)kThreads * items_per_thread(n);
+  return (n > 0 ? n + ti - 1 : ti) / ti;
+}
 
 // Item count: a host bound, lowered to a device-side count when one is given
 // (the grid is sized for the bound; blocks past the count do nothing).
@@ -99,18 +108,23 @@ __device__ void block_scan_inplace(uint32_t* __restrict__ v, int nb, uint32_t* _
 
 // Block sums of the input; the last block scans them (exclusive, in place)
 // and writes the grand total.
+template <int kIt>
 __global__ void __launch_bounds__(kThreads) scan_reduce(const uint32_t* __restrict__ in, int64_t n_max,
                                                         const uint32_t* __restrict__ n_dev,
                                                         uint32_t* __restrict__ sums,
                                                         uint32_t* __restrict__ total,
                                                         uint32_t* __restrict__ done) {
   const int64_t n = item_count(n_max, n_dev);
-  const int64_t base = (int64_t)blockIdx.x * kTileItems;
-  uint32_t s = 0;
-  for (int i = threadIdx.x; i < kTileItems; i += kThreads) {
-    const int64_t k = base + i;
-    if (k < n) s += in[k];
+  const int64_t base = (int64_t)blockIdx.x * (kThreads * kIt);
+  uint32_t x[kIt];
+#pragma unroll
+  for (int i = 0; i < kIt; ++i) {
+    const int64_t k = base + i * kThreads + threadIdx.x;
+    x[i] = k < n ? in[k] : 0u;
   }
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kIt; ++i) s += x[i];
   __shared__ uint32_t tot;
   block_excl_scan(s, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
@@ -118,62 +132,79 @@ __global__ void __launch_bounds__(kThreads) scan_reduce(const uint32_t* __restri
   block_scan_inplace(sums, (int)gridDim.x, total);
 }
 
+template <int kIt>
 __global__ void __launch_bounds__(kThreads) scan_down(const uint32_t* __restrict__ in,
                                                       uint32_t* __restrict__ out, int64_t n_max,
                                                       const uint32_t* __restrict__ n_dev,
                                                       const uint32_t* __restrict__ sums) {
-  __shared__ uint32_t tile[kTileItems];
+  constexpr int kTI = kThreads * kIt;
+  __shared__ uint32_t tile[kTI];
   const int64_t n = item_count(n_max, n_dev);
-  const int64_t base = (int64_t)blockIdx.x * kTileItems;
-  // coalesced load into shared memory, then each thread scans kItems
+  const int64_t base = (int64_t)blockIdx.x * kTI;
+  if (base >= n) return;
+  // coalesced load into shared memory, then each thread scans kIt
   // consecutive entries
-  for (int i = threadIdx.x; i < kTileItems; i += kThreads) {
-    const int64_t k = base + i;
-    tile[i] = k < n ? in[k] : 0u;
+  uint32_t x[kIt];
+#pragma unroll
+  for (int i = 0; i < kIt; ++i) {
+    const int64_t k = base + i * kThreads + threadIdx.x;
+    x[i] = k < n ? in[k] : 0u;
   }
+#pragma unroll
+  for (int i = 0; i < kIt; ++i) tile[i * kThreads + threadIdx.x] = x[i];
   __syncthreads();
-  uint32_t v[kItems];
   uint32_t s = 0;
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    v[i] = tile[threadIdx.x * kItems + i];
-    s += v[i];
+  for (int i = 0; i < kIt; ++i) {
+    x[i] = tile[threadIdx.x * kIt + i];
+    s += x[i];
   }
   __shared__ uint32_t tot;
   uint32_t pre = block_excl_scan(s, &tot) + sums[blockIdx.x];
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    tile[threadIdx.x * kItems + i] = pre;
-    pre += v[i];
+  for (int i = 0; i < kIt; ++i) {
+    tile[threadIdx.x * kIt + i] = pre;
+    pre += x[i];
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kTileItems; i += kThreads) {
-    const int64_t k = base + i;
-    if (k < n) out[k] = tile[i];
+#pragma unroll
+  for (int i = 0; i < kIt; ++i) {
+    const int64_t k = base + i * kThreads + threadIdx.x;
+    if (k < n) out[k] = tile[i * kThreads + threadIdx.x];
   }
 }
 
 // ---- radix sort -----------------------------------------------------------
+//
+// Per pass: every block counts the digits of its kThreads * kIt keys
+// (upsweep); one block per digit scans that digit's counts over the blocks
+// (offsets; the counts are stored digit-major, so the scan reads them in
+// order); every block then ranks its keys stably (per warp, a match over the
+// lanes' digits; the warps of the block in order) and scatters them
+// (downsweep).  Only the blocks that hold items (from the device-side count)
+// take part.
 
+template <int kIt>
 __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __restrict__ keys,
                                                           int64_t n_max, const uint32_t* __restrict__ n_dev,
                                                           int shift, int nbins,
                                                           uint32_t* __restrict__ hist) {
   const int64_t n = item_count(n_max, n_dev);
+  if ((int64_t)blockIdx.x * (kThreads * kIt) >= n) return;
   __shared__ uint32_t h[kBins];
   for (int i = threadIdx.x; i < kBins; i += kThreads) h[i] = 0u;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kTileItems + w * (32 * kItems);
+  const int64_t base = (int64_t)blockIdx.x * (kThreads * kIt) + w * (32 * kIt);
   const uint32_t mask = (uint32_t)nbins - 1u;
-  uint32_t kk[kItems];
+  uint32_t kk[kIt];
 #pragma unroll
-  for (int it = 0; it < kItems; ++it) {
+  for (int it = 0; it < kIt; ++it) {
     const int64_t k = base + it * 32 + lane;
     kk[it] = k < n ? keys[k] : 0u;
   }
 #pragma unroll
-  for (int it = 0; it < kItems; ++it) {
+  for (int it = 0; it < kIt; ++it) {
     const int64_t k = base + it * 32 + lane;
     const bool valid = k < n;
     const uint32_t d = valid ? ((kk[it] >> shift) & mask) : 0x100u;
@@ -181,39 +212,40 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __rest
     if (valid && lane == (31 - __clz(peers))) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < nbins; d += kThreads) hist[(int64_t)blockIdx.x * kBins + d] = h[d];
+  for (int d = threadIdx.x; d < nbins; d += kThreads) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
 }
 
-// Per digit d (one block each): exclusive prefix of the digit's per-block
-// counts over the blocks, in place, and the digit's total.
-__global__ void __launch_bounds__(kThreads) radix_offsets(uint32_t* __restrict__ hist, int nb,
+// Per digit d (one block each): exclusive prefix of the digit's counts over
+// the nb_active blocks that hold items, in place, and the digit's total.
+__global__ void __launch_bounds__(kThreads) radix_offsets(uint32_t* __restrict__ hist, int nb, int ti,
+                                                          int64_t n_max, const uint32_t* __restrict__ n_dev,
                                                           uint32_t* __restrict__ dtot) {
-  const int d = blockIdx.x;
-  const int per = (nb + kThreads - 1) / kThreads;
-  const int b0 = threadIdx.x * per;
-  uint32_t s = 0;
-  for (int i = 0; i < per; ++i)
-    if (b0 + i < nb) s += hist[(int64_t)(b0 + i) * kBins + d];
-  __shared__ uint32_t tot;
-  uint32_t run = block_excl_scan(s, &tot);
-  for (int i = 0; i < per; ++i) {
-    if (b0 + i < nb) {
-      uint32_t* h = hist + (int64_t)(b0 + i) * kBins + d;
-      const uint32_t x = *h;
-      *h = run;
-      run += x;
-    }
-  }
-  if (threadIdx.x == 0) dtot[d] = tot;
+  const int64_t n = item_count(n_max, n_dev);
+  const int act = (int)((n + ti - 1) / ti);
+  block_scan_inplace(hist + (int64_t)blockIdx.x * nb, act < nb ? act : nb, dtot + blockIdx.x);
 }
 
+// gsrc/gout (optional, last pass): gout[dst] = gsrc[value] for every moved
+// pair, a gather through the sorted values fused into the scatter.
+template <int kIt>
 __global__ void __launch_bounds__(kThreads) radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, int64_t n_max, const uint32_t* __restrict__ n_dev, int shift, int nbins,
-    const uint32_t* __restrict__ offs, const uint32_t* __restrict__ dtot) {
+    const uint32_t* __restrict__ offs, const uint32_t* __restrict__ dtot,
+    const uint32_t* __restrict__ gsrc, uint32_t* __restrict__ gout) {
   const int64_t n = item_count(n_max, n_dev);
+  if ((int64_t)blockIdx.x * (kThreads * kIt) >= n) return;
   __shared__ uint32_t wh[kWarps][kBins];
   __shared__ uint32_t dbase[kBins];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * (kThreads * kIt) + w * (32 * kIt);
+  uint32_t kk[kIt], vv[kIt], pos[kIt];
+#pragma unroll
+  for (int it = 0; it < kIt; ++it) {
+    const int64_t k = base + it * 32 + lane;
+    kk[it] = k < n ? kin[k] : 0u;
+    vv[it] = k < n ? vin[k] : 0u;
+  }
   {
     __shared__ uint32_t tot;
     const uint32_t x = threadIdx.x < nbins ? dtot[threadIdx.x] : 0u;
@@ -221,17 +253,12 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
   }
   for (int i = threadIdx.x; i < kWarps * kBins; i += kThreads) (&wh[0][0])[i] = 0u;
   __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
-  const int64_t base = (int64_t)blockIdx.x * kTileItems + w * (32 * kItems);
   const uint32_t mask = (uint32_t)nbins - 1u;
-  uint32_t kk[kItems], vv[kItems], pos[kItems];
 #pragma unroll
-  for (int it = 0; it < kItems; ++it) {
+  for (int it = 0; it < kIt; ++it) {
     const int64_t k = base + it * 32 + lane;
     const bool valid = k < n;
-    kk[it] = valid ? kin[k] : 0u;
-    vv[it] = valid ? vin[k] : 0u;
     const uint32_t d = valid ? ((kk[it] >> shift) & mask) : 0x100u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t cur = 0u;
@@ -243,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
   }
   __syncthreads();
   for (int d = threadIdx.x; d < nbins; d += kThreads) {
-    uint32_t run = dbase[d] + offs[(int64_t)blockIdx.x * kBins + d];
+    uint32_t run = dbase[d] + offs[(int64_t)d * gridDim.x + blockIdx.x];
 #pragma unroll
     for (int ww = 0; ww < kWarps; ++ww) {
       const uint32_t t = wh[ww][d];
@@ -253,12 +280,13 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
   }
   __syncthreads();
 #pragma unroll
-  for (int it = 0; it < kItems; ++it) {
+  for (int it = 0; it < kIt; ++it) {
     if (pos[it] == 0xFFFFFFFFu) continue;
     const uint32_t d = (kk[it] >> shift) & mask;
     const uint32_t dst = wh[w][d] + pos[it];
     kout[dst] = kk[it];
     vout[dst] = vv[it];
+    if (gout) gout[dst] = gsrc[vv[it]];
   }
 }
 
@@ -400,49 +428,76 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const int2* __restrict
 }  // namespace
 
 // block sums, then the last-block counter
-size_t scan_tmp_words(int64_t n) { return (size_t)div_up(n > 0 ? n : 1, kTileItems) + 2; }
+size_t scan_tmp_words(int64_t n) { return (size_t)blocks_for(n) + 2; }
 
 cudaError_t launch_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev,
                         uint32_t* tmp, cudaStream_t st, const uint32_t* n_dev) {
   if (n <= 0) {
     return total_dev ? cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), st) : cudaSuccess;
   }
-  const unsigned nb = div_up(n, kTileItems);
+  const unsigned nb = (unsigned)blocks_for(n);
   uint32_t* done = tmp + nb + 1;
   ProfScope ps(kProfSort, st);
   cudaError_t e = cudaMemsetAsync(done, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   count_launch(2);
-  scan_reduce<<<nb, kThreads, 0, st>>>(in, n, n_dev, tmp, total_dev, done);
-  scan_down<<<nb, kThreads, 0, st>>>(in, out, n, n_dev, tmp);
+  switch (items_per_thread(n)) {
+    case 4:
+      scan_reduce<4><<<nb, kThreads, 0, st>>>(in, n, n_dev, tmp, total_dev, done);
+      scan_down<4><<<nb, kThreads, 0, st>>>(in, out, n, n_dev, tmp);
+      break;
+    case 8:
+      scan_reduce<8><<<nb, kThreads, 0, st>>>(in, n, n_dev, tmp, total_dev, done);
+      scan_down<8><<<nb, kThreads, 0, st>>>(in, out, n, n_dev, tmp);
+      break;
+    default:
+      scan_reduce<16><<<nb, kThreads, 0, st>>>(in, n, n_dev, tmp, total_dev, done);
+      scan_down<16><<<nb, kThreads, 0, st>>>(in, out, n, n_dev, tmp);
+      break;
+  }
   return cudaGetLastError();
 }
 
-// block-major histogram (kBins words per block), then the digit totals
-size_t radix_tmp_words(int64_t n) {
-  const size_t nb = div_up(n > 0 ? n : 1, kTileItems);
-  return nb * kBins + kBins;
+// digit-major counts (kBins rows of one word per block), then the digit totals
+size_t radix_tmp_words(int64_t n) { return (size_t)blocks_for(n) * kBins + kBins; }
+
+namespace {
+template <int kIt>
+void radix_pass(const uint32_t* ki, const uint32_t* vi, uint32_t* ko, uint32_t* vo, int64_t n,
+                const uint32_t* n_dev, int shift, int nbins, unsigned nb, uint32_t* hist, uint32_t* dtot,
+                const uint32_t* gsrc, uint32_t* gout, cudaStream_t st) {
+  radix_upsweep<kIt><<<nb, kThreads, 0, st>>>(ki, n, n_dev, shift, nbins, hist);
+  radix_offsets<<<nbins, kThreads, 0, st>>>(hist, (int)nb, kThreads * kIt, n, n_dev, dtot);
+  radix_downsweep<kIt><<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, nbins, hist, dtot, gsrc, gout);
 }
+}  // namespace
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                              uint32_t* vals_alt, int64_t n, int bits, uint32_t* tmp,
                              uint32_t** keys_out, uint32_t** vals_out, cudaStream_t st,
-                             const uint32_t* n_dev) {
+                             const uint32_t* n_dev, const uint32_t* gsrc, uint32_t* gout) {
   *keys_out = keys;
   *vals_out = vals;
-  if (n <= 1 || bits <= 0) return cudaSuccess;
+  if (n <= 1 || bits <= 0) {
+    // no pass to fuse the gather into
+    return gout ? launch_gather_counts(vals, gsrc, gout, n, st, n_dev) : cudaSuccess;
+  }
   ProfScope ps(kProfSort, st);
-  const unsigned nb = div_up(n, kTileItems);
+  const unsigned nb = (unsigned)blocks_for(n);
+  const int it = items_per_thread(n);
   uint32_t* hist = tmp;
   uint32_t* dtot = tmp + (size_t)nb * kBins;
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   for (int shift = 0; shift < bits; shift += kRadixBits) {
     const int pb = bits - shift < kRadixBits ? bits - shift : kRadixBits;
     const int nbins = 1 << pb;
+    const bool last = shift + kRadixBits >= bits;
+    const uint32_t* gs = last ? gsrc : nullptr;
+    uint32_t* go = last ? gout : nullptr;
     count_launch(3);
-    radix_upsweep<<<nb, kThreads, 0, st>>>(ki, n, n_dev, shift, nbins, hist);
-    radix_offsets<<<nbins, kThreads, 0, st>>>(hist, (int)nb, dtot);
-    radix_downsweep<<<nb, kThreads, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, nbins, hist, dtot);
+    if (it == 4) radix_pass<4>(ki, vi, ko, vo, n, n_dev, shift, nbins, nb, hist, dtot, gs, go, st);
+    else if (it == 8) radix_pass<8>(ki, vi, ko, vo, n, n_dev, shift, nbins, nb, hist, dtot, gs, go, st);
+    else radix_pass<16>(ki, vi, ko, vo, n, n_dev, shift, nbins, nb, hist, dtot, gs, go, st);
     uint32_t* t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
   }
