@@ -66,18 +66,35 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
   return r;
 }
 
-// Last-block election: every block calls this once, after its writes to
-// global memory.  Returns true in the block that arrives last, to which all
-// blocks' writes are then visible (it reads them through L2).  atomicInc
-// wraps the counter back to zero, so it is ready for the next launch.
+// Last-block election: every block calls this once, after its thread 0 has
+// written the block's result to global memory.  Returns true in the block
+// that arrives last, to which all blocks' results are then visible (it reads
+// them through L2).  atomicInc wraps the counter back to zero, so it is ready
+// for the next launch.
 __device__ __forceinline__ bool last_block(uint32_t* done) {
   __shared__ bool last;
-  __threadfence();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's result before its arrival
+    last = atomicInc(done, gridDim.x - 1u) == gridDim.x - 1u;
+    if (last) __threadfence();
+  }
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicInc(done, gridDim.x - 1u) == gridDim.x - 1u;
-  __syncthreads();
-  if (last) __threadfence();
   return last;
+}
+
+// Sum of one value per thread over the block (256 threads), in thread 0.
+__device__ __forceinline__ uint32_t block_sum(uint32_t v) {
+  __shared__ uint32_t ws[kWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  uint32_t t = 0;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < kWarps; ++i) t += ws[i];
+  return t;
 }
 
 // One block: exclusive scan of nb values in place; their sum to *total.
@@ -125,9 +142,8 @@ __global__ void __launch_bounds__(kThreads) scan_reduce(const uint32_t* __restri
   uint32_t s = 0;
 #pragma unroll
   for (int i = 0; i < kIt; ++i) s += x[i];
-  __shared__ uint32_t tot;
-  block_excl_scan(s, &tot);
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+  s = block_sum(s);
+  if (threadIdx.x == 0) sums[blockIdx.x] = s;
   if (!last_block(done)) return;
   block_scan_inplace(sums, (int)gridDim.x, total);
 }
@@ -179,10 +195,22 @@ __global__ void __launch_bounds__(kThreads) scan_down(const uint32_t* __restrict
 // Per pass: every block counts the digits of its kThreads * kIt keys
 // (upsweep); one block per digit scans that digit's counts over the blocks
 // (offsets; the counts are stored digit-major, so the scan reads them in
-// order); every block then ranks its keys stably (per warp, a match over the
-// lanes' digits; the warps of the block in order) and scatters them
+// order); every block then ranks its keys stably (per warp, from ballots of the
+// lanes' digit bits; the warps of the block in order) and scatters them
 // (downsweep).  Only the blocks that hold items (from the device-side count)
 // take part.
+
+// Lanes of the warp whose 9-bit digit equals this lane's: the AND over the
+// digit's bits of each bit's ballot (or its complement).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+  uint32_t peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const uint32_t bl = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+    peers &= ((d >> b) & 1u) ? bl : ~bl;
+  }
+  return peers;
+}
 
 template <int kIt>
 __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __restrict__ keys,
@@ -207,9 +235,7 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep(const uint32_t* __rest
   for (int it = 0; it < kIt; ++it) {
     const int64_t k = base + it * 32 + lane;
     const bool valid = k < n;
-    const uint32_t d = valid ? ((kk[it] >> shift) & mask) : 0x100u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (valid && lane == (31 - __clz(peers))) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    if (valid) atomicAdd(&h[(kk[it] >> shift) & mask], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < nbins; d += kThreads) hist[(int64_t)d * gridDim.x + blockIdx.x] = h[d];
@@ -260,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep(
     const int64_t k = base + it * 32 + lane;
     const bool valid = k < n;
     const uint32_t d = valid ? ((kk[it] >> shift) & mask) : 0x100u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t peers = digit_peers(d);
     uint32_t cur = 0u;
     if (valid) cur = wh[w][d];
     __syncwarp();
@@ -306,17 +332,12 @@ __global__ void gather_counts_kernel(const uint32_t* __restrict__ order,
 // lanes instead of keeping one lane busy while the others wait); each row's
 // place within its surfel's run comes from a segmented prefix sum of the
 // rows' tile counts.
-__global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order,
-                                                   const uint32_t* __restrict__ offs,
-                                                   const uint32_t* __restrict__ counts,
-                                                   const uint2* __restrict__ rect,
-                                                   const RowGeom* __restrict__ geom, float rf, int64_t n_max,
-                                                   const uint32_t* __restrict__ n_dev, int tiles_x,
-                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+__device__ __forceinline__ void emit_warp(int64_t r, int64_t n, int lane, const uint32_t* __restrict__ order,
+                                          const uint32_t* __restrict__ offs, const uint32_t* __restrict__ counts,
+                                          const uint2* __restrict__ rect, const RowGeom* __restrict__ geom,
+                                          float rf, int tiles_x, uint32_t* __restrict__ keys,
+                                          uint32_t* __restrict__ vals) {
   constexpr unsigned kFull = 0xffffffffu;
-  const int64_t n = item_count(n_max, n_dev);
-  const int lane = threadIdx.x & 31;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = r < n && counts[r] > 0u;
   uint32_t s = 0u, base = 0u;
   int ty0 = 0, nrows = 0;
@@ -380,6 +401,22 @@ __global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ 
     const int sum = __shfl_sync(kFull, sc, max(l1, 0)) - __shfl_sync(kFull, sx, min(l0, 31));
     if (nrows > 0 && l0 <= l1) done += (uint32_t)sum;
   }
+}
+
+__global__ void __launch_bounds__(256) emit_kernel(const uint32_t* __restrict__ order,
+                                                   const uint32_t* __restrict__ offs,
+                                                   const uint32_t* __restrict__ counts,
+                                                   const uint2* __restrict__ rect,
+                                                   const RowGeom* __restrict__ geom, float rf, int64_t n_max,
+                                                   const uint32_t* __restrict__ n_dev, int tiles_x,
+                                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t n = item_count(n_max, n_dev);
+  const int lane = threadIdx.x & 31;
+  // grid-stride over warps of 32 candidates (the grid is sized for the
+  // resident CTAs, the count is known on the device only)
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); r0 < n;
+       r0 += (int64_t)gridDim.x * blockDim.x)
+    emit_warp(r0 + lane, n, lane, order, offs, counts, rect, geom, rf, tiles_x, keys, vals);
 }
 
 __global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t K, int2* __restrict__ ranges) {
@@ -521,8 +558,16 @@ cudaError_t launch_emit(const uint32_t* order, const uint32_t* offs, const uint3
   if (n <= 0) return cudaSuccess;
   ProfScope ps(kProfSort, st);
   count_launch();
-  emit_kernel<<<div_up(n, 256), 256, 0, st>>>(order, offs, counts, rect, geom, rf, n, n_dev, tiles_x, keys,
-                                               vals);
+  // at most eight CTAs per SM (the count of candidates is on the device; the
+  // bound n is usually several times larger)
+  static const unsigned resident = [] {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return 8u * (unsigned)sms;
+  }();
+  const unsigned blocks = div_up(n, 256) < resident ? div_up(n, 256) : resident;
+  emit_kernel<<<blocks, 256, 0, st>>>(order, offs, counts, rect, geom, rf, n, n_dev, tiles_x, keys, vals);
   return cudaGetLastError();
 }
 
