@@ -394,12 +394,36 @@ __global__ void __launch_bounds__(256) preprocess_main_kernel(ParamsDev P, CamDe
 // Gradient of one visible surfel n: chain the per-surfel record (d Ji, d e,
 // d c, d p_z, d opacity, d rgb, d normal) back to mu, q, s, o and SH,
 // accumulated into G.  kVec: SH rows and gradient rows are float4-aligned.
+// Every load that does not depend on the computation (the surfel's tile
+// count tc, its gradient record, parameters and the current values of the
+// small gradient arrays) is issued before the first use, so that a surfel
+// costs two memory round trips (these loads, then the SH gradient row) and
+// not one per dependent access.  The gradient arrays must not overlap one
+// another or the parameters.
 template <int DEG, bool kVec>
-__device__ __forceinline__ void bwd_one(const ParamsDev& P, const CamDev& cam, int n,
+__device__ __forceinline__ void bwd_one(const ParamsDev& P, const CamDev& cam, int n, uint32_t tc,
                                         const float* __restrict__ grec, const gs_param_grads& G) {
   static_assert(kGradRec == 16, "gradient record of four float4");
+  float* __restrict__ Gq = G.quat;
+  float* __restrict__ Gm = G.mu;
+  float* __restrict__ Gs = G.scale;
+  float* __restrict__ Go = G.opacity;
   const float4* g4 = reinterpret_cast<const float4*>(grec + (size_t)n * kGradRec);
   const float4 ga4 = g4[0], gb4 = g4[1], gc4 = g4[2], gd4 = g4[3];
+  float oq[4] = {0.f, 0.f, 0.f, 0.f}, om[3] = {0.f, 0.f, 0.f}, os[2] = {0.f, 0.f}, oo = 0.f;
+  if (Gq) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) oq[i] = Gq[4 * n + i];
+  }
+  if (Gm) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) om[i] = Gm[3 * n + i];
+  }
+  if (Gs) {
+    os[0] = Gs[2 * n];
+    os[1] = Gs[2 * n + 1];
+  }
+  if (Go) oo = Go[n];
   float gJi11 = ga4.x, gJi12 = ga4.y, gJi21 = ga4.z, gJi22 = ga4.w;
   const float ge1 = gb4.x, ge2 = gb4.y, gcx = gb4.z, gcy = gb4.w, gpz0 = gc4.x, gop = gc4.y;
   const float grgb[3] = {gc4.z, gc4.w, gd4.x};
@@ -476,6 +500,7 @@ __device__ __forceinline__ void bwd_one(const ParamsDev& P, const CamDev& cam, i
 #pragma unroll
     for (int i = 0; i < K * 3; ++i) fv[i] = f[i];
   }
+  if (tc == 0u) return;  // no tile: nothing to add
   float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < K; ++k)
@@ -530,22 +555,22 @@ __device__ __forceinline__ void bwd_one(const ParamsDev& P, const CamDev& cam, i
   const float dqz = 2.f * (-2.f * qz * R00 - qw * R01 + qx * R02 + qw * R10 - 2.f * qz * R11 +
                            qy * R12 + qx * R20 + qy * R21);
   const float qd = qw * dqw + qx * dqx + qy * dqy + qz * dqz;
-  if (G.quat) {
-    G.quat[4 * n] += (dqw - qw * qd) * iqn;
-    G.quat[4 * n + 1] += (dqx - qx * qd) * iqn;
-    G.quat[4 * n + 2] += (dqy - qy * qd) * iqn;
-    G.quat[4 * n + 3] += (dqz - qz * qd) * iqn;
+  if (Gq) {
+    Gq[4 * n] = oq[0] + (dqw - qw * qd) * iqn;
+    Gq[4 * n + 1] = oq[1] + (dqx - qx * qd) * iqn;
+    Gq[4 * n + 2] = oq[2] + (dqy - qy * qd) * iqn;
+    Gq[4 * n + 3] = oq[3] + (dqz - qz * qd) * iqn;
   }
-  if (G.mu) {
-    G.mu[3 * n] += gmu.x;
-    G.mu[3 * n + 1] += gmu.y;
-    G.mu[3 * n + 2] += gmu.z;
+  if (Gm) {
+    Gm[3 * n] = om[0] + gmu.x;
+    Gm[3 * n + 1] = om[1] + gmu.y;
+    Gm[3 * n + 2] = om[2] + gmu.z;
   }
-  if (G.scale) {
-    G.scale[2 * n] += gsu;
-    G.scale[2 * n + 1] += gsv;
+  if (Gs) {
+    Gs[2 * n] = os[0] + gsu;
+    Gs[2 * n + 1] = os[1] + gsv;
   }
-  if (G.opacity) G.opacity[n] += gop;
+  if (Go) Go[n] = oo + gop;
 }
 
 // Over the render's candidates (a grid-stride loop over the device-side
@@ -560,8 +585,7 @@ __global__ void __launch_bounds__(256, 2) preprocess_bwd_kernel(ParamsDev P, Cam
   const int nc = (int)*ncand;
   for (int ci = blockIdx.x * blockDim.x + threadIdx.x; ci < nc; ci += gridDim.x * blockDim.x) {
     const int n = (int)cand[ci];
-    if (tcount[n] == 0u) continue;
-    bwd_one<DEG, kVec>(P, cam, n, grec, G);
+    bwd_one<DEG, kVec>(P, cam, n, tcount[n], grec, G);
   }
 }
 
