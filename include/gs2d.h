@@ -234,7 +234,7 @@ gs_status gs_loss_noalloc(int32_t width, int32_t height, const float* out,
 
 /* Parameter gradients, device, same shapes as the parameters.  gs_backward
  * ADDS into them (like accumulating .grad); a null pointer skips that
- * parameter. */
+ * parameter.  The arrays must not overlap one another or the parameters. */
 typedef struct {
   float* mu;
   float* quat;

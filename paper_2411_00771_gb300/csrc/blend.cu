@@ -638,15 +638,21 @@ constexpr int batch_b(int min_ctas) { return min_ctas >= 5 ? 128 : 224; }
 constexpr int kDenseListLen = 400;
 
 // Per-pair gradient vector.  General layout (any adjoint planes):
-//   [0..15] per-surfel record (d Ji, d e, d c, d p_z, d opacity, d rgb,
-//   d normal), [16 + 2 s, 17 + 2 s] screen-space gradient of set s.
+//   [0..5] d Ji, d e; [6] Zc, the depth term of the centre gradient (below);
+//   [7] d p_z, [8] d opacity, [9..11] d rgb, [12..14] d normal;
+//   [15 + 2 s, 16 + 2 s] screen-space gradient of set s.
 // Loss layout (set 0 on colour and inverse depth only, later sets on
-// colour): the normal slots are dropped, [0..12] record without d normal,
-// [13 + 2 s, 14 + 2 s] screen gradients; the flush maps them back.
+// colour): the normal slots are dropped, [0..11] as above without d normal,
+// [12 + 2 s, 13 + 2 s] screen gradients.
+// The centre gradient is not accumulated on its own: per pair it is set 0's
+// screen gradient plus, on the object-space branch, the term of the depth
+// z = p_z / (1 + e.d) through d, (d rden / d d) p_z dz = -e p_z rden^2 dz;
+// so d c = (screen gradient of set 0) + e * Zc with Zc the sum of
+// p_z rden^2 dz, formed once per entry at the flush.
 template <bool kLoss>
 struct Layout {
-  static constexpr int kRec = kLoss ? 13 : kGradRec;
-  static constexpr int kN = kRec + 2 * kMaxSets;  // 19 or 22
+  static constexpr int kRec = kLoss ? 12 : kGradRec - 1;
+  static constexpr int kN = kRec + 2 * kMaxSets;  // 18 or 21
 };
 
 // Balanced reduce-scatter of N values over the warp: at each halving level
@@ -799,16 +805,15 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
   const float c2 = 2.f * q.rho * q.rden;
   const float u = q.nu * q.rden, vv = q.nv * q.rden;
   const float dnu = 2.f * u * q.rden * drho, dnv = 2.f * vv * q.rden * drho;
+  const float zr2 = dzv * pz * r2d;
   const float drden = 2.f * drho * (u * q.nu + vv * q.nv) + dzv * pz;
   const float dden = -drden * r2d;
   const bool ob = q.obj;
   const float rx = ob ? 2.f * r2d * tx - c2 * e0.z : 2.f * set.sinv * q.dx;
   const float ry = ob ? 2.f * r2d * ty - c2 * e0.w : 2.f * set.sinv * q.dy;
-  const float gdx = ob ? dnu * e1.x + dnv * e1.z + dden * e0.z : drho * rx;
-  const float gdy = ob ? dnu * e1.y + dnv * e1.w + dden * e0.w : drho * ry;
   const float gpz = ob ? dzv * q.rden : dzv;
-  // the object-space terms of Ji and e, zero (and finite) where the screen
-  // branch was taken
+  // the object-space terms of Ji, e and the centre's depth term, zero (and
+  // finite) where the screen branch was taken
   const float dnu_o = ob ? dnu : 0.f, dnv_o = ob ? dnv : 0.f, dden_o = ob ? dden : 0.f;
   v[0] = fmaf(dnu_o, q.dx, v[0]);
   v[1] = fmaf(dnu_o, q.dy, v[1]);
@@ -816,17 +821,16 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
   v[3] = fmaf(dnv_o, q.dy, v[3]);
   v[4] = fmaf(dden_o, q.dx, v[4]);
   v[5] = fmaf(dden_o, q.dy, v[5]);
-  v[6] -= gdx;
-  v[7] -= gdy;
-  v[8] += gpz;
-  v[9] = fmaf(dLda[0], unclamped ? q.G : 0.f, v[9]);
-  v[10] += w * p.gC[0][0];
-  v[11] += w * p.gC[0][1];
-  v[12] += w * p.gC[0][2];
+  v[6] += ob ? zr2 : 0.f;
+  v[7] += gpz;
+  v[8] = fmaf(dLda[0], unclamped ? q.G : 0.f, v[8]);
+  v[9] += w * p.gC[0][0];
+  v[10] += w * p.gC[0][1];
+  v[11] += w * p.gC[0][2];
   if constexpr (!kLoss) {
-    v[13] += w * p.gN0;
-    v[14] += w * p.gN1;
-    v[15] += w * p.gN2;
+    v[12] += w * p.gN0;
+    v[13] += w * p.gN1;
+    v[14] += w * p.gN2;
   }
 #pragma unroll
   for (int s = 0; s < kMaxSets; ++s) {
@@ -960,15 +964,23 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
       }
     }
     __syncthreads();
-    // flush this batch: one (surfel, tile) gradient record per entry
+    // flush this batch: one (surfel, tile) gradient record per entry, the
+    // centre gradient formed from set 0's screen gradient and Zc
     for (int t = threadIdx.x; t < nb; t += kThreads) {
       const uint32_t s = sh.sid[t];
       float* g = grec + (size_t)s * kGradRec;
+      const float* x = sh.acc[t];
+      const float4 e0 = sh.s0[t];
+      float r[kGradRec];
 #pragma unroll
-      for (int i = 0; i < LY::kRec; ++i) {
-        const float x = sh.acc[t][i];
-        if (x != 0.f) atomicAdd(&g[i], x);
-      }
+      for (int i = 0; i < 6; ++i) r[i] = x[i];
+      r[6] = fmaf(e0.z, x[6], x[LY::kRec]);
+      r[7] = fmaf(e0.w, x[6], x[LY::kRec + 1]);
+#pragma unroll
+      for (int i = 7; i < LY::kRec; ++i) r[i + 1] = x[i];
+#pragma unroll
+      for (int i = 0; i < LY::kRec + 1; ++i)
+        if (r[i] != 0.f) atomicAdd(&g[i], r[i]);
       if (screen) {
         for (int st = 0; st < nsets; ++st) {
           const float x0 = sh.acc[t][LY::kRec + 2 * st];
