@@ -794,23 +794,26 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
       dLda[s] = 0.f;
     }
   }
-  // alpha -> rho (zero where alpha is clamped at alpha_max)
+  // alpha -> rho (zero where alpha is clamped at alpha_max).  Every
+  // derivative of rho below carries a factor 2; it is kept in
+  // dadrho2 = 2 d alpha / d rho and drho2 = 2 dL / d rho (exact scalings),
+  // and rx, ry are half of d rho / d d.
   const bool unclamped = e2.y * q.G < set.alpha_max;
-  const float dadrho = unclamped ? -0.5f * q.alpha : 0.f;
-  const float drho = dLda[0] * dadrho;
+  const float dadrho2 = unclamped ? -q.alpha : 0.f;
+  const float drho2 = dLda[0] * dadrho2;
   // object-space branch: rho = u^2 + v^2 with (u, v) = (nu, nv) rden,
   // z = p_z rden (its terms may be non-finite where it was not taken)
   const float r2d = q.rden * q.rden;
   const float tx = q.nu * e1.x + q.nv * e1.z, ty = q.nu * e1.y + q.nv * e1.w;
-  const float c2 = 2.f * q.rho * q.rden;
+  const float c1 = q.rho * q.rden;
   const float u = q.nu * q.rden, vv = q.nv * q.rden;
-  const float dnu = 2.f * u * q.rden * drho, dnv = 2.f * vv * q.rden * drho;
+  const float dnu = u * q.rden * drho2, dnv = vv * q.rden * drho2;
   const float zr2 = dzv * pz * r2d;
-  const float drden = 2.f * drho * (u * q.nu + vv * q.nv) + dzv * pz;
+  const float drden = drho2 * (u * q.nu + vv * q.nv) + dzv * pz;
   const float dden = -drden * r2d;
   const bool ob = q.obj;
-  const float rx = ob ? 2.f * r2d * tx - c2 * e0.z : 2.f * set.sinv * q.dx;
-  const float ry = ob ? 2.f * r2d * ty - c2 * e0.w : 2.f * set.sinv * q.dy;
+  const float rx = ob ? r2d * tx - c1 * e0.z : set.sinv * q.dx;
+  const float ry = ob ? r2d * ty - c1 * e0.w : set.sinv * q.dy;
   const float gpz = ob ? dzv * q.rden : dzv;
   // the object-space terms of Ji, e and the centre's depth term, zero (and
   // finite) where the screen branch was taken
@@ -834,7 +837,7 @@ __device__ __forceinline__ void bwd_pair(BwdPix& p, const Pair& q, float4 e0, fl
   }
 #pragma unroll
   for (int s = 0; s < kMaxSets; ++s) {
-    const float dr = dLda[s] * dadrho;
+    const float dr = dLda[s] * dadrho2;
     v[LY::kRec + 2 * s] -= dr * rx;
     v[LY::kRec + 2 * s + 1] -= dr * ry;
   }
@@ -856,10 +859,9 @@ struct BwdSmem {
 template <bool kLoss, int kN, int kAcc, int kBB>
 __device__ __forceinline__ void bwd_entry(BwdSmem<kAcc, kBB>& sh, int kk, int k, float lx, float ly, BwdPix& a,
                                           BwdPix& b, int nsets, const SetDev& set, int lane, int myslot,
-                                          unsigned& replayed, unsigned& wentries, unsigned& wlanes) {
+                                          unsigned& wentries, unsigned& wlanes) {
   const float4 e0 = sh.s0[kk], jh = sh.s1[kk], e2 = sh.s2[kk];
   const bool liveA = k < a.last, liveB = k < b.last;
-  replayed += (unsigned)liveA + (unsigned)liveB;
   Pair qa, qb;
   const float4 jl = sh.s4[kk];
   eval_two(lx, ly, e0, jh, jl, sh.s5[kk], e2.y, set, qa, qb);
@@ -954,13 +956,24 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
     for (int i = threadIdx.x; i < nb * kAcc; i += kThreads) (&sh.acc[0][0])[i] = 0.f;
     __syncthreads();
     warp_entry_bits<kWordsB>(sh.sm, nb, warp, lane, sh.wbits[warp]);
+    if (counters) {
+      // the batch's entries before each pixel's last blended one that the
+      // warp visits (performance counter)
+#pragma unroll
+      for (int j = 0; j < kWordsB; ++j) {
+        const uint32_t bits = sh.wbits[warp][j];
+        const int la = a.last - b0 - 32 * j, lb = b.last - b0 - 32 * j;
+        replayed += (unsigned)__popc(la >= 32 ? bits : (la > 0 ? bits & ((1u << la) - 1u) : 0u));
+        replayed += (unsigned)__popc(lb >= 32 ? bits : (lb > 0 ? bits & ((1u << lb) - 1u) : 0u));
+      }
+    }
     for (int j = kWordsB - 1; j >= 0; --j) {
       uint32_t bits = sh.wbits[warp][j];
       while (bits != 0u) {  // back to front: highest set bit first
         const int hb = 31 - __clz(bits);
         bits &= ~(1u << hb);
         bwd_entry<kLoss, kN, kAcc, kBatchB>(sh, 32 * j + hb, b0 + 32 * j + hb, lx, lyA, a, b, nsets, set, lane, myslot,
-                                   replayed, wentries, wlanes);
+                                   wentries, wlanes);
       }
     }
     __syncthreads();
