@@ -935,6 +935,11 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
   atomicMax(&sh.smax, max(a.last, b.last));
   __syncthreads();
   const int maxlast = sh.smax;
+  // the warp's own last blended position: entries behind it are dead for all
+  // of its pixels and are not visited
+  int wlast = max(a.last, b.last);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
   unsigned replayed = 0, wentries = 0, wlanes = 0;
 
   for (int bend = maxlast; bend > 0; bend -= kBatchB) {
@@ -956,6 +961,14 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) blend_bwd_kernel(
     for (int i = threadIdx.x; i < nb * kAcc; i += kThreads) (&sh.acc[0][0])[i] = 0.f;
     __syncthreads();
     warp_entry_bits<kWordsB>(sh.sm, nb, warp, lane, sh.wbits[warp]);
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < kWordsB; ++j) {
+        const int lw = wlast - b0 - 32 * j;
+        sh.wbits[warp][j] &= lw >= 32 ? 0xffffffffu : (lw > 0 ? (1u << lw) - 1u : 0u);
+      }
+    }
+    __syncwarp();
     if (counters) {
       // the batch's entries before each pixel's last blended one that the
       // warp visits (performance counter)
