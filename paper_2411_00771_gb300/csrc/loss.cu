@@ -44,8 +44,10 @@ struct Gauss {
 
 // Stage a kHalo x kHalo window (top-left at (ox, oy)) of NP planes of a
 // W x H image, zero outside the image; all loads of a thread are issued
-// before the first store.
-constexpr int kStageIt = (kHalo * kHalo + kThr - 1) / kThr;  // 7
+// before the first store.  Thread t takes column t % kHalo of rows
+// t / kHalo, + kStageRows, ...: its index arithmetic is done once.
+constexpr int kStageRows = kThr / kHalo;                           // 6
+constexpr int kStageIt = (kHalo + kStageRows - 1) / kStageRows;    // 7
 template <int NP>
 struct Planes {
   const float* p[NP];
@@ -53,21 +55,22 @@ struct Planes {
 template <int NP>
 __device__ __forceinline__ void stage_halo(float (*dst)[kHalo][kSX], Planes<NP> src, int W, int H, int ox,
                                            int oy) {
+  const int r0 = threadIdx.x / kHalo, hx = threadIdx.x - r0 * kHalo;
+  if (r0 >= kStageRows) return;
+  const int gx = ox + hx;
+  const bool inx = gx >= 0 && gx < W;
   float v[NP][kStageIt];
 #pragma unroll
   for (int k = 0; k < kStageIt; ++k) {
-    const int i = threadIdx.x + k * kThr;
-    const int hy = i / kHalo, hx = i - hy * kHalo;
-    const int gx = ox + hx, gy = oy + hy;
-    const bool in = i < kHalo * kHalo && gx >= 0 && gx < W && gy >= 0 && gy < H;
+    const int hy = r0 + k * kStageRows, gy = oy + hy;
+    const bool in = inx && hy < kHalo && gy >= 0 && gy < H;
 #pragma unroll
     for (int q = 0; q < NP; ++q) v[q][k] = in ? src.p[q][(size_t)gy * W + gx] : 0.f;
   }
 #pragma unroll
   for (int k = 0; k < kStageIt; ++k) {
-    const int i = threadIdx.x + k * kThr;
-    if (i < kHalo * kHalo) {
-      const int hy = i / kHalo, hx = i - hy * kHalo;
+    const int hy = r0 + k * kStageRows;
+    if (hy < kHalo) {
 #pragma unroll
       for (int q = 0; q < NP; ++q) dst[q][hy][hx] = v[q][k];
     }
@@ -79,12 +82,12 @@ __device__ __forceinline__ void stage_halo(float (*dst)[kHalo][kSX], Planes<NP> 
 template <int NO>
 __device__ __forceinline__ void slide(const float* in, const Gauss& g, float* o) {
 #pragma unroll
-  for (int i = 0; i < NO; ++i) o[i] = 0.f;
-#pragma unroll
   for (int j = 0; j < NO + kTaps - 1; ++j)
 #pragma unroll
-    for (int i = 0; i < NO; ++i)
-      if (j - i >= 0 && j - i < kTaps) o[i] = fmaf(g.w[j - i], in[j], o[i]);
+    for (int i = 0; i < NO; ++i) {
+      if (j == i) o[i] = g.w[0] * in[j];
+      else if (j - i > 0 && j - i < kTaps) o[i] = fmaf(g.w[j - i], in[j], o[i]);
+    }
 }
 
 __global__ void __launch_bounds__(kThr) ssim_fwd_kernel(int W, int H, const float* __restrict__ out,
