@@ -13,15 +13,16 @@ namespace gs2d {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
+constexpr int kItems = 16;  // per thread in one-block scans
 constexpr int kWarps = kThreads / 32;
 constexpr int kRadixBits = 8;
 constexpr int kBins = 1 << kRadixBits;
 
 // Items per thread of the scans and radix passes, by the grid's item bound:
-// a small block (1024 items) spreads a few hundred thousand items over all
-// SMs and keeps each block's serial ranking short; large inputs take 4096
-// to keep the per-block digit counts (and the offsets scan over them) small.
+// a small block (1024 items, up to 4M items) spreads a few hundred thousand
+// items over all SMs and keeps each block's serial ranking short; larger
+// inputs take 2048 (up to 16M) and 4096 items per block, to keep the
+// per-block digit counts (and the offsets scan over them) small.
 inline int items_per_thread(int64_t n) { return n <= (int64_t(1) << 22) ? 4 : (n <= (int64_t(1) << 24) ? 8 : 16); }
 inline int64_t blocks_for(int64_t n) {
   const int64_t ti = (int64_t)kThreads * items_per_thread(n);
