@@ -438,14 +438,22 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const int2* __restrict
                                                           uint32_t* __restrict__ order) {
   __shared__ uint8_t oct[kMaxOrderTiles];
   __shared__ uint32_t cnt[32], cur[32];
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) cnt[threadIdx.x] = 0u;
   __syncthreads();
-#pragma unroll 8
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-    const int2 r = ranges[t];
-    const int o = __clz((uint32_t)(r.y - r.x) | 1u);  // 31 - octave: longest first
-    oct[t] = (uint8_t)o;
-    atomicAdd(&cnt[o], 1u);
+  // per warp and octave one shared-memory atomic (lanes of the same octave
+  // are counted together): a few octaves hold most tiles
+  for (int t0 = threadIdx.x - lane; t0 < ntiles; t0 += blockDim.x) {
+    const int t = t0 + lane;
+    const bool valid = t < ntiles;
+    uint32_t o = 32u;
+    if (valid) {
+      const int2 r = ranges[t];
+      o = (uint32_t)__clz((uint32_t)(r.y - r.x) | 1u);  // 31 - octave: longest first
+      oct[t] = (uint8_t)o;
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, o);
+    if (valid && lane == 31 - __clz(peers)) atomicAdd(&cnt[o], (uint32_t)__popc(peers));
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -460,7 +468,17 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const int2* __restrict
     cur[threadIdx.x] = v - c;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) order[atomicAdd(&cur[oct[t]], 1u)] = (uint32_t)t;
+  for (int t0 = threadIdx.x - lane; t0 < ntiles; t0 += blockDim.x) {
+    const int t = t0 + lane;
+    const bool valid = t < ntiles;
+    const uint32_t o = valid ? (uint32_t)oct[t] : 32u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, o);
+    const int leader = 31 - __clz(peers);
+    uint32_t base = 0u;
+    if (valid && lane == leader) base = atomicAdd(&cur[o], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) order[base + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
+  }
 }
 
 }  // namespace
